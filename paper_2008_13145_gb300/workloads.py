@@ -1,0 +1,180 @@
+"""Seeded synthetic workloads: shape grids and input matrices.
+
+This module holds recipes and random draws only, none of the method's
+arithmetic, so that both the CUDA path (tests, bench) and the CPU oracle can be
+fed from it without sharing any computation.
+
+Recipes (all from a counter-based Philox stream seeded per workload):
+
+* ``single_gemm_256``: one row-major NN GEMM, M = N = K = 256, alpha = 1,
+  beta = 0, A then B drawn i.i.d. uniform[-1, 1] from seed 0.
+* ``shape_grid``: the tuning grid, n shapes with M, N, K log-uniform in
+  [lo, hi] (rounded to integers), batch uniform in {1, 2, 4, 8, 16} and
+  transA / transB uniform in {N, T}.  The paper's own size sets come from
+  VGG, ResNet and MobileNet layers (Section 3, "The dataset"); they are not
+  available here, and this grid stands in for them.
+* ``vgg16_layers``: the 13 3x3 convolutions of VGG16 lowered by im2col
+  (M = H*W*batch, K = 9*Cin, N = Cout) and the three fully connected layers
+  (M = batch), following the network used in Section 6.
+* ``grouped_problems``: uneven groups of GEMMs with M, N, K log-uniform.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+BATCH_CHOICES = (1, 2, 4, 8, 16)
+
+
+def rng_for(seed: int, stream: int = 0) -> np.random.Generator:
+    """A Philox generator for (seed, stream); streams separate independent draws."""
+    return np.random.Generator(np.random.Philox(key=[seed, stream]))
+
+
+def round_up(x: int, m: int) -> int:
+    return ((int(x) + m - 1) // m) * m
+
+
+@dataclasses.dataclass(frozen=True)
+class Shape:
+    M: int
+    N: int
+    K: int
+    batch: int = 1
+    transA: str = "N"
+    transB: str = "N"
+
+    @property
+    def flops(self) -> int:
+        return 2 * self.M * self.N * self.K * self.batch
+
+    def stored_a(self) -> tuple[int, int]:
+        """(rows, cols) of A as stored (row-major)."""
+        return (self.M, self.K) if self.transA == "N" else (self.K, self.M)
+
+    def stored_b(self) -> tuple[int, int]:
+        return (self.K, self.N) if self.transB == "N" else (self.N, self.K)
+
+
+def log_uniform_int(rng: np.random.Generator, lo: int, hi: int, n: int) -> np.ndarray:
+    v = np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), n))).astype(np.int64)
+    return np.clip(v, lo, hi)
+
+
+def shape_grid(n: int = 1000, seed: int = 1, lo: int = 16, hi: int = 4096) -> list[Shape]:
+    """The tuning grid: M, N, K drawn (in that order) log-uniform, then batch, transA, transB."""
+    rng = rng_for(seed)
+    M = log_uniform_int(rng, lo, hi, n)
+    N = log_uniform_int(rng, lo, hi, n)
+    K = log_uniform_int(rng, lo, hi, n)
+    batch = rng.choice(np.array(BATCH_CHOICES), n)
+    ta = rng.integers(0, 2, n)
+    tb = rng.integers(0, 2, n)
+    return [Shape(int(M[i]), int(N[i]), int(K[i]), int(batch[i]),
+                  "NT"[int(ta[i])], "NT"[int(tb[i])]) for i in range(n)]
+
+
+def train_test_split(n: int, seed: int, train_frac: float = 0.8) -> tuple[np.ndarray, np.ndarray]:
+    """Seeded split of shape indices; the paper does not state its ratio, 80/20 is used."""
+    perm = rng_for(seed, 7).permutation(n)
+    n_train = int(round(train_frac * n))
+    return np.sort(perm[:n_train]), np.sort(perm[n_train:])
+
+
+def vgg16_layers(batch: int) -> list[tuple[str, Shape]]:
+    """VGG16 GEMMs.  Activations (im2col rows) are A (M x K, 'N'); weights are
+    stored output-channel-major (N x K), so op(B) = B^T ('T')."""
+    convs = [("conv1_1", 224, 3, 64), ("conv1_2", 224, 64, 64),
+             ("conv2_1", 112, 64, 128), ("conv2_2", 112, 128, 128),
+             ("conv3_1", 56, 128, 256), ("conv3_2", 56, 256, 256), ("conv3_3", 56, 256, 256),
+             ("conv4_1", 28, 256, 512), ("conv4_2", 28, 512, 512), ("conv4_3", 28, 512, 512),
+             ("conv5_1", 14, 512, 512), ("conv5_2", 14, 512, 512), ("conv5_3", 14, 512, 512)]
+    out = [(name, Shape(hw * hw * batch, cout, 9 * cin, 1, "N", "T")) for name, hw, cin, cout in convs]
+    out += [("fc6", Shape(batch, 4096, 25088, 1, "N", "T")),
+            ("fc7", Shape(batch, 4096, 4096, 1, "N", "T")),
+            ("fc8", Shape(batch, 1000, 4096, 1, "N", "T"))]
+    return out
+
+
+def grouped_problems(n: int = 256, seed: int = 3, lo: int = 32, hi: int = 4096) -> list[Shape]:
+    """Uneven group: M, N, K log-uniform; op(A) = A (M x K), op(B) = B^T with B
+    stored N x K, so both operands are K-contiguous."""
+    rng = rng_for(seed)
+    M = log_uniform_int(rng, lo, hi, n)
+    N = log_uniform_int(rng, lo, hi, n)
+    K = log_uniform_int(rng, lo, hi, n)
+    return [Shape(int(M[i]), int(N[i]), int(K[i]), 1, "N", "T") for i in range(n)]
+
+
+def uniform_matrix(rows: int, cols: int, ld: int, batch: int, seed: int, stream: int,
+                   lo: float = -1.0, hi: float = 1.0, pad_value: float = np.nan) -> np.ndarray:
+    """float32 array (batch, rows, ld): i.i.d. uniform[lo, hi) in the first
+    ``cols`` columns and ``pad_value`` in the padding, so that a kernel which
+    reads padding poisons its result."""
+    rng = rng_for(seed, stream)
+    out = np.full((batch, rows, ld), pad_value, dtype=np.float32)
+    vals = rng.uniform(lo, hi, size=(batch, rows, cols))
+    out[:, :, :cols] = vals.astype(np.float32)
+    return out
+
+
+def normal_matrix(rows: int, cols: int, ld: int, batch: int, seed: int, stream: int,
+                  std: float, absolute: bool = False, pad_value: float = np.nan) -> np.ndarray:
+    """float32 (batch, rows, ld) of N(0, std^2) draws (|.| of them if ``absolute``)."""
+    rng = rng_for(seed, stream)
+    out = np.full((batch, rows, ld), pad_value, dtype=np.float32)
+    vals = rng.normal(0.0, std, size=(batch, rows, cols))
+    if absolute:
+        vals = np.abs(vals)
+    out[:, :, :cols] = vals.astype(np.float32)
+    return out
+
+
+def integer_matrix(rows: int, cols: int, ld: int, batch: int, seed: int, stream: int,
+                   bound: int, pad_value: float = np.nan) -> np.ndarray:
+    """float32 (batch, rows, ld) of integers uniform in [-bound, bound]."""
+    rng = rng_for(seed, stream)
+    out = np.full((batch, rows, ld), pad_value, dtype=np.float32)
+    out[:, :, :cols] = rng.integers(-bound, bound + 1, size=(batch, rows, cols)).astype(np.float32)
+    return out
+
+
+def gemm_inputs(shape: Shape, seed: int, ld_multiple: int = 4, beta_nonzero: bool = False,
+                kind: str = "uniform", bound: int = 8):
+    """Seeded A, B, C0 for one shape, each float32 (batch, rows, ld) with ld the
+    stored column count rounded up to ``ld_multiple``.  A is drawn first, then B, then C0."""
+    ar, ac = shape.stored_a()
+    br, bc = shape.stored_b()
+    lda, ldb, ldc = round_up(ac, ld_multiple), round_up(bc, ld_multiple), round_up(shape.N, ld_multiple)
+    if kind == "uniform":
+        A = uniform_matrix(ar, ac, lda, shape.batch, seed, 1)
+        B = uniform_matrix(br, bc, ldb, shape.batch, seed, 2)
+        C0 = uniform_matrix(shape.M, shape.N, ldc, shape.batch, seed, 3) if beta_nonzero else \
+            np.full((shape.batch, shape.M, ldc), np.nan, dtype=np.float32)
+    elif kind == "integer":
+        A = integer_matrix(ar, ac, lda, shape.batch, seed, 1, bound)
+        B = integer_matrix(br, bc, ldb, shape.batch, seed, 2, bound)
+        C0 = integer_matrix(shape.M, shape.N, ldc, shape.batch, seed, 3, bound) if beta_nonzero else \
+            np.full((shape.batch, shape.M, ldc), np.nan, dtype=np.float32)
+    else:
+        raise ValueError(kind)
+    return A, B, C0
+
+
+def sample_positions(shape: Shape, n_rows: int, n_cols: int, seed: int) -> np.ndarray:
+    """Deterministic sample of output entries (b, i, j) for large-shape checks:
+    per batch entry, ``n_rows`` seeded rows x all columns plus ``n_cols``
+    seeded columns x all rows (duplicates removed)."""
+    rng = rng_for(seed, 11)
+    pos = []
+    for b in range(shape.batch):
+        rows = rng.choice(shape.M, size=min(n_rows, shape.M), replace=False)
+        cols = rng.choice(shape.N, size=min(n_cols, shape.N), replace=False)
+        for i in rows:
+            pos.append(np.stack([np.full(shape.N, b), np.full(shape.N, i), np.arange(shape.N)], 1))
+        for j in cols:
+            pos.append(np.stack([np.full(shape.M, b), np.arange(shape.M), np.full(shape.M, j)], 1))
+    p = np.unique(np.concatenate(pos, 0).astype(np.int64), axis=0)
+    return p

@@ -1,0 +1,195 @@
+"""Pins for the pruning/selection oracle: closed forms, brute force, invariants,
+and (where scikit-learn is present) library cross-checks."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import select as osel
+
+
+# ---------------------------------------------------------------- normalisation (Section 3.4)
+def test_sigmoid_closed_form():
+    perf = np.array([[0.85, 0.80, 1.0, 0.5]])
+    x = osel.normalise(perf, "sigmoid")[0]
+    assert x[0] == pytest.approx(0.5, abs=1e-15)
+    assert x[1] == pytest.approx(1.0 / (1.0 + math.exp(2.5)), rel=1e-14)
+    assert x[1] < 0.1
+    assert x[2] == pytest.approx(1.0 / (1.0 + math.exp(-7.5)), rel=1e-14)
+
+
+def test_standard_and_cutoffs():
+    perf = np.array([[10.0, 9.5, 8.0, 0.0], [0.0, 0.0, 0.0, 0.0], [2.0, 1.0, 4.0, 3.8]])
+    s = osel.normalise(perf, "standard")
+    assert np.array_equal(s[0], [1.0, 0.95, 0.8, 0.0])
+    assert np.array_equal(s[1], [0, 0, 0, 0])
+    assert s[2].max() == 1.0
+    r = osel.normalise(perf, "raw_cutoff")
+    assert np.array_equal(r[0], [1.0, 0.95, 0.0, 0.0])
+    sc = osel.normalise(perf, "standard_cutoff")
+    assert sc[0][0] == 1.0 and sc[0][1] == pytest.approx(0.5) and sc[0][2] == 0.0
+    assert sc[2][3] == pytest.approx(0.5)
+
+
+# ---------------------------------------------------------------- k-means (Section 4.1)
+def blobs(n_per, centres, spread, seed):
+    rng = np.random.default_rng(seed)
+    return np.concatenate([c + spread * rng.standard_normal((n_per, len(c))) for c in centres])
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_kmeans_reaches_brute_force_optimum(k):
+    X = blobs(3, [np.array([0.0, 0.0, 1.0]), np.array([1.0, 1.0, 0.0]), np.array([0.0, 1.0, 0.0])][:k],
+              0.05, seed=k)
+    if k == 2:
+        X = X[:7]
+    opt, _ = osel.brute_force_partition(X, k)
+    u = np.random.default_rng(1).random((10, k))
+    _, labels, inertia, _ = osel.kmeans(X, k, u)
+    assert inertia == pytest.approx(opt, rel=1e-12)
+
+
+def test_brute_force_small_case_by_hand():
+    # 1-D points {0, 1, 10, 11}, k = 2: optimum {0,1} | {10,11}, cost 0.5 + 0.5.
+    cost, labels = osel.brute_force_partition(np.array([[0.0], [1.0], [10.0], [11.0]]), 2)
+    assert cost == pytest.approx(1.0)
+    assert labels[0] == labels[1] != labels[2] == labels[3]
+
+
+def test_lloyd_inertia_non_increasing():
+    X = np.random.default_rng(4).random((60, 5))
+    C0 = X[[0, 1, 2, 3]]
+    prev = math.inf
+    for it in range(1, 12):
+        _, _, inertia, _ = osel.lloyd(X, C0, max_iter=it, tol=0.0)
+        assert inertia <= prev + 1e-12
+        prev = inertia
+
+
+def test_kmeanspp_first_centre_and_far_point():
+    X = np.array([[0.0], [0.1], [10.0]])
+    C = osel.kmeanspp_init(X, 2, np.array([0.0, 0.5]))
+    assert C[0, 0] == 0.0
+    # D^2 = [0, 0.01, 100]: half the total lies past point 1, so point 2 is picked.
+    assert C[1, 0] == 10.0
+
+
+def test_kmeans_matches_sklearn_inertia():
+    sk = pytest.importorskip("sklearn.cluster")
+    X = blobs(20, [np.zeros(6), np.ones(6), np.r_[np.ones(3), np.zeros(3)]], 0.1, seed=9)
+    u = np.random.default_rng(2).random((10, 3))
+    _, labels, inertia, _ = osel.kmeans(X, 3, u)
+    ref = sk.KMeans(3, n_init=10, random_state=0).fit(X)
+    assert inertia == pytest.approx(ref.inertia_, rel=1e-9)
+
+
+# ---------------------------------------------------------------- representatives / Top-N (Section 4.2)
+def test_representatives_argmax_and_dedupe():
+    centres = np.array([[0.1, 0.9, 0.8, 0.0],
+                        [0.2, 0.95, 0.1, 0.3],
+                        [1.0, 0.0, 0.0, 0.0]])
+    labels = np.array([0, 0, 0, 1, 1, 2])
+    assert list(osel.representatives(centres, labels, dedupe=True)) == [1, 3, 0]
+    # without dedupe the smaller cluster with the same best config is dropped
+    assert list(osel.representatives(centres, labels, dedupe=False)) == [1, 0]
+
+
+def test_cluster_geomean_representative():
+    X = np.array([[1.0, 0.5], [0.25, 1.0], [0.9, 0.8]])
+    # geometric means: col0 (1*0.25)^(1/2)=0.5, col1 (0.5*1)^(1/2)=0.707 -> 1 for cluster {0,1}
+    reps = osel.cluster_geomean_representatives(X, np.array([0, 0, 1]), 2)
+    assert list(reps) == [1, 0]
+
+
+def test_top_n_counts():
+    perf = np.array([[1, 2, 3], [3, 2, 1], [0, 5, 1], [1, 1, 9], [2, 1, 8.0]])
+    assert list(osel.top_n(perf, 2)) == [2, 0]
+    assert list(osel.top_n(perf, 3)) == [2, 0, 1]
+
+
+def test_top_n_fill():
+    perf = np.array([[1.0, 0.5, 0.9], [1.0, 0.2, 0.95]])
+    assert list(osel.top_n(perf, 3)) == [0, 2, 1]
+
+
+# ---------------------------------------------------------------- score (Section 4.3)
+def test_score_closed_form():
+    perf = np.array([[4.0, 2.0, 1.0], [1.0, 1.0, 2.0]])
+    s = osel.score(perf, deployed=np.array([1]))
+    assert s["geomean"] == pytest.approx(math.sqrt(0.5 * 0.5))
+    s = osel.score(perf, chosen=np.array([2, 0]))
+    assert s["geomean"] == pytest.approx(math.sqrt(0.25 * 0.5))
+    assert s["mean"] == pytest.approx(0.375)
+    assert osel.score(perf)["geomean"] == 1.0
+    assert osel.score(perf, deployed=np.arange(3))["geomean"] == 1.0
+
+
+def test_top_n_all_is_optimal():
+    perf = np.random.default_rng(0).random((30, 7))
+    assert osel.score(perf, deployed=osel.top_n(perf, 7))["geomean"] == pytest.approx(1.0)
+
+
+# ---------------------------------------------------------------- decision tree (Section 5.1)
+def brute_best_split(F, y, n_classes, min_leaf):
+    best = None
+    n = len(y)
+    for f in range(F.shape[1]):
+        for t in sorted(set(F[:, f])):
+            left = F[:, f] <= t
+            nl = left.sum()
+            if nl < min_leaf or n - nl < min_leaf:
+                continue
+            w = 0.0
+            for side in (left, ~left):
+                cnt = np.bincount(y[side], minlength=n_classes)
+                w += side.sum() * (1 - np.sum((cnt / side.sum()) ** 2))
+            if best is None or w / n < best - 1e-15:
+                best = w / n
+    return best
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_best_split_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    F = rng.integers(0, 6, (12, 3)).astype(float)
+    y = rng.integers(0, 3, 12)
+    s = osel.best_split(F, y, 3, 1)
+    assert s[2] == pytest.approx(brute_best_split(F, y, 3, 1), abs=1e-14)
+
+
+def test_tree_separable_is_perfect_and_limits_hold():
+    rng = np.random.default_rng(1)
+    F = rng.integers(16, 4096, (200, 4)).astype(float)
+    y = (F[:, 0] > 500).astype(int) + 2 * (F[:, 2] > 1000).astype(int)
+    nodes = osel.tree_train(F, y, 4)
+    assert np.array_equal(osel.tree_predict(nodes, F), y)
+    nodes_c = osel.tree_train(F, y, 4, max_depth=1, min_leaf=4)
+
+    def depth(j):
+        n = nodes_c[j]
+        return 0 if n["feature"] < 0 else 1 + max(depth(n["left"]), depth(n["right"]))
+    assert depth(0) <= 1
+    assert all(n["n"] >= 4 for n in nodes_c)
+
+
+def test_tree_matches_sklearn_on_tie_free_data():
+    sk = pytest.importorskip("sklearn.tree")
+    rng = np.random.default_rng(7)
+    F = rng.permutation(1000)[:300].reshape(100, 3).astype(float)
+    y = ((F[:, 0] > 400) ^ (F[:, 1] > 600)).astype(int) + (F[:, 2] > 800).astype(int)
+    for name, (depth, leaf) in osel.TREES.items():
+        nodes = osel.tree_train(F, y, 3, depth, leaf)
+        ref = sk.DecisionTreeClassifier(max_depth=depth, min_samples_leaf=leaf, random_state=0).fit(F, y)
+        Ft = rng.integers(0, 1000, (500, 3)).astype(float) + 0.25
+        assert np.array_equal(osel.tree_predict(nodes, Ft), ref.predict(Ft)), name
+
+
+# ---------------------------------------------------------------- PCA (Section 3.3)
+def test_pca_matches_svd():
+    X = np.random.default_rng(3).random((50, 8)) @ np.diag([5, 3, 1, 1, 0.5, 0.1, 0.1, 0.01])
+    ev = osel.pca_explained_variance(X)
+    s = np.linalg.svd(X - X.mean(0), compute_uv=False)
+    assert np.allclose(ev, s ** 2 / np.sum(s ** 2), rtol=1e-10, atol=1e-14)
+    assert osel.components_for(np.array([0.5, 0.3, 0.15, 0.05]), 0.8) == 2
+    assert osel.components_for(np.array([0.5, 0.3, 0.15, 0.05]), 0.95) == 3
