@@ -265,35 +265,44 @@ def score(perf: np.ndarray, deployed: np.ndarray | None = None, chosen: np.ndarr
 
 
 # ----------------------------------------------------------------------------- Section 5.1
-def gini(counts: np.ndarray) -> float:
-    n = counts.sum()
-    if n == 0:
-        return 0.0
-    p = counts / n
-    return float(1.0 - np.sum(p * p))
+def gini_ordered(counts: np.ndarray, n) -> np.ndarray:
+    """1 - sum_c (counts_c / n)^2 with the class sum taken in class order, so
+    that two splits with equal counts give bit-identical impurities.
+    ``counts`` is (..., n_classes), ``n`` broadcasts against its leading dims."""
+    n = np.asarray(n, np.float64)
+    s = np.zeros(counts.shape[:-1], np.float64)
+    for c in range(counts.shape[-1]):
+        p = counts[..., c] / n
+        s = s + p * p
+    return 1.0 - s
 
 
 def best_split(F: np.ndarray, y: np.ndarray, n_classes: int, min_leaf: int):
-    """Lowest weighted child Gini over every (feature, midpoint threshold) whose
-    two sides each hold >= min_leaf samples.  Features in column order,
-    thresholds ascending; the first best is kept.  Returns (feature, threshold,
-    weighted impurity) or None."""
+    """Lowest weighted child Gini, (n_L G_L + n_R G_R) / n, over every
+    (feature, midpoint threshold) whose two sides each hold >= min_leaf
+    samples.  Features in column order, thresholds ascending; the first best
+    is kept.  Returns (feature, threshold, weighted impurity) or None."""
     n = len(y)
     best = None
     for f in range(F.shape[1]):
-        vals = np.unique(F[:, f])
-        for a, b in zip(vals[:-1], vals[1:]):
-            t = (float(a) + float(b)) / 2.0
-            left = F[:, f] <= t
-            nl = int(left.sum())
-            nr = n - nl
-            if nl < min_leaf or nr < min_leaf:
-                continue
-            gl = gini(np.bincount(y[left], minlength=n_classes).astype(np.float64))
-            gr = gini(np.bincount(y[~left], minlength=n_classes).astype(np.float64))
-            w = (nl * gl + nr * gr) / n
-            if best is None or w < best[2]:
-                best = (f, t, w)
+        order = np.argsort(F[:, f], kind="stable")
+        xs = F[order, f]
+        onehot = np.zeros((n, n_classes))
+        onehot[np.arange(n), y[order]] = 1.0
+        cum = np.cumsum(onehot, axis=0)            # class counts of the first i+1 sorted samples
+        pos = np.nonzero(xs[:-1] < xs[1:])[0]      # split between sorted positions i and i+1
+        nl = (pos + 1).astype(np.float64)
+        nr = n - nl
+        ok = (nl >= min_leaf) & (nr >= min_leaf)
+        pos, nl, nr = pos[ok], nl[ok], nr[ok]
+        if len(pos) == 0:
+            continue
+        cl = cum[pos]
+        cr = cum[-1] - cl
+        w = (nl * gini_ordered(cl, nl) + nr * gini_ordered(cr, nr)) / n
+        j = int(np.argmin(w))
+        if best is None or w[j] < best[2]:
+            best = (f, (float(xs[pos[j]]) + float(xs[pos[j] + 1])) / 2.0, float(w[j]))
     return best
 
 
