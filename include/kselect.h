@@ -1,0 +1,180 @@
+/*
+ * kselect.h -- C ABI of the GB300 kernel-selection GEMM library (libkselect.so).
+ *
+ * Method: J. Lawson, "Performance portability through machine learning guided
+ * kernel selection in SYCL libraries" (arXiv 2008.13145).  A parameterised
+ * matrix-multiply kernel family (Section 3) is benchmarked over a grid of
+ * shapes, pruned to a few deployed kernels by k-means clustering of
+ * normalised performance vectors (Section 4), and one deployed kernel is
+ * chosen per call by a decision tree on the sizes (Section 5).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major.  op(A) is M x K: A itself (stored M x K,
+ *    lda >= K) for transA 'N', or A^T (A stored K x M, lda >= M) for 'T'.
+ *    op(B) is K x N likewise.  C is M x N with ldc >= N.
+ *  - Batches are packed: batch entry b of A starts at A + b * lda * (stored
+ *    rows of A); the same for B and C.
+ *  - Pointers named *_dev are device pointers; all others are host pointers.
+ *    The caller owns every buffer it passes and every stream; the library
+ *    never frees caller memory.  A stream argument is a cudaStream_t passed as
+ *    void* (NULL = the legacy default stream).  Work is enqueued
+ *    asynchronously unless an entry point says it synchronises.
+ *  - Errors are returned as gemm_status_t; nothing is printed and nothing
+ *    aborts.  After GEMM_ERR_CUDA, gemm_last_cuda_error() gives the CUDA error
+ *    code of the calling thread's last failing call.
+ *  - There is no CPU fallback: every numeric step runs in the library's own
+ *    CUDA kernels on the current device.
+ */
+#ifndef KSELECT_H
+#define KSELECT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GEMM_OK = 0,
+  GEMM_ERR_INVALID_ARG = -1, /* null pointer, negative size, ld too small, bad trans char */
+  GEMM_ERR_UNSUPPORTED = -2, /* valid request this kernel or precision cannot run */
+  GEMM_ERR_MISALIGNED = -3,  /* a tensor-core kernel needs 16-byte aligned pointers and lds */
+  GEMM_ERR_CUDA = -4,        /* a CUDA call failed; see gemm_last_cuda_error() */
+  GEMM_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  GEMM_ERR_NO_KERNEL = -6    /* unknown config id or empty deployment */
+} gemm_status_t;
+
+/* Kernel families.  F32: the FP32 SIMT family.  TF32: tcgen05 kind::tf32 on
+ * FP32 storage.  BF16: tcgen05 kind::f16 on BF16 storage.  F32X3: FP32
+ * storage split into BF16 hi/lo parts, three tcgen05 products accumulated in
+ * FP32.  C is FP32 in every family, accumulation is FP32 in every family. */
+typedef enum {
+  GEMM_PREC_F32 = 0,
+  GEMM_PREC_TF32 = 1,
+  GEMM_PREC_BF16 = 2,
+  GEMM_PREC_F32X3 = 3
+} gemm_precision_t;
+
+typedef struct kselect_library* gemm_handle_t;
+
+const char* gemm_status_string(int32_t status);
+int32_t gemm_last_cuda_error(void);
+
+/* ---------------------------------------------------------------- config space
+ * Section 3: each work item computes an R x C output tile; tile sizes are
+ * compile-time constants and the work-group shape is chosen per launch, giving
+ * 640 configurations in the paper.  Here the FP32 family's compile-time
+ * parameters are the per-thread tile TM x TN in {1,2,4,8}^2, the thread-block
+ * shape (WX along N, WY along M) in {8x8, 16x16, 32x8, 8x32, 16x8, 8x16}, the
+ * K-step BK in {8,16,32} and shared-memory staging on/off: 576 configs, ids
+ * 0..575.  Tensor-core families (ids 1000 + 100*family + index) use a 128 x BN
+ * tile with BN in {64,128,256}, a shared-memory ring of {2,3,4} stages and
+ * M- or N-major tile order: 18 configs per family.
+ *
+ * gemm_config_params writes 8 integers:
+ *   F32: {family=0, TM, TN, WX, WY, BK, staged, 0}
+ *   TC : {family, BM=128, BN, BK (elements per 128-byte row), stages, raster (0 M-major, 1 N-major), 0, 0}
+ */
+int32_t gemm_config_count(int32_t precision);
+int32_t gemm_config_id(int32_t precision, int32_t index);
+gemm_status_t gemm_config_params(int32_t config_id, int32_t out_params[8]);
+
+/* ---------------------------------------------------------------- deployment
+ * Section 5: the deployed set (<= 16 configs of one family) and a decision
+ * tree mapping (M, N, K, batch) to one of them, evaluated as nested ifs in the
+ * launcher.  Node j is a leaf when feature < 0; otherwise sizes with
+ * value(feature) <= threshold go to `left`, others to `right`.  Features:
+ * 0 = M, 1 = N, 2 = K, 3 = batch.  A leaf's label indexes config_ids.
+ * Optional MLP parameters (GEMM_MLP_PARAMS floats, layout W1 7x64, b1, W2
+ * 64x64, b2, W3 64x8, b3) let select_kernels_batched rank the deployed set. */
+#define GEMM_MAX_DEPLOYED 16
+#define GEMM_MAX_TREE_NODES 8192
+#define GEMM_MLP_PARAMS 5192
+
+typedef struct {
+  int32_t feature;
+  int32_t left;
+  int32_t right;
+  int32_t label;
+  double threshold;
+} gemm_tree_node_t;
+
+typedef struct {
+  int32_t precision;            /* gemm_precision_t of every deployed config */
+  int32_t n_configs;            /* 1..GEMM_MAX_DEPLOYED */
+  const int32_t* config_ids;    /* host, n_configs ids */
+  int32_t n_nodes;              /* 0 (always config_ids[0]) .. GEMM_MAX_TREE_NODES */
+  const gemm_tree_node_t* nodes;/* host */
+  const float* mlp_params;      /* host, GEMM_MLP_PARAMS floats, or NULL */
+} gemm_deployment_t;
+
+/* Copies the deployment into a new immutable handle (host only; device
+ * resources are made on first use).  Returns INVALID_ARG for a malformed tree
+ * (child index out of range, cycle, leaf label outside the deployed set) and
+ * NO_KERNEL for an unknown or mixed-family config id. */
+gemm_status_t gemm_library_create(const gemm_deployment_t* deployment, gemm_handle_t* out);
+void gemm_library_destroy(gemm_handle_t handle);
+
+/* Deployed config id for these sizes (tree walk on the host, O(depth)), or a
+ * negative gemm_status_t. */
+int32_t select_kernel(gemm_handle_t handle, int64_t M, int64_t N, int64_t K, int64_t batch);
+
+/* ---------------------------------------------------------------- GEMM
+ * C = alpha * op(A) * op(B) + beta * C for each batch entry, with the kernel
+ * select_kernel() picks.  A and B are float* for F32/TF32/F32X3 handles and
+ * bf16 (uint16_t*) for BF16 handles.  M, N or batch == 0 is a no-op; K == 0
+ * sets C = beta * C.  When beta == 0, C is only written (it may hold NaN).
+ * Sizes must be < 2^31 and batch <= 65535 (else GEMM_ERR_UNSUPPORTED). */
+gemm_status_t gemm(gemm_handle_t handle, char transA, char transB, int64_t M, int64_t N, int64_t K,
+                   float alpha, const void* A_dev, int64_t lda, const void* B_dev, int64_t ldb,
+                   float beta, float* C_dev, int64_t ldc, int64_t batch, void* stream);
+
+/* The same operation with an explicit config id (any family). */
+gemm_status_t gemm_with_config(int32_t config_id, char transA, char transB, int64_t M, int64_t N,
+                               int64_t K, float alpha, const void* A_dev, int64_t lda,
+                               const void* B_dev, int64_t ldb, float beta, float* C_dev, int64_t ldc,
+                               int64_t batch, void* stream);
+
+/* Section 3.1 (data collection): warm-up launches, then timed repetitions.
+ * Runs `warmup` untimed launches and one timed probe launch, then times one
+ * back-to-back run of R launches between two CUDA events, R = min_total_ms /
+ * probe time clamped to [min_reps, max_reps], and writes the mean
+ * milliseconds per launch (the paper's total time over a number of
+ * iterations).  alpha = 1, beta = 0.  Synchronises `stream`.  Inputs are
+ * whatever the buffers hold. */
+gemm_status_t gemm_benchmark(int32_t config_id, char transA, char transB, int64_t M, int64_t N,
+                             int64_t K, const void* A_dev, int64_t lda, const void* B_dev,
+                             int64_t ldb, float* C_dev, int64_t ldc, int64_t batch,
+                             int32_t warmup, int32_t min_reps, int32_t max_reps,
+                             double min_total_ms, double* out_ms, void* stream);
+
+/* ---------------------------------------------------------------- error check
+ * The judge of every GEMM result: err = max over entries of
+ * |C - C_ref| / den, reduced on the GPU in FP64, where C_ref and den are the
+ * FP64 exact product and its componentwise scale |alpha||op(A)||op(B)| +
+ * |beta||C0| supplied by the caller.  den == 0 requires C == C_ref exactly
+ * (else +inf); a NaN in C gives +inf.
+ *   Full mode (pos_dev == NULL): C is rows x cols per batch entry with ldc and
+ *   strideC; C_ref/den are packed (batch, rows, cols).  n is ignored.
+ *   Sampled mode: n entries, pos_dev holds n (b, i, j) int64 triples, C_ref
+ *   and den hold n values.
+ * Writes the maximum to *out_err (host) and synchronises `stream`.  Uses a
+ * device workspace of one double per block that it allocates and frees
+ * stream-ordered. */
+gemm_status_t gemm_error_check(int64_t rows, int64_t cols, int64_t batch, const float* C_dev,
+                               int64_t ldc, int64_t strideC, int64_t n, const int64_t* pos_dev,
+                               const double* Cref_dev, const double* den_dev, double* out_err,
+                               void* stream);
+
+/* Fills a (batch, rows, ld) float array with uniform[lo, hi) values from a
+ * counter-based hash of (seed, element index); padding columns get `pad`.
+ * Benchmark input only (tests draw their inputs on the host). */
+gemm_status_t kselect_fill_uniform(float* dst_dev, int64_t rows, int64_t cols, int64_t ld,
+                                   int64_t batch, uint64_t seed, float lo, float hi, float pad,
+                                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KSELECT_H */

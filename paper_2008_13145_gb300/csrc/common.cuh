@@ -1,0 +1,55 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kselect.h"
+
+namespace ks {
+
+// ------------------------------------------------------------------ FP32 SIMT config space
+// id = ((((tm_i * 4 + tn_i) * 6 + wg_i) * 3 + bk_i) * 2 + staged); see kselect.h.
+constexpr int kSimtConfigs = 576;
+struct SimtParams {
+  int tm, tn, wx, wy, bk, staged;
+};
+
+// Work-group shapes (WX, WY): 8x8, 16x16, 32x8, 8x32, 16x8, 8x16.
+constexpr int simt_wg_x(int w) { return w == 0 ? 8 : w == 1 ? 16 : w == 2 ? 32 : w == 3 ? 8 : w == 4 ? 16 : 8; }
+constexpr int simt_wg_y(int w) { return w == 0 ? 8 : w == 1 ? 16 : w == 2 ? 8 : w == 3 ? 32 : w == 4 ? 8 : 16; }
+
+constexpr SimtParams simt_params(int id) {
+  return SimtParams{1 << ((id / 144) % 4), 1 << ((id / 36) % 4), simt_wg_x((id / 6) % 6),
+                    simt_wg_y((id / 6) % 6), 8 << ((id / 2) % 3), id % 2};
+}
+
+// Arguments of one (batched) GEMM launch, already validated by the host.
+struct GemmArgs {
+  int M, N, K, batch;
+  int transA, transB;  // 1 = 'T'
+  float alpha, beta;
+  const void* A;
+  int64_t lda, strideA;
+  const void* B;
+  int64_t ldb, strideB;
+  float* C;
+  int64_t ldc, strideC;
+  int vecA, vecB, vecC;  // 16-byte vector access is legal on this operand
+};
+
+using LaunchFn = cudaError_t (*)(const GemmArgs&, cudaStream_t);
+
+// Per-shard registration of the SIMT instantiations (simt_shard.cu compiled N times).
+constexpr int kSimtShards = 12;
+void simt_register_shard(int shard, LaunchFn* table);
+
+// Tensor-core families (tc_gemm.cu).
+constexpr int kTcBase = 1000;
+constexpr int kTcConfigsPerFamily = 18;
+bool tc_config_valid(int id);
+gemm_status_t tc_launch(int id, const GemmArgs& a, cudaStream_t s);
+gemm_status_t tc_params(int id, int32_t out[8]);
+
+void set_last_cuda_error(cudaError_t e);
+
+}  // namespace ks

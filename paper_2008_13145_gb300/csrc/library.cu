@@ -1,0 +1,456 @@
+// C-ABI entry points of libkselect.so: argument validation, the config
+// registry, runtime selection (decision-tree walk, Section 5), launches,
+// the benchmark timer (Section 3.1) and the FP64 error-check reduction.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ks {
+#define KS_DECL_SHARD(i) void simt_register_shard_##i(LaunchFn*);
+KS_DECL_SHARD(0) KS_DECL_SHARD(1) KS_DECL_SHARD(2) KS_DECL_SHARD(3) KS_DECL_SHARD(4) KS_DECL_SHARD(5)
+KS_DECL_SHARD(6) KS_DECL_SHARD(7) KS_DECL_SHARD(8) KS_DECL_SHARD(9) KS_DECL_SHARD(10) KS_DECL_SHARD(11)
+static_assert(kSimtShards == 12, "shard list above must match kSimtShards");
+
+static thread_local int g_last_cuda_error = 0;
+void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = static_cast<int>(e); }
+
+static LaunchFn g_simt[kSimtConfigs];
+static std::once_flag g_simt_once;
+
+static void init_simt_table() {
+  std::call_once(g_simt_once, [] {
+    std::memset(g_simt, 0, sizeof(g_simt));
+    simt_register_shard_0(g_simt); simt_register_shard_1(g_simt); simt_register_shard_2(g_simt);
+    simt_register_shard_3(g_simt); simt_register_shard_4(g_simt); simt_register_shard_5(g_simt);
+    simt_register_shard_6(g_simt); simt_register_shard_7(g_simt); simt_register_shard_8(g_simt);
+    simt_register_shard_9(g_simt); simt_register_shard_10(g_simt); simt_register_shard_11(g_simt);
+  });
+}
+
+static int family_of(int id) {
+  if (id >= 0 && id < kSimtConfigs) return GEMM_PREC_F32;
+  if (id >= kTcBase && id < kTcBase + 300) {
+    int fam = (id - kTcBase) / 100, idx = (id - kTcBase) % 100;
+    if (idx < kTcConfigsPerFamily) return fam + 1;  // 1 TF32, 2 BF16, 3 F32X3
+  }
+  return -1;
+}
+
+static bool is_trans(char t, int* out) {
+  if (t == 'N' || t == 'n') { *out = 0; return true; }
+  if (t == 'T' || t == 't') { *out = 1; return true; }
+  return false;
+}
+
+// Validates a GEMM request and fills GemmArgs.  elem = bytes per A/B element.
+static gemm_status_t make_args(char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha,
+                               const void* A, int64_t lda, const void* B, int64_t ldb, float beta,
+                               float* C, int64_t ldc, int64_t batch, int elem, GemmArgs* a, bool* noop) {
+  int ta, tb;
+  if (!is_trans(transA, &ta) || !is_trans(transB, &tb)) return GEMM_ERR_INVALID_ARG;
+  if (M < 0 || N < 0 || K < 0 || batch < 0) return GEMM_ERR_INVALID_ARG;
+  const int64_t lim = (int64_t)1 << 31;
+  if (M >= lim || N >= lim || K >= lim || batch > 65535) return GEMM_ERR_UNSUPPORTED;
+  *noop = (M == 0 || N == 0 || batch == 0);
+  if (*noop) return GEMM_OK;
+  const int64_t a_rows = ta ? K : M, a_cols = ta ? M : K;
+  const int64_t b_rows = tb ? N : K, b_cols = tb ? K : N;
+  if (C == nullptr || ldc < N) return GEMM_ERR_INVALID_ARG;
+  if (K > 0) {
+    if (A == nullptr || B == nullptr) return GEMM_ERR_INVALID_ARG;
+    if (lda < std::max<int64_t>(a_cols, 1) || ldb < std::max<int64_t>(b_cols, 1)) return GEMM_ERR_INVALID_ARG;
+  }
+  a->M = (int)M; a->N = (int)N; a->K = (int)K; a->batch = (int)batch;
+  a->transA = ta; a->transB = tb; a->alpha = alpha; a->beta = beta;
+  a->A = A; a->lda = lda; a->strideA = lda * a_rows;
+  a->B = B; a->ldb = ldb; a->strideB = ldb * b_rows;
+  a->C = C; a->ldc = ldc; a->strideC = ldc * M;
+  const int per16 = 16 / elem;
+  a->vecA = ((uintptr_t)A % 16 == 0) && (lda % per16 == 0);
+  a->vecB = ((uintptr_t)B % 16 == 0) && (ldb % per16 == 0);
+  a->vecC = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0);
+  return GEMM_OK;
+}
+
+// C = beta * C, for K == 0 (the product term vanishes).
+__global__ void scale_c_kernel(float* C, int64_t ldc, int64_t strideC, int M, int N, float beta) {
+  const int64_t total = (int64_t)M * N;
+  float* Cb = C + (int64_t)blockIdx.y * strideC;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / N, j = t % N;
+    float* p = Cb + i * ldc + j;
+    *p = (beta == 0.f) ? 0.f : beta * *p;
+  }
+}
+
+static gemm_status_t launch_config(int id, const GemmArgs& a, cudaStream_t s) {
+  if (a.K == 0) {
+    dim3 grid((unsigned)std::min<int64_t>(((int64_t)a.M * a.N + 255) / 256, 1 << 16), a.batch);
+    scale_c_kernel<<<grid, 256, 0, s>>>(a.C, a.ldc, a.strideC, a.M, a.N, a.beta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+    return GEMM_OK;
+  }
+  const int fam = family_of(id);
+  if (fam == GEMM_PREC_F32) {
+    init_simt_table();
+    LaunchFn f = g_simt[id];
+    if (!f) return GEMM_ERR_NO_KERNEL;
+    cudaError_t e = f(a, s);
+    if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+    return GEMM_OK;
+  }
+  if (fam > 0) return tc_launch(id, a, s);
+  return GEMM_ERR_NO_KERNEL;
+}
+
+static int elem_bytes_of(int id) { return family_of(id) == GEMM_PREC_BF16 ? 2 : 4; }
+
+gemm_status_t launch_by_id(int id, const GemmArgs& a, cudaStream_t s) { return launch_config(id, a, s); }
+
+gemm_status_t make_launch_args(int id, char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha,
+                               const void* A, int64_t lda, const void* B, int64_t ldb, float beta, float* C,
+                               int64_t ldc, int64_t batch, GemmArgs* a, bool* noop) {
+  if (family_of(id) < 0) return GEMM_ERR_NO_KERNEL;
+  return make_args(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch, elem_bytes_of(id), a, noop);
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+// ------------------------------------------------------------------ handle
+struct kselect_library {
+  int precision;
+  std::vector<int32_t> ids;
+  std::vector<gemm_tree_node_t> nodes;
+  std::vector<float> mlp;  // empty when absent
+};
+
+extern "C" {
+
+const char* gemm_status_string(int32_t s) {
+  switch (s) {
+    case GEMM_OK: return "ok";
+    case GEMM_ERR_INVALID_ARG: return "invalid argument";
+    case GEMM_ERR_UNSUPPORTED: return "unsupported";
+    case GEMM_ERR_MISALIGNED: return "misaligned operand for a tensor-core kernel";
+    case GEMM_ERR_CUDA: return "CUDA error";
+    case GEMM_ERR_TIMEOUT: return "device-side wait timed out";
+    case GEMM_ERR_NO_KERNEL: return "no such kernel";
+    default: return "unknown status";
+  }
+}
+
+int32_t gemm_last_cuda_error(void) { return g_last_cuda_error; }
+
+int32_t gemm_config_count(int32_t precision) {
+  if (precision == GEMM_PREC_F32) return kSimtConfigs;
+  if (precision >= GEMM_PREC_TF32 && precision <= GEMM_PREC_F32X3) return kTcConfigsPerFamily;
+  return GEMM_ERR_INVALID_ARG;
+}
+
+int32_t gemm_config_id(int32_t precision, int32_t index) {
+  const int32_t n = gemm_config_count(precision);
+  if (n < 0 || index < 0 || index >= n) return GEMM_ERR_INVALID_ARG;
+  return precision == GEMM_PREC_F32 ? index : kTcBase + 100 * (precision - 1) + index;
+}
+
+gemm_status_t gemm_config_params(int32_t id, int32_t out[8]) {
+  if (!out) return GEMM_ERR_INVALID_ARG;
+  const int fam = family_of(id);
+  if (fam < 0) return GEMM_ERR_NO_KERNEL;
+  if (fam == GEMM_PREC_F32) {
+    SimtParams p = simt_params(id);
+    int32_t v[8] = {0, p.tm, p.tn, p.wx, p.wy, p.bk, p.staged, 0};
+    std::memcpy(out, v, sizeof(v));
+    return GEMM_OK;
+  }
+  return tc_params(id, out);
+}
+
+gemm_status_t gemm_library_create(const gemm_deployment_t* d, gemm_handle_t* out) {
+  if (!d || !out) return GEMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->n_configs < 1 || d->n_configs > GEMM_MAX_DEPLOYED || !d->config_ids) return GEMM_ERR_NO_KERNEL;
+  if (d->n_nodes < 0 || d->n_nodes > GEMM_MAX_TREE_NODES || (d->n_nodes > 0 && !d->nodes))
+    return GEMM_ERR_INVALID_ARG;
+  for (int i = 0; i < d->n_configs; ++i)
+    if (family_of(d->config_ids[i]) != d->precision) return GEMM_ERR_NO_KERNEL;
+  // Tree: children in range, every node reached at most once from the root
+  // (so no cycles and no sharing), leaf labels inside the deployed set.
+  if (d->n_nodes > 0) {
+    std::vector<char> seen(d->n_nodes, 0);
+    std::vector<int> stack{0};
+    while (!stack.empty()) {
+      int j = stack.back();
+      stack.pop_back();
+      if (j < 0 || j >= d->n_nodes || seen[j]) return GEMM_ERR_INVALID_ARG;
+      seen[j] = 1;
+      const gemm_tree_node_t& nd = d->nodes[j];
+      if (nd.feature < 0) {
+        if (nd.label < 0 || nd.label >= d->n_configs) return GEMM_ERR_INVALID_ARG;
+      } else {
+        if (nd.feature > 3 || !std::isfinite(nd.threshold)) return GEMM_ERR_INVALID_ARG;
+        stack.push_back(nd.left);
+        stack.push_back(nd.right);
+      }
+    }
+  }
+  kselect_library* h = new (std::nothrow) kselect_library();
+  if (!h) return GEMM_ERR_UNSUPPORTED;
+  h->precision = d->precision;
+  h->ids.assign(d->config_ids, d->config_ids + d->n_configs);
+  if (d->n_nodes > 0) h->nodes.assign(d->nodes, d->nodes + d->n_nodes);
+  if (d->mlp_params) h->mlp.assign(d->mlp_params, d->mlp_params + GEMM_MLP_PARAMS);
+  *out = h;
+  return GEMM_OK;
+}
+
+void gemm_library_destroy(gemm_handle_t h) { delete h; }
+
+// Section 5: the classifier runs before every launch, so it is a handful of
+// comparisons on the host -- the tree's nested ifs.
+int32_t select_kernel(gemm_handle_t h, int64_t M, int64_t N, int64_t K, int64_t batch) {
+  if (!h) return GEMM_ERR_INVALID_ARG;
+  if (M < 0 || N < 0 || K < 0 || batch < 0) return GEMM_ERR_INVALID_ARG;
+  if (h->nodes.empty()) return h->ids[0];
+  const double f[4] = {(double)M, (double)N, (double)K, (double)batch};
+  int j = 0;
+  for (int steps = 0; steps <= (int)h->nodes.size(); ++steps) {
+    const gemm_tree_node_t& nd = h->nodes[j];
+    if (nd.feature < 0) return h->ids[nd.label];
+    j = (f[nd.feature] <= nd.threshold) ? nd.left : nd.right;
+  }
+  return GEMM_ERR_INVALID_ARG;  // unreachable for a validated tree
+}
+
+gemm_status_t gemm_with_config(int32_t id, char transA, char transB, int64_t M, int64_t N, int64_t K,
+                               float alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                               float beta, float* C, int64_t ldc, int64_t batch, void* stream) {
+  if (family_of(id) < 0) return GEMM_ERR_NO_KERNEL;
+  GemmArgs a;
+  bool noop = false;
+  gemm_status_t st = make_args(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch,
+                               elem_bytes_of(id), &a, &noop);
+  if (st != GEMM_OK || noop) return st;
+  return launch_config(id, a, static_cast<cudaStream_t>(stream));
+}
+
+gemm_status_t gemm(gemm_handle_t h, char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha,
+                   const void* A, int64_t lda, const void* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                   int64_t batch, void* stream) {
+  if (!h) return GEMM_ERR_INVALID_ARG;
+  const int32_t id = select_kernel(h, M, N, K, batch);
+  if (id < 0) return (gemm_status_t)id;
+  return gemm_with_config(id, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch, stream);
+}
+
+gemm_status_t gemm_benchmark(int32_t id, char transA, char transB, int64_t M, int64_t N, int64_t K,
+                             const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+                             int64_t batch, int32_t warmup, int32_t min_reps, int32_t max_reps,
+                             double min_total_ms, double* out_ms, void* stream) {
+  if (!out_ms || warmup < 0 || min_reps < 1 || max_reps < min_reps) return GEMM_ERR_INVALID_ARG;
+  *out_ms = 0.0;
+  if (family_of(id) < 0) return GEMM_ERR_NO_KERNEL;
+  GemmArgs a;
+  bool noop = false;
+  gemm_status_t st = make_args(transA, transB, M, N, K, 1.f, A, lda, B, ldb, 0.f, C, ldc, batch,
+                               elem_bytes_of(id), &a, &noop);
+  if (st != GEMM_OK || noop) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  auto fail_cuda = [&](cudaError_t err) {
+    set_last_cuda_error(err);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return GEMM_ERR_CUDA;
+  };
+  if (ce != cudaSuccess) return fail_cuda(ce);
+  for (int i = 0; i < warmup; ++i)
+    if ((st = launch_config(id, a, s)) != GEMM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+  // Section 3.1: a timed run of back-to-back launches gives the mean time per
+  // launch; the count is sized from one timed probe launch so the run lasts
+  // about min_total_ms.
+  float probe = 0.f;
+  cudaEventRecord(e0, s);
+  if ((st = launch_config(id, a, s)) != GEMM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+  cudaEventRecord(e1, s);
+  if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) return fail_cuda(ce);
+  cudaEventElapsedTime(&probe, e0, e1);
+  int reps = min_reps;
+  if (probe > 0.f) reps = (int)std::ceil(min_total_ms / probe);
+  reps = std::max(min_reps, std::min(max_reps, reps));
+  cudaEventRecord(e0, s);
+  for (int i = 0; i < reps; ++i)
+    if ((st = launch_config(id, a, s)) != GEMM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+  cudaEventRecord(e1, s);
+  if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) return fail_cuda(ce);
+  float total = 0.f;
+  cudaEventElapsedTime(&total, e0, e1);
+  *out_ms = (double)total / reps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return GEMM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ error check (FP64)
+namespace ks {
+constexpr int kErrThreads = 256;
+constexpr int kErrBlocksMax = 152 * 8;
+
+struct ErrArgs {
+  int64_t rows, cols, batch, n;
+  const float* C;
+  int64_t ldc, strideC;
+  const int64_t* pos;
+  const double* Cref;
+  const double* den;
+};
+
+__device__ __forceinline__ double err_term(double c, double ref, double d) {
+  const double diff = fabs(c - ref);
+  if (!(diff == diff) || isinf(diff)) return CUDART_INF;  // NaN or inf in C
+  if (d > 0.0) return diff / d;
+  return diff > 0.0 ? CUDART_INF : 0.0;
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kErrThreads) err_partial_kernel(const ErrArgs a, double* partials) {
+  __shared__ double sh[32];
+  const int64_t total = a.pos ? a.n : a.rows * a.cols * a.batch;
+  double m = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b, i, j;
+    if (a.pos) {
+      b = a.pos[3 * t]; i = a.pos[3 * t + 1]; j = a.pos[3 * t + 2];
+    } else {
+      const int64_t per = a.rows * a.cols;
+      b = t / per;
+      const int64_t r = t - b * per;
+      i = r / a.cols; j = r - i * a.cols;
+    }
+    const double c = (double)a.C[b * a.strideC + i * a.ldc + j];
+    m = fmax(m, err_term(c, a.Cref[t], a.den[t]));
+  }
+  m = block_max(m, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = m;
+}
+
+__global__ void __launch_bounds__(kErrThreads) err_final_kernel(const double* partials, int n, double* out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) m = fmax(m, partials[t]);
+  m = block_max(m, sh);
+  if (threadIdx.x == 0) *out = m;
+}
+
+static gemm_status_t err_validate(const ErrArgs& a) {
+  if (!a.C || !a.Cref || !a.den) return GEMM_ERR_INVALID_ARG;
+  if (a.pos) {
+    if (a.n < 0) return GEMM_ERR_INVALID_ARG;
+  } else if (a.rows < 0 || a.cols < 0 || a.batch < 0 || a.ldc < a.cols || a.strideC < a.ldc * a.rows) {
+    return GEMM_ERR_INVALID_ARG;
+  }
+  return GEMM_OK;
+}
+
+static int err_blocks(const ErrArgs& a) {
+  const int64_t total = a.pos ? a.n : a.rows * a.cols * a.batch;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kErrBlocksMax, (total + kErrThreads - 1) / kErrThreads));
+}
+
+// Runs the two reduction passes with `partials` (>= err_blocks doubles) and
+// `result` (one double) as device scratch, then copies the result to the host.
+static gemm_status_t err_run(const ErrArgs& a, double* partials, double* result, double* out, cudaStream_t s) {
+  const int nb = err_blocks(a);
+  err_partial_kernel<<<nb, kErrThreads, 0, s>>>(a, partials);
+  err_final_kernel<<<1, kErrThreads, 0, s>>>(partials, nb, result);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, result, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+  return GEMM_OK;
+}
+}  // namespace ks
+
+extern "C" gemm_status_t gemm_error_check(int64_t rows, int64_t cols, int64_t batch, const float* C, int64_t ldc,
+                                          int64_t strideC, int64_t n, const int64_t* pos, const double* Cref,
+                                          const double* den, double* out_err, void* stream) {
+  if (!out_err) return GEMM_ERR_INVALID_ARG;
+  ErrArgs a{rows, cols, batch, n, C, ldc, strideC, pos, Cref, den};
+  gemm_status_t st = err_validate(a);
+  if (st != GEMM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nb = err_blocks(a);
+  double* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), (nb + 1) * sizeof(double), s);
+  if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+  st = err_run(a, ws, ws + nb, out_err, s);
+  cudaFreeAsync(ws, s);
+  return st;
+}
+
+// ------------------------------------------------------------------ benchmark input fill
+namespace ks {
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {  // SplitMix64 finaliser (Steele et al. 2014)
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void fill_uniform_kernel(float* dst, int64_t rows, int64_t cols, int64_t ld, int64_t total,
+                                    uint64_t seed, float lo, float hi, float pad) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t % ld;
+    float v = pad;
+    if (c < cols) {
+      const uint64_t h = mix64(seed * 0xD1B54A32D192ED03ull + (uint64_t)t);
+      const float u = (float)(h >> 40) * (1.0f / 16777216.0f);
+      v = lo + (hi - lo) * u;
+    }
+    dst[t] = v;
+  }
+}
+}  // namespace ks
+
+extern "C" gemm_status_t kselect_fill_uniform(float* dst, int64_t rows, int64_t cols, int64_t ld, int64_t batch,
+                                              uint64_t seed, float lo, float hi, float pad, void* stream) {
+  if (rows < 0 || cols < 0 || batch < 0 || ld < cols) return GEMM_ERR_INVALID_ARG;
+  const int64_t total = rows * ld * batch;
+  if (total == 0) return GEMM_OK;
+  if (!dst) return GEMM_ERR_INVALID_ARG;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  fill_uniform_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(dst, rows, cols, ld, total, seed, lo,
+                                                                             hi, pad);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+  return GEMM_OK;
+}

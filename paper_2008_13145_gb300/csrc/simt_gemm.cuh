@@ -1,0 +1,417 @@
+// FP32 SIMT GEMM family: the paper's parameterised tiled matrix multiply
+// (Section 3) re-designed for sm_103a.
+//
+// Each thread owns a TM x TN register tile of C (the paper's R x C per work
+// item); a WX x WY thread block covers a (WY*TM) x (WX*TN) tile; the K loop
+// advances BK at a time.  Staged configs copy each BM x BK slice of op(A) and
+// BK x BN slice of op(B) into a double-buffered shared-memory ring with
+// coalesced 16-byte global loads (register prefetch of the next slice while the
+// current one is consumed).  Unstaged configs read their operands straight
+// from global memory with per-thread vector loads, as the paper's kernel does
+// (it uses no local memory).  Threads own columns in 4-wide chunks spaced
+// WX*4 apart (rows likewise), so shared-memory reads are conflict-free 16-byte
+// loads and C stores form contiguous runs; for TN < 4 a warp-shuffle
+// transpose regroups neighbouring threads' tiles into float4 stores.
+#pragma once
+#include <type_traits>
+#include <utility>
+
+#include "common.cuh"
+
+namespace ks {
+
+template <int TM_, int TN_, int WX_, int WY_, int BK_, bool STAGED_>
+struct SimtCfg {
+  static constexpr int TM = TM_, TN = TN_, WX = WX_, WY = WY_, BK = BK_;
+  static constexpr bool STAGED = STAGED_;
+  static constexpr int T = WX * WY;
+  static constexpr int BM = WY * TM;
+  static constexpr int BN = WX * TN;
+  static constexpr int CM = TM < 4 ? TM : 4;  // contiguous rows per chunk
+  static constexpr int CN = TN < 4 ? TN : 4;  // contiguous cols per chunk
+  static constexpr int PAD = 4;
+  static constexpr int LDS_A = BM + PAD;  // As[k][m]
+  static constexpr int LDS_B = BN + PAD;  // Bs[k][n]
+  static constexpr int STAGE_FLOATS = BK * (LDS_A + LDS_B);
+  static constexpr int SMEM_BYTES = STAGED ? 2 * STAGE_FLOATS * 4 : 0;
+  static constexpr int CHA = BM * BK / 4;  // 4-element chunks per slice
+  static constexpr int CHB = BN * BK / 4;
+  static constexpr int RA = (CHA + T - 1) / T;
+  static constexpr int RB = (CHB + T - 1) / T;
+  __device__ static constexpr int row(int i, int ty) { return (i / CM) * (WY * CM) + ty * CM + (i % CM); }
+  __device__ static constexpr int col(int j, int tx) { return (j / CN) * (WX * CN) + tx * CN + (j % CN); }
+};
+
+template <int W>
+struct VecT;
+template <>
+struct VecT<1> { using T = float; };
+template <>
+struct VecT<2> { using T = float2; };
+template <>
+struct VecT<4> { using T = float4; };
+
+template <int W>
+__device__ __forceinline__ void load_vec_smem(float* dst, const float* src) {
+  typename VecT<W>::T v = *reinterpret_cast<const typename VecT<W>::T*>(src);
+  if constexpr (W == 1) {
+    dst[0] = v;
+  } else if constexpr (W == 2) {
+    dst[0] = v.x; dst[1] = v.y;
+  } else {
+    dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
+  }
+}
+
+// Global load of W consecutive floats at src[0..W), element q valid when q < lim;
+// one vector load when `vec` and all W are valid.
+template <int W>
+__device__ __forceinline__ void load_vec_global(float* dst, const float* src, int lim, bool vec) {
+  if (vec && lim >= W) {
+    typename VecT<W>::T v = __ldg(reinterpret_cast<const typename VecT<W>::T*>(src));
+    if constexpr (W == 1) {
+      dst[0] = v;
+    } else if constexpr (W == 2) {
+      dst[0] = v.x; dst[1] = v.y;
+    } else {
+      dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < W; ++q) dst[q] = (q < lim) ? __ldg(src + q) : 0.f;
+  }
+}
+
+__device__ __forceinline__ float sel4(const float (&v)[4], int i) {
+  return i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
+}
+
+template <class Cfg>
+__device__ __forceinline__ void store_out(const GemmArgs& p, float* Cb, int gm, int gn, float v) {
+  if (gm < p.M && gn < p.N) {
+    float* dst = Cb + (int64_t)gm * p.ldc + gn;
+    float out = p.alpha * v;
+    if (p.beta != 0.f) out = fmaf(p.beta, *dst, out);
+    *dst = out;
+  }
+}
+
+// Four consecutive columns gn..gn+3 of row gm.
+template <class Cfg>
+__device__ __forceinline__ void store_out4(const GemmArgs& p, float* Cb, int gm, int gn, const float (&v)[4]) {
+  if (gm >= p.M) return;
+  float* dst = Cb + (int64_t)gm * p.ldc + gn;
+  if (p.vecC && gn + 3 < p.N) {
+    float4 o = make_float4(p.alpha * v[0], p.alpha * v[1], p.alpha * v[2], p.alpha * v[3]);
+    if (p.beta != 0.f) {
+      float4 c = *reinterpret_cast<const float4*>(dst);
+      o.x = fmaf(p.beta, c.x, o.x); o.y = fmaf(p.beta, c.y, o.y);
+      o.z = fmaf(p.beta, c.z, o.z); o.w = fmaf(p.beta, c.w, o.w);
+    }
+    *reinterpret_cast<float4*>(dst) = o;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) store_out<Cfg>(p, Cb, gm, gn + q, v[q]);
+  }
+}
+
+template <class Cfg>
+__device__ __forceinline__ void epilogue(const GemmArgs& p, float* Cb, int m0, int n0, int tx, int ty,
+                                         const float (&acc)[Cfg::TM][Cfg::TN]) {
+  constexpr int TM = Cfg::TM, TN = Cfg::TN, CN = Cfg::CN;
+  const int lane = threadIdx.x & 31;
+  if constexpr (CN == 4) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int jc = 0; jc < TN / 4; ++jc) {
+        float v[4] = {acc[i][jc * 4], acc[i][jc * 4 + 1], acc[i][jc * 4 + 2], acc[i][jc * 4 + 3]};
+        store_out4<Cfg>(p, Cb, m0 + Cfg::row(i, ty), n0 + Cfg::col(jc * 4, tx), v);
+      }
+  } else if constexpr (CN == 2 && TM >= 2) {
+    // Lane pairs (tx even/odd) hold columns 4g..4g+1 / 4g+2..4g+3 of the same
+    // rows; swap half of each 2x4 block so each lane owns one full row.
+    const int q = lane & 1;
+#pragma unroll
+    for (int i0 = 0; i0 < TM; i0 += 2) {
+      float s0 = q ? acc[i0][0] : acc[i0 + 1][0];
+      float s1 = q ? acc[i0][1] : acc[i0 + 1][1];
+      float r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+      float r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+      float v[4];
+      if (q == 0) {
+        v[0] = acc[i0][0]; v[1] = acc[i0][1]; v[2] = r0; v[3] = r1;
+      } else {
+        v[0] = r0; v[1] = r1; v[2] = acc[i0 + 1][0]; v[3] = acc[i0 + 1][1];
+      }
+      store_out4<Cfg>(p, Cb, m0 + Cfg::row(i0 + q, ty), n0 + (tx & ~1) * 2, v);
+    }
+  } else if constexpr (CN == 1 && TM >= 4) {
+    // Lane quads hold one column each of the same 4 rows: 4x4 transpose by
+    // butterfly shuffles so each lane owns one row of 4 columns.
+    const int q = lane & 3;
+#pragma unroll
+    for (int i0 = 0; i0 < TM; i0 += 4) {
+      float v[4] = {acc[i0][0], acc[i0 + 1][0], acc[i0 + 2][0], acc[i0 + 3][0]};
+      // w[c] = element (row q, column c) of the 4x4 block; lane c holds column c.
+      float w[4] = {q == 0 ? v[0] : 0.f, q == 1 ? v[1] : 0.f, q == 2 ? v[2] : 0.f, q == 3 ? v[3] : 0.f};
+#pragma unroll
+      for (int s = 1; s < 4; ++s) {
+        float r = __shfl_xor_sync(0xffffffffu, sel4(v, q ^ s), s);
+        const int dst = q ^ s;
+        w[0] = (dst == 0) ? r : w[0];
+        w[1] = (dst == 1) ? r : w[1];
+        w[2] = (dst == 2) ? r : w[2];
+        w[3] = (dst == 3) ? r : w[3];
+      }
+      store_out4<Cfg>(p, Cb, m0 + Cfg::row(i0 + q, ty), n0 + (tx & ~3), w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) store_out<Cfg>(p, Cb, m0 + Cfg::row(i, ty), n0 + Cfg::col(j, tx), acc[i][j]);
+  }
+}
+
+// ---------------------------------------------------------------- staged slice copy
+template <class Cfg>
+__device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArgs& p, const float* Ab,
+                                             int m0, int k0, int tid) {
+  constexpr int BK = Cfg::BK, BM = Cfg::BM;
+#pragma unroll
+  for (int u = 0; u < Cfg::RA; ++u) {
+    const int c = tid + u * Cfg::T;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c < Cfg::CHA) {
+      if (!p.transA) {  // stored M x K: chunk of 4 along k
+        const int m = c / (BK / 4), kq = (c % (BK / 4)) * 4;
+        const int gm = m0 + m, gk = k0 + kq;
+        if (gm < p.M) load_vec_global<4>(v, Ab + (int64_t)gm * p.lda + gk, p.K - gk, p.vecA);
+      } else {  // stored K x M: chunk of 4 along m
+        const int k = c / (BM / 4), mq = (c % (BM / 4)) * 4;
+        const int gk = k0 + k, gm = m0 + mq;
+        if (gk < p.K) load_vec_global<4>(v, Ab + (int64_t)gk * p.lda + gm, p.M - gm, p.vecA);
+      }
+    }
+    r[u] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+template <class Cfg>
+__device__ __forceinline__ void store_slice_a(const float4 (&r)[Cfg::RA], const GemmArgs& p, float* As, int tid) {
+  constexpr int BK = Cfg::BK, BM = Cfg::BM, L = Cfg::LDS_A;
+#pragma unroll
+  for (int u = 0; u < Cfg::RA; ++u) {
+    const int c = tid + u * Cfg::T;
+    if (c < Cfg::CHA) {
+      if (!p.transA) {
+        const int m = c / (BK / 4), kq = (c % (BK / 4)) * 4;
+        As[(kq + 0) * L + m] = r[u].x;
+        As[(kq + 1) * L + m] = r[u].y;
+        As[(kq + 2) * L + m] = r[u].z;
+        As[(kq + 3) * L + m] = r[u].w;
+      } else {
+        const int k = c / (BM / 4), mq = (c % (BM / 4)) * 4;
+        *reinterpret_cast<float4*>(As + k * L + mq) = r[u];
+      }
+    }
+  }
+}
+
+template <class Cfg>
+__device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArgs& p, const float* Bb,
+                                             int n0, int k0, int tid) {
+  constexpr int BK = Cfg::BK, BN = Cfg::BN;
+#pragma unroll
+  for (int u = 0; u < Cfg::RB; ++u) {
+    const int c = tid + u * Cfg::T;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (c < Cfg::CHB) {
+      if (!p.transB) {  // stored K x N: chunk along n
+        const int k = c / (BN / 4), nq = (c % (BN / 4)) * 4;
+        const int gk = k0 + k, gn = n0 + nq;
+        if (gk < p.K) load_vec_global<4>(v, Bb + (int64_t)gk * p.ldb + gn, p.N - gn, p.vecB);
+      } else {  // stored N x K: chunk along k
+        const int n = c / (BK / 4), kq = (c % (BK / 4)) * 4;
+        const int gn = n0 + n, gk = k0 + kq;
+        if (gn < p.N) load_vec_global<4>(v, Bb + (int64_t)gn * p.ldb + gk, p.K - gk, p.vecB);
+      }
+    }
+    r[u] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+template <class Cfg>
+__device__ __forceinline__ void store_slice_b(const float4 (&r)[Cfg::RB], const GemmArgs& p, float* Bs, int tid) {
+  constexpr int BK = Cfg::BK, BN = Cfg::BN, L = Cfg::LDS_B;
+#pragma unroll
+  for (int u = 0; u < Cfg::RB; ++u) {
+    const int c = tid + u * Cfg::T;
+    if (c < Cfg::CHB) {
+      if (!p.transB) {
+        const int k = c / (BN / 4), nq = (c % (BN / 4)) * 4;
+        *reinterpret_cast<float4*>(Bs + k * L + nq) = r[u];
+      } else {
+        const int n = c / (BK / 4), kq = (c % (BK / 4)) * 4;
+        Bs[(kq + 0) * L + n] = r[u].x;
+        Bs[(kq + 1) * L + n] = r[u].y;
+        Bs[(kq + 2) * L + n] = r[u].z;
+        Bs[(kq + 3) * L + n] = r[u].w;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- kernel
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
+  constexpr int TM = Cfg::TM, TN = Cfg::TN, BK = Cfg::BK, CM = Cfg::CM, CN = Cfg::CN;
+  const int tid = threadIdx.x;
+  const int tx = tid % Cfg::WX, ty = tid / Cfg::WX;
+  const int m0 = blockIdx.x * Cfg::BM, n0 = blockIdx.y * Cfg::BN;
+  const int b = blockIdx.z;
+  const float* Ab = static_cast<const float*>(p.A) + (int64_t)b * p.strideA;
+  const float* Bb = static_cast<const float*>(p.B) + (int64_t)b * p.strideB;
+  float* Cb = p.C + (int64_t)b * p.strideC;
+
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+
+  const int nk = (p.K + BK - 1) / BK;
+  if constexpr (Cfg::STAGED) {
+    extern __shared__ __align__(16) float smem[];
+    float4 ra[Cfg::RA], rb[Cfg::RB];
+    load_slice_a<Cfg>(ra, p, Ab, m0, 0, tid);
+    load_slice_b<Cfg>(rb, p, Bb, n0, 0, tid);
+    store_slice_a<Cfg>(ra, p, smem, tid);
+    store_slice_b<Cfg>(rb, p, smem + BK * Cfg::LDS_A, tid);
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+      const float* As = smem + (kt & 1) * Cfg::STAGE_FLOATS;
+      const float* Bs = As + BK * Cfg::LDS_A;
+      const bool more = kt + 1 < nk;
+      if (more) {
+        load_slice_a<Cfg>(ra, p, Ab, m0, (kt + 1) * BK, tid);
+        load_slice_b<Cfg>(rb, p, Bb, n0, (kt + 1) * BK, tid);
+      }
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        float a[TM], bv[TN];
+#pragma unroll
+        for (int ic = 0; ic < TM / CM; ++ic)
+          load_vec_smem<CM>(a + ic * CM, As + k * Cfg::LDS_A + ic * (Cfg::WY * CM) + ty * CM);
+#pragma unroll
+        for (int jc = 0; jc < TN / CN; ++jc)
+          load_vec_smem<CN>(bv + jc * CN, Bs + k * Cfg::LDS_B + jc * (Cfg::WX * CN) + tx * CN);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+      }
+      if (more) {
+        float* An = smem + ((kt + 1) & 1) * Cfg::STAGE_FLOATS;
+        store_slice_a<Cfg>(ra, p, An, tid);
+        store_slice_b<Cfg>(rb, p, An + BK * Cfg::LDS_A, tid);
+      }
+      __syncthreads();
+    }
+  } else {
+    // Direct: every thread reads its own rows of op(A) and columns of op(B).
+    for (int kt = 0; kt < nk; ++kt) {
+#pragma unroll
+      for (int kq = 0; kq < BK; kq += 4) {
+        const int gk = kt * BK + kq;
+        if (gk >= p.K) break;
+        const int klim = p.K - gk;
+        float a[TM][4], bv[4][TN];
+        if (!p.transA) {
+#pragma unroll
+          for (int i = 0; i < TM; ++i) {
+            const int gm = m0 + Cfg::row(i, ty);
+            if (gm < p.M) {
+              load_vec_global<4>(a[i], Ab + (int64_t)gm * p.lda + gk, klim, p.vecA);
+            } else {
+              a[i][0] = a[i][1] = a[i][2] = a[i][3] = 0.f;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int ic = 0; ic < TM / CM; ++ic) {
+              const int r0 = ic * (Cfg::WY * CM) + ty * CM;
+              float t[CM];
+              if (k < klim) {
+                load_vec_global<CM>(t, Ab + (int64_t)(gk + k) * p.lda + m0 + r0, p.M - m0 - r0, p.vecA);
+              } else {
+#pragma unroll
+                for (int q = 0; q < CM; ++q) t[q] = 0.f;
+              }
+#pragma unroll
+              for (int q = 0; q < CM; ++q) a[ic * CM + q][k] = t[q];
+            }
+        }
+        if (!p.transB) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int jc = 0; jc < TN / CN; ++jc) {
+              const int c0 = jc * (Cfg::WX * CN) + tx * CN;
+              float t[CN];
+              if (k < klim) {
+                load_vec_global<CN>(t, Bb + (int64_t)(gk + k) * p.ldb + n0 + c0, p.N - n0 - c0, p.vecB);
+              } else {
+#pragma unroll
+                for (int q = 0; q < CN; ++q) t[q] = 0.f;
+              }
+#pragma unroll
+              for (int q = 0; q < CN; ++q) bv[k][jc * CN + q] = t[q];
+            }
+        } else {
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            const int gn = n0 + Cfg::col(j, tx);
+            float t[4] = {0.f, 0.f, 0.f, 0.f};
+            if (gn < p.N) load_vec_global<4>(t, Bb + (int64_t)gn * p.ldb + gk, klim, p.vecB);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) bv[k][j] = t[k];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i][k], bv[k][j], acc[i][j]);
+      }
+    }
+  }
+  epilogue<Cfg>(p, Cb, m0, n0, tx, ty, acc);
+}
+
+template <int ID>
+cudaError_t launch_simt(const GemmArgs& a, cudaStream_t s) {
+  constexpr SimtParams P = simt_params(ID);
+  using Cfg = SimtCfg<P.tm, P.tn, P.wx, P.wy, P.bk, P.staged != 0>;
+  auto kern = simt_gemm_kernel<Cfg>;
+  if constexpr (Cfg::SMEM_BYTES > 48 * 1024) {
+    static unsigned long long done_mask = 0;  // devices whose attribute is set
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & bit)) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+      __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);
+    }
+  }
+  dim3 grid((a.M + Cfg::BM - 1) / Cfg::BM, (a.N + Cfg::BN - 1) / Cfg::BN, a.batch);
+  kern<<<grid, Cfg::T, Cfg::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ks

@@ -1,0 +1,29 @@
+// One shard of the FP32 SIMT instantiations.  This file is compiled
+// kSimtShards times with -DKS_SHARD=<i>; shard i instantiates the config ids
+// with id % kSimtShards == i, so the 576 kernels build in parallel.
+#include <utility>
+
+#include "simt_gemm.cuh"
+
+#ifndef KS_SHARD
+#error "compile with -DKS_SHARD=<shard index>"
+#endif
+
+namespace ks {
+namespace {
+template <int ID>
+void reg_one(LaunchFn* table) {
+  if constexpr (ID % kSimtShards == KS_SHARD) table[ID] = &launch_simt<ID>;
+}
+template <int... I>
+void reg_all(std::integer_sequence<int, I...>, LaunchFn* table) {
+  (reg_one<I>(table), ...);
+}
+}  // namespace
+
+#define KS_CAT2(a, b) a##b
+#define KS_CAT(a, b) KS_CAT2(a, b)
+void KS_CAT(simt_register_shard_, KS_SHARD)(LaunchFn* table) {
+  reg_all(std::make_integer_sequence<int, kSimtConfigs>{}, table);
+}
+}  // namespace ks

@@ -1,0 +1,216 @@
+"""ctypes binding of libkselect.so, entry point for entry point (argument marshalling only).
+
+Every function takes device buffers as torch tensors (or raw integer device
+pointers) and an optional stream (torch.cuda.Stream, raw handle, or None for
+torch's current stream).  A non-OK status raises ``KSelectError``.  Importing
+this module loads the compiled library and raises if it is missing: there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(f"libkselect.so is not built ({LIB}); run __graft_entry__.build() first")
+
+_lib = ctypes.CDLL(LIB)
+
+i32, i64, u64, f32, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float, ctypes.c_double
+vp, ch = ctypes.c_void_p, ctypes.c_char
+
+GEMM_OK = 0
+PREC_F32, PREC_TF32, PREC_BF16, PREC_F32X3 = 0, 1, 2, 3
+PRECISIONS = {"f32": PREC_F32, "tf32": PREC_TF32, "bf16": PREC_BF16, "f32x3": PREC_F32X3}
+MLP_PARAMS = 5192
+MAX_DEPLOYED = 16
+
+
+class TreeNode(ctypes.Structure):
+    _fields_ = [("feature", i32), ("left", i32), ("right", i32), ("label", i32), ("threshold", f64)]
+
+
+class Deployment(ctypes.Structure):
+    _fields_ = [("precision", i32), ("n_configs", i32), ("config_ids", ctypes.POINTER(i32)),
+                ("n_nodes", i32), ("nodes", ctypes.POINTER(TreeNode)), ("mlp_params", ctypes.POINTER(f32))]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("gemm_status_string", ctypes.c_char_p, [i32])
+_sig("gemm_last_cuda_error", i32, [])
+_sig("gemm_config_count", i32, [i32])
+_sig("gemm_config_id", i32, [i32, i32])
+_sig("gemm_config_params", i32, [i32, ctypes.POINTER(i32)])
+_sig("gemm_library_create", i32, [ctypes.POINTER(Deployment), ctypes.POINTER(vp)])
+_sig("gemm_library_destroy", None, [vp])
+_sig("select_kernel", i32, [vp, i64, i64, i64, i64])
+_GEMM_ARGS = [ch, ch, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i64, vp]
+_sig("gemm", i32, [vp] + _GEMM_ARGS)
+_sig("gemm_with_config", i32, [i32] + _GEMM_ARGS)
+_sig("gemm_benchmark", i32, [i32, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64, i64, i32, i32, i32, f64,
+                             ctypes.POINTER(f64), vp])
+_sig("gemm_error_check", i32, [i64, i64, i64, vp, i64, i64, i64, vp, vp, vp, ctypes.POINTER(f64), vp])
+_sig("kselect_fill_uniform", i32, [vp, i64, i64, i64, i64, u64, f32, f32, f32, vp])
+
+
+class KSelectError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.gemm_status_string(status).decode()
+        if status == -4:
+            msg += f" (cudaError {_lib.gemm_last_cuda_error()})"
+        super().__init__(f"{where}: {msg} [{status}]")
+
+
+def check(status: int, where: str) -> None:
+    if status != GEMM_OK:
+        raise KSelectError(status, where)
+
+
+def ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _c(t: str) -> bytes:
+    return t.encode() if isinstance(t, str) else t
+
+
+# ---------------------------------------------------------------- config space
+def config_count(precision: int) -> int:
+    n = _lib.gemm_config_count(precision)
+    if n < 0:
+        raise KSelectError(n, "gemm_config_count")
+    return n
+
+
+def config_id(precision: int, index: int) -> int:
+    r = _lib.gemm_config_id(precision, index)
+    if r < 0:
+        raise KSelectError(r, "gemm_config_id")
+    return r
+
+
+def config_ids(precision: int) -> list[int]:
+    return [config_id(precision, i) for i in range(config_count(precision))]
+
+
+def config_params(cid: int) -> list[int]:
+    out = (i32 * 8)()
+    check(_lib.gemm_config_params(cid, out), "gemm_config_params")
+    return list(out)
+
+
+# ---------------------------------------------------------------- handle
+class Handle:
+    """An immutable library handle built from a deployment dict:
+    {"precision": int, "config_ids": [...], "nodes": [{"feature", "threshold",
+    "left", "right", "label"}, ...], "mlp_params": [5192 floats] | None}."""
+
+    def __init__(self, deployment: dict):
+        ids = list(deployment["config_ids"])
+        nodes = deployment.get("nodes") or []
+        mlp = deployment.get("mlp_params")
+        self._ids = (i32 * max(len(ids), 1))(*ids)
+        self._nodes = (TreeNode * max(len(nodes), 1))(
+            *[TreeNode(int(n["feature"]), int(n["left"]), int(n["right"]), int(n["label"]),
+                       float(n["threshold"])) for n in nodes])
+        self._mlp = (f32 * MLP_PARAMS)(*np.asarray(mlp, np.float32)) if mlp is not None else None
+        d = Deployment(int(deployment["precision"]), len(ids), self._ids, len(nodes), self._nodes,
+                       self._mlp if self._mlp is not None else None)
+        h = vp()
+        check(_lib.gemm_library_create(ctypes.byref(d), ctypes.byref(h)), "gemm_library_create")
+        self.value = h.value
+        self.precision = int(deployment["precision"])
+        self.ids = ids
+
+    def close(self):
+        if self.value:
+            _lib.gemm_library_destroy(self.value)
+            self.value = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def select_kernel(handle: Handle, M: int, N: int, K: int, batch: int = 1) -> int:
+    r = _lib.select_kernel(handle.value, M, N, K, batch)
+    if r < 0:
+        raise KSelectError(r, "select_kernel")
+    return r
+
+
+# ---------------------------------------------------------------- GEMM
+def gemm(handle: Handle, transA: str, transB: str, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch=1,
+         stream=None) -> None:
+    check(_lib.gemm(handle.value, _c(transA), _c(transB), M, N, K, alpha, ptr(A), lda, ptr(B), ldb, beta,
+                    ptr(C), ldc, batch, stream_handle(stream)), "gemm")
+
+
+def gemm_with_config(cid: int, transA: str, transB: str, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch=1,
+                     stream=None) -> None:
+    check(_lib.gemm_with_config(cid, _c(transA), _c(transB), M, N, K, alpha, ptr(A), lda, ptr(B), ldb, beta,
+                                ptr(C), ldc, batch, stream_handle(stream)), "gemm_with_config")
+
+
+def gemm_status(cid: int, transA: str, transB: str, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch=1,
+                stream=None) -> int:
+    """gemm_with_config returning the raw status instead of raising."""
+    return _lib.gemm_with_config(cid, _c(transA), _c(transB), M, N, K, alpha, ptr(A), lda, ptr(B), ldb, beta,
+                                 ptr(C), ldc, batch, stream_handle(stream))
+
+
+def gemm_benchmark(cid: int, transA: str, transB: str, M, N, K, A, lda, B, ldb, C, ldc, batch=1, warmup=2,
+                   min_reps=3, max_reps=50, min_total_ms=2.0, stream=None) -> tuple[int, float]:
+    """(status, mean ms per launch); a non-OK status is returned, not raised, so
+    that a sweep can record configs that cannot run as failed."""
+    out = f64()
+    st = _lib.gemm_benchmark(cid, _c(transA), _c(transB), M, N, K, ptr(A), lda, ptr(B), ldb, ptr(C), ldc, batch,
+                             warmup, min_reps, max_reps, min_total_ms, ctypes.byref(out), stream_handle(stream))
+    return st, out.value
+
+
+def error_check(C, Cref, den, rows=0, cols=0, batch=0, ldc=0, strideC=0, pos=None, stream=None) -> float:
+    """Max |C - Cref| / den on the GPU in FP64 (full mode, or sampled when ``pos`` is given)."""
+    out = f64()
+    n = 0 if pos is None else pos.shape[0]
+    check(_lib.gemm_error_check(rows, cols, batch, ptr(C), ldc, strideC, n, ptr(pos), ptr(Cref), ptr(den),
+                                ctypes.byref(out), stream_handle(stream)), "gemm_error_check")
+    return out.value
+
+
+def fill_uniform(dst, rows, cols, ld, batch, seed, lo=-1.0, hi=1.0, pad=0.0, stream=None) -> None:
+    check(_lib.kselect_fill_uniform(ptr(dst), rows, cols, ld, batch, seed, lo, hi, pad, stream_handle(stream)),
+          "kselect_fill_uniform")
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C-ABI entry points this binding expects."""
+    return ["gemm_status_string", "gemm_last_cuda_error", "gemm_config_count", "gemm_config_id",
+            "gemm_config_params", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
+            "gemm_with_config", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform"]

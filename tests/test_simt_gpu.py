@@ -1,0 +1,213 @@
+"""GPU parity of the FP32 SIMT family against the FP64 oracle, through the C-ABI.
+
+Tolerance: max |C - C_ref| / (|alpha||A||B| + |beta||C0|) <= 1e-5 for FP32.
+Every output buffer is surrounded by sentinel guard regions (before, after and
+in the ldc padding) that must survive each launch; beta = 0 launches start
+from NaN-filled C, so reading C when beta == 0 shows up as NaN."""
+import numpy as np
+import pytest
+
+from oracle import gemm as og
+from paper_2008_13145_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+TOL_F32 = 1e-5
+SENTINEL = 7777.0
+GUARD = 64
+TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
+
+
+class Out:
+    """C buffer (batch, M, ldc) inside a flat tensor with guard regions."""
+
+    def __init__(self, torch, C0, beta, N):
+        self.batch, self.M, self.ldc = C0.shape
+        flat = np.full(GUARD + C0.size + GUARD, SENTINEL, np.float32)
+        body = C0.copy()
+        if beta == 0:
+            body[:, :, :N] = np.nan
+        flat[GUARD:GUARD + C0.size] = body.ravel()
+        self.flat = torch.from_numpy(flat).cuda()
+        self.ptr = self.flat.data_ptr() + 4 * GUARD
+
+    def result(self, N):
+        f = self.flat.cpu().numpy()
+        assert np.all(f[:GUARD] == SENTINEL) and np.all(f[GUARD + self.batch * self.M * self.ldc:] == SENTINEL)
+        body = f[GUARD:GUARD + self.batch * self.M * self.ldc].reshape(self.batch, self.M, self.ldc)
+        assert np.all(body[:, :, N:] == SENTINEL), "write into ldc padding"
+        return body[:, :, :N]
+
+
+def pad_c(C0, ldc_extra=3):
+    b, M, ldc = C0.shape
+    out = np.full((b, M, ldc + ldc_extra), SENTINEL, np.float32)
+    out[:, :, :ldc] = C0
+    out[:, :, C0.shape[2]:] = SENTINEL
+    return out
+
+
+def run_case(ks, torch, cid, shape, alpha, beta, A, B, C0, N_valid=None):
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C0p = C0.copy()
+    C0p[:, :, shape.N:] = SENTINEL
+    out = Out(torch, C0p, beta, shape.N)
+    ks.gemm_with_config(cid, shape.transA, shape.transB, shape.M, shape.N, shape.K, alpha, tA, A.shape[2], tB,
+                        B.shape[2], beta, out.ptr, C0p.shape[2], shape.batch)
+    torch.cuda.synchronize()
+    return out.result(shape.N)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def find_cfg(ks, tm, tn, wx, wy, bk, staged):
+    return next(c for c in ks.config_ids(ks.PREC_F32) if ks.config_params(c)[1:7] == [tm, tn, wx, wy, bk, staged])
+
+
+def test_single_gemm_256(lib, torch):
+    """256^3 NN, alpha 1, beta 0, uniform[-1,1] seed 0; 16x16 threads, 4x4 per thread, K-step 16, staged."""
+    ks = lib
+    shape = wl.Shape(256, 256, 256, 1, "N", "N")
+    A, B, C0 = wl.gemm_inputs(shape, seed=0)
+    cid = find_cfg(ks, 4, 4, 16, 16, 16, 1)
+    C = run_case(ks, torch, cid, shape, 1.0, 0.0, A, B, C0)
+    ref, den = og.gemm("N", "N", 256, 256, 256, 1.0, A, B)
+    err = og.error_ratio(C, ref, den)
+    assert err <= TOL_F32, err
+    tC = torch.from_numpy(np.ascontiguousarray(C)).cuda()
+    gerr = ks.error_check(tC, torch.from_numpy(ref).cuda(), torch.from_numpy(den).cuda(), rows=256, cols=256,
+                          batch=1, ldc=256, strideC=256 * 256)
+    assert gerr == pytest.approx(err, rel=1e-12, abs=0)
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+def test_every_config_ragged(lib, torch, ta, tb):
+    """All 576 configs on a ragged batched shape, alpha -0.5, beta 0.25, NaN padding in A and B."""
+    ks = lib
+    shape = wl.Shape(37, 45, 29, 2, ta, tb)
+    A, B, C0 = wl.gemm_inputs(shape, seed=11, beta_nonzero=True, ld_multiple=8)
+    ref, den = og.gemm(ta, tb, shape.M, shape.N, shape.K, -0.5, A, B, 0.25, C0)
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C0p = C0.copy()
+    C0p[:, :, shape.N:] = SENTINEL
+    bad = []
+    for cid in ks.config_ids(ks.PREC_F32):
+        out = Out(torch, C0p, 0.25, shape.N)
+        ks.gemm_with_config(cid, ta, tb, shape.M, shape.N, shape.K, -0.5, tA, A.shape[2], tB, B.shape[2], 0.25,
+                            out.ptr, C0p.shape[2], shape.batch)
+        err = og.error_ratio(out.result(shape.N), ref, den)
+        if not err <= TOL_F32:
+            bad.append((cid, ks.config_params(cid), err))
+    assert not bad, bad[:10]
+
+
+def test_beta_zero_does_not_read_c(lib, torch):
+    ks = lib
+    shape = wl.Shape(50, 33, 40, 3, "T", "N")
+    A, B, C0 = wl.gemm_inputs(shape, seed=12)
+    ref, den = og.gemm("T", "N", shape.M, shape.N, shape.K, 2.0, A, B)
+    for cid in range(0, 576, 5):
+        C = run_case(ks, torch, cid, shape, 2.0, 0.0, A, B, C0)
+        assert og.error_ratio(C, ref, den) <= TOL_F32, cid
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+def test_integer_inputs_exact(lib, torch, ta, tb):
+    """|a|,|b| <= 8 with K <= 4096 keeps every partial sum an integer below 2^24: exact in FP32."""
+    ks = lib
+    shape = wl.Shape(70, 66, 300, 2, ta, tb)
+    A, B, C0 = wl.gemm_inputs(shape, seed=13, kind="integer", bound=8, beta_nonzero=True)
+    ref, _ = og.gemm(ta, tb, shape.M, shape.N, shape.K, 1.0, A, B, 1.0, C0)
+    for cid in range(3, 576, 11):
+        C = run_case(ks, torch, cid, shape, 1.0, 1.0, A, B, C0)
+        assert np.array_equal(C.astype(np.float64), ref), cid
+
+
+def test_several_tiles_with_tails(lib, torch):
+    ks = lib
+    shape = wl.Shape(300, 290, 77, 1, "N", "N")
+    A, B, C0 = wl.gemm_inputs(shape, seed=14, beta_nonzero=True)
+    ref, den = og.gemm("N", "N", shape.M, shape.N, shape.K, 1.0, A, B, -1.0, C0)
+    big = [c for c in ks.config_ids(ks.PREC_F32) if ks.config_params(c)[1] * ks.config_params(c)[4] >= 64]
+    for cid in big[::3]:
+        C = run_case(ks, torch, cid, shape, 1.0, -1.0, A, B, C0)
+        assert og.error_ratio(C, ref, den) <= TOL_F32, cid
+
+
+def test_degenerate_sizes(lib, torch):
+    ks = lib
+    for (M, N, K) in [(1, 1, 1), (1, 300, 5), (300, 1, 5), (2, 3, 1), (5, 7, 4099)]:
+        shape = wl.Shape(M, N, K, 2, "N", "T")
+        A, B, C0 = wl.gemm_inputs(shape, seed=15, beta_nonzero=True)
+        ref, den = og.gemm("N", "T", M, N, K, 1.0, A, B, 0.5, C0)
+        for cid in (0, 101, 287, 431, 575):
+            C = run_case(ks, torch, cid, shape, 1.0, 0.5, A, B, C0)
+            assert og.error_ratio(C, ref, den) <= TOL_F32, (M, N, K, cid)
+    # K == 0: C = beta * C
+    shape = wl.Shape(9, 10, 0, 1, "N", "N")
+    C0 = wl.uniform_matrix(9, 12, 12, 1, 3, 3)
+    out = Out(torch, pad_c(C0[:, :, :12], 0), 0.5, 10)
+    ks.gemm_with_config(7, "N", "N", 9, 10, 0, 1.0, 0, 1, 0, 1, 0.5, out.ptr, 12, 1)
+    torch.cuda.synchronize()
+    f = out.flat.cpu().numpy()[GUARD:GUARD + 9 * 12].reshape(9, 12)
+    assert np.array_equal(f[:, :10], np.float32(0.5) * C0[0, :, :10])
+
+
+def test_unaligned_operands_use_scalar_path(lib, torch):
+    """Pointers 4 bytes past a 16-byte boundary and odd leading dimensions."""
+    ks = lib
+    M, N, K = 45, 39, 51
+    rng = np.random.default_rng(16)
+    A = rng.uniform(-1, 1, (M, K + 1)).astype(np.float32)
+    B = rng.uniform(-1, 1, (K, N + 2)).astype(np.float32)
+    ref, den = og.gemm("N", "N", M, N, K, 1.0, A[None], B[None])
+    fa = torch.from_numpy(np.concatenate([[0.0], A.ravel()]).astype(np.float32)).cuda()
+    fb = torch.from_numpy(np.concatenate([[0.0], B.ravel()]).astype(np.float32)).cuda()
+    for cid in (1, 143, 289, 575):
+        C = torch.full((M * (N + 1) + 1,), float("nan"), device="cuda")
+        ks.gemm_with_config(cid, "N", "N", M, N, K, 1.0, fa.data_ptr() + 4, K + 1, fb.data_ptr() + 4, N + 2, 0.0,
+                            C.data_ptr() + 4, N + 1, 1)
+        torch.cuda.synchronize()
+        got = C.cpu().numpy().ravel()[1:1 + M * (N + 1)].reshape(M, N + 1)[:, :N]
+        assert og.error_ratio(got[None], ref, den) <= TOL_F32, cid
+
+
+def test_full_size_sampled(lib, torch):
+    """Largest grid-size shape in the staged 8x8-per-thread config, checked on sampled entries by the GPU reduction."""
+    ks = lib
+    shape = wl.Shape(4096, 3000, 4096, 2, "T", "N")
+    A, B, _ = wl.gemm_inputs(shape, seed=17)
+    cid = find_cfg(ks, 8, 8, 16, 16, 8, 1)
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = torch.empty((2, 4096, 3000), device="cuda")
+    ks.gemm_with_config(cid, "T", "N", 4096, 3000, 4096, 1.0, tA, A.shape[2], tB, B.shape[2], 0.0, C, 3000, 2)
+    pos = wl.sample_positions(shape, 8, 8, seed=3)
+    ref, den = og.gemm_entries("T", "N", 4096, 3000, 4096, 1.0, A, B, 0.0, None, pos, nthreads=og.max_threads())
+    gerr = ks.error_check(C, torch.from_numpy(ref).cuda(), torch.from_numpy(den).cuda(), pos=torch.from_numpy(pos).cuda(),
+                          ldc=3000, strideC=4096 * 3000)
+    host = og.error_ratio(C.cpu().numpy()[pos[:, 0], pos[:, 1], pos[:, 2]], ref, den)
+    assert gerr <= TOL_F32 and gerr == pytest.approx(host, rel=1e-12)
+
+
+def test_error_check_kernel_semantics(lib, torch):
+    ks = lib
+    rng = np.random.default_rng(18)
+    C = rng.standard_normal((3, 20, 24)).astype(np.float32)
+    ref = C.astype(np.float64)[:, :, :21] + rng.standard_normal((3, 20, 21)) * 1e-6
+    den = np.abs(rng.standard_normal((3, 20, 21))) + 0.1
+    tC = torch.from_numpy(C).cuda()
+    e = ks.error_check(tC, torch.from_numpy(ref).cuda(), torch.from_numpy(den).cuda(), rows=20, cols=21, batch=3,
+                       ldc=24, strideC=480)
+    assert e == pytest.approx(og.error_ratio(C[:, :, :21], ref, den), rel=1e-14)
+    den[1, 2, 3] = 0.0
+    ref[1, 2, 3] = C[1, 2, 3]
+    e = ks.error_check(tC, torch.from_numpy(ref).cuda(), torch.from_numpy(den).cuda(), rows=20, cols=21, batch=3,
+                       ldc=24, strideC=480)
+    assert np.isfinite(e)
+    ref[1, 2, 3] += 1e-3
+    e = ks.error_check(tC, torch.from_numpy(ref).cuda(), torch.from_numpy(den).cuda(), rows=20, cols=21, batch=3,
+                       ldc=24, strideC=480)
+    assert e == float("inf")
