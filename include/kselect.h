@@ -149,6 +149,77 @@ gemm_status_t gemm_benchmark(int32_t config_id, char transA, char transB, int64_
                              int32_t warmup, int32_t min_reps, int32_t max_reps,
                              double min_total_ms, double* out_ms, void* stream);
 
+/* Section 3.1, over a configuration list on one set of sizes.  Pass 1 times
+ * one warm launch of every config (a launch longer than 2 ms is its own
+ * warm-up; shorter ones are re-timed after `warmup` more launches).  Pass 2
+ * re-times, as a back-to-back run sized like gemm_benchmark's, every config
+ * whose pass-1 time is <= refine_ratio x the fastest; the others keep their
+ * pass-1 time.  out_ms[c] is the time per launch (0 when out_status[c] != 0;
+ * configs that cannot run this request report their status and are skipped).
+ * Stops at the first GEMM_ERR_CUDA, which it returns.  Synchronises `stream`. */
+gemm_status_t gemm_benchmark_configs(int32_t n_configs, const int32_t* config_ids, char transA, char transB,
+                                     int64_t M, int64_t N, int64_t K, const void* A_dev, int64_t lda,
+                                     const void* B_dev, int64_t ldb, float* C_dev, int64_t ldc, int64_t batch,
+                                     int32_t warmup, int32_t min_reps, int32_t max_reps, double min_total_ms,
+                                     double refine_ratio, double* out_ms, int32_t* out_status, void* stream);
+
+/* ---------------------------------------------------------------- pruning pipeline (Sections 3.4, 4)
+ * Section 3.4: per row of an n_rows x n_cols throughput table (row-major,
+ * FP32, device), x = perf / max(row) (0 for a row of zeros), then
+ * mode 0 standard: x; 1 raw cutoff: 0 where x < 0.9; 2 standard cutoff:
+ * 0 where x < 0.9, else (x - 0.9) / 0.1; 3 sigmoid: 1 / (1 + exp(50 (0.85 - x))).
+ * out_dev may alias perf_dev. */
+gemm_status_t kselect_normalise(int64_t n_rows, int32_t n_cols, const float* perf_dev, float* out_dev,
+                                int32_t mode, void* stream);
+
+/* Section 4.1: k-means over the n rows (points in R^d, FP32, device) of X.
+ * n_init seeded runs, one thread block each: k-means++ seeding driven by the
+ * host array draws (n_init x k uint32; centre 0 is point (draw * n) >> 32,
+ * centre c picks the first point whose running sum of squared distances to
+ * the nearest chosen centre exceeds draw / 2^32 times the total), then
+ * Lloyd's iterations (nearest centre, lowest index on ties; each centre to
+ * the mean of its points, an empty cluster keeps its centre) until the
+ * total squared centre shift is <= tol x mean per-dimension variance of X,
+ * or max_iter.  The run of lowest inertia (first on ties) is written:
+ * centres_out_dev (k x d), labels_out_dev (n), *inertia_out, *iters_out.
+ * Allocates its scratch stream-ordered; synchronises `stream`. */
+gemm_status_t kselect_kmeans(int32_t n, int32_t d, int32_t k, int32_t n_init, const float* X_dev,
+                             const uint32_t* draws, int32_t max_iter, float tol, float* centres_out_dev,
+                             int32_t* labels_out_dev, double* inertia_out, int32_t* iters_out, void* stream);
+
+/* Section 4.3: over the rows of a throughput table (device), ratio =
+ * perf[r, pick] / max(row) with pick = chosen_dev[r] (a classifier's column,
+ * device int32) when chosen_dev is not NULL, else the best of the host list
+ * deployed_cols (the deployed set's attainable maximum), else every column.
+ * out[0] = geometric mean of max(ratio, floor), out[1] = arithmetic mean,
+ * out[2] = number of ratios below floor.  Synchronises `stream`. */
+gemm_status_t kselect_score(int32_t n_rows, int32_t n_cols, const float* perf_dev, int32_t n_deployed,
+                            const int32_t* deployed_cols, const int32_t* chosen_dev, float floor_, double out[3],
+                            void* stream);
+
+/* Section 4.2 (host): the best column of each of k centres (k x d, host),
+ * clusters in descending size from labels (n, host; lower index first on
+ * ties).  With dedupe a cluster whose best is taken gets its best unused
+ * column, without it the cluster is dropped.  Writes out_cols and *out_count. */
+gemm_status_t kselect_representatives(int32_t k, int32_t d, const float* centres, int32_t n, const int32_t* labels,
+                                      int32_t dedupe, int32_t* out_cols, int32_t* out_count);
+
+/* Section 4.2 Top-N baseline (host): the n columns that are a row's best most
+ * often (lowest index on ties), filled up by highest mean normalised value. */
+gemm_status_t kselect_top_n(int32_t n_rows, int32_t n_cols, const float* perf, int32_t n, int32_t* out_cols);
+
+/* Section 5.1 (host): CART classification tree on features (n x 4 doubles:
+ * M, N, K, batch) and labels (n, in [0, n_classes)).  Gini impurity with the
+ * class sum in class order; thresholds at midpoints of consecutive distinct
+ * values; features in order, thresholds ascending, first best split kept; a
+ * node is a leaf when pure, at max_depth (< 0: unlimited) or without a split
+ * leaving >= min_leaf samples on each side; leaf label = majority, lowest
+ * class on ties.  Nodes in depth-first preorder; UNSUPPORTED when more than
+ * max_nodes are needed. */
+gemm_status_t kselect_tree_train(int32_t n, const double* features, const int32_t* labels, int32_t n_classes,
+                                 int32_t max_depth, int32_t min_leaf, gemm_tree_node_t* out_nodes,
+                                 int32_t max_nodes, int32_t* out_n_nodes);
+
 /* ---------------------------------------------------------------- error check
  * The judge of every GEMM result: err = max over entries of
  * |C - C_ref| / den, reduced on the GPU in FP64, where C_ref and den are the

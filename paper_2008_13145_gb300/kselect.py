@@ -61,6 +61,17 @@ _sig("gemm_benchmark", i32, [i32, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i
                              ctypes.POINTER(f64), vp])
 _sig("gemm_error_check", i32, [i64, i64, i64, vp, i64, i64, i64, vp, vp, vp, ctypes.POINTER(f64), vp])
 _sig("kselect_fill_uniform", i32, [vp, i64, i64, i64, i64, u64, f32, f32, f32, vp])
+_sig("gemm_benchmark_configs", i32, [i32, ctypes.POINTER(i32), ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64,
+                                     i64, i32, i32, i32, f64, f64, ctypes.POINTER(f64), ctypes.POINTER(i32), vp])
+_sig("kselect_normalise", i32, [i64, i32, vp, vp, i32, vp])
+_sig("kselect_kmeans", i32, [i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_uint32), i32, f32, vp, vp,
+                             ctypes.POINTER(f64), ctypes.POINTER(i32), vp])
+_sig("kselect_score", i32, [i32, i32, vp, i32, ctypes.POINTER(i32), vp, f32, ctypes.POINTER(f64), vp])
+_sig("kselect_representatives", i32, [i32, i32, ctypes.POINTER(f32), i32, ctypes.POINTER(i32), i32,
+                                      ctypes.POINTER(i32), ctypes.POINTER(i32)])
+_sig("kselect_top_n", i32, [i32, i32, ctypes.POINTER(f32), i32, ctypes.POINTER(i32)])
+_sig("kselect_tree_train", i32, [i32, ctypes.POINTER(f64), ctypes.POINTER(i32), i32, i32, i32,
+                                 ctypes.POINTER(TreeNode), i32, ctypes.POINTER(i32)])
 
 
 class KSelectError(RuntimeError):
@@ -209,8 +220,88 @@ def fill_uniform(dst, rows, cols, ld, batch, seed, lo=-1.0, hi=1.0, pad=0.0, str
           "kselect_fill_uniform")
 
 
+def _arr(a, dtype, ctype):
+    a = np.ascontiguousarray(a, dtype)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def benchmark_configs(cids, transA, transB, M, N, K, A, lda, B, ldb, C, ldc, batch=1, warmup=1, min_reps=2,
+                      max_reps=50, min_total_ms=2.0, refine_ratio=2.0, stream=None):
+    """Section 3.1 over a config list: (ms per launch, status) arrays."""
+    ids, pids = _arr(cids, np.int32, i32)
+    ms = np.zeros(len(ids), np.float64)
+    st = np.zeros(len(ids), np.int32)
+    check(_lib.gemm_benchmark_configs(len(ids), pids, _c(transA), _c(transB), M, N, K, ptr(A), lda, ptr(B), ldb,
+                                      ptr(C), ldc, batch, warmup, min_reps, max_reps, min_total_ms, refine_ratio,
+                                      ms.ctypes.data_as(ctypes.POINTER(f64)), st.ctypes.data_as(ctypes.POINTER(i32)),
+                                      stream_handle(stream)), "gemm_benchmark_configs")
+    return ms, st
+
+
+NORM_MODES = {"standard": 0, "raw_cutoff": 1, "standard_cutoff": 2, "sigmoid": 3}
+
+
+def normalise(perf, out, mode="standard", stream=None) -> None:
+    n_rows, n_cols = perf.shape
+    check(_lib.kselect_normalise(n_rows, n_cols, ptr(perf), ptr(out), NORM_MODES[mode], stream_handle(stream)),
+          "kselect_normalise")
+
+
+def kmeans(X, k: int, draws: np.ndarray, centres_out, labels_out, max_iter=300, tol=1e-4, stream=None):
+    """Returns (inertia, iterations); draws is (n_init, k) uint32."""
+    n, d = X.shape
+    dr, pdr = _arr(draws, np.uint32, ctypes.c_uint32)
+    inertia, iters = f64(), i32()
+    check(_lib.kselect_kmeans(n, d, k, dr.shape[0], ptr(X), pdr, max_iter, tol, ptr(centres_out), ptr(labels_out),
+                              ctypes.byref(inertia), ctypes.byref(iters), stream_handle(stream)), "kselect_kmeans")
+    return inertia.value, iters.value
+
+
+def score(perf, deployed_cols=None, chosen=None, floor=1e-6, stream=None) -> dict:
+    n_rows, n_cols = perf.shape
+    dep = list(deployed_cols) if deployed_cols is not None else []
+    d, pd = _arr(dep if dep else [0], np.int32, i32)
+    out = (f64 * 3)()
+    check(_lib.kselect_score(n_rows, n_cols, ptr(perf), len(dep), pd, ptr(chosen), floor, out,
+                             stream_handle(stream)), "kselect_score")
+    return {"geomean": out[0], "mean": out[1], "clamped": int(out[2])}
+
+
+def representatives(centres: np.ndarray, labels: np.ndarray, dedupe=True) -> np.ndarray:
+    k, d = centres.shape
+    c, pc = _arr(centres, np.float32, f32)
+    lab, pl = _arr(labels, np.int32, i32)
+    out = np.zeros(k, np.int32)
+    cnt = i32()
+    check(_lib.kselect_representatives(k, d, pc, len(lab), pl, int(dedupe), out.ctypes.data_as(ctypes.POINTER(i32)),
+                                       ctypes.byref(cnt)), "kselect_representatives")
+    return out[:cnt.value].copy()
+
+
+def top_n(perf: np.ndarray, n: int) -> np.ndarray:
+    p, pp = _arr(perf, np.float32, f32)
+    out = np.zeros(n, np.int32)
+    check(_lib.kselect_top_n(p.shape[0], p.shape[1], pp, n, out.ctypes.data_as(ctypes.POINTER(i32))), "kselect_top_n")
+    return out
+
+
+def tree_train(features: np.ndarray, labels: np.ndarray, n_classes: int, max_depth=None, min_leaf=1,
+               max_nodes=8192) -> list[dict]:
+    F, pF = _arr(features, np.float64, f64)
+    assert F.ndim == 2 and F.shape[1] == 4
+    y, py = _arr(labels, np.int32, i32)
+    nodes = (TreeNode * max_nodes)()
+    cnt = i32()
+    check(_lib.kselect_tree_train(F.shape[0], pF, py, n_classes, -1 if max_depth is None else max_depth, min_leaf,
+                                  nodes, max_nodes, ctypes.byref(cnt)), "kselect_tree_train")
+    return [{"feature": nodes[j].feature, "threshold": nodes[j].threshold, "left": nodes[j].left,
+             "right": nodes[j].right, "label": nodes[j].label} for j in range(cnt.value)]
+
+
 def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points this binding expects."""
     return ["gemm_status_string", "gemm_last_cuda_error", "gemm_config_count", "gemm_config_id",
             "gemm_config_params", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
-            "gemm_with_config", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform"]
+            "gemm_with_config", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
+            "gemm_benchmark_configs", "kselect_normalise", "kselect_kmeans", "kselect_score",
+            "kselect_representatives", "kselect_top_n", "kselect_tree_train"]

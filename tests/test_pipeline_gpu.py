@@ -1,0 +1,87 @@
+"""GPU parity of the pruning pipeline kernels against the FP64 oracle.
+
+Normalisation and scores are FP32 on the GPU: relative tolerance 1e-6 (a few
+FP32 ulps through one division and, for the sigmoid, one exp).  k-means runs
+in FP32 with the same seeding draws as the oracle: on separated clusters the
+labels must agree exactly and the inertia to 1e-4 relative (FP32 sums of
+~10^4 squared distances)."""
+import numpy as np
+import pytest
+
+from oracle import select as osel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.mark.parametrize("mode", osel.NORMALISATIONS)
+def test_normalise(lib, torch, mode):
+    rng = np.random.default_rng(1)
+    perf = (rng.random((333, 576)) ** 4 * 50).astype(np.float32)
+    perf[5] = 0.0
+    perf[7, :10] = 0.0
+    out = torch.empty(perf.shape, device="cuda")
+    lib.normalise(torch.from_numpy(perf).cuda(), out, mode)
+    got = out.cpu().numpy().astype(np.float64)
+    want = osel.normalise(perf.astype(np.float64), mode)
+    assert np.allclose(got, want, rtol=1e-6, atol=1e-6)
+    assert np.all(got[5] == want[5])
+
+
+def planted(n_per, k, d, spread, seed):
+    rng = np.random.default_rng(seed)
+    centres = rng.random((k, d))
+    X = np.concatenate([c + spread * rng.standard_normal((n_per, d)) for c in centres])
+    return X.astype(np.float32)
+
+
+@pytest.mark.parametrize("k,d,seed", [(3, 5, 0), (4, 64, 1), (8, 576, 2), (15, 200, 3)])
+def test_kmeans_matches_oracle(lib, torch, k, d, seed):
+    X = planted(25, k, d, 0.02, seed)
+    n = X.shape[0]
+    draws = np.random.default_rng(seed + 10).integers(0, 2 ** 32, (10, k), dtype=np.uint64).astype(np.uint32)
+    cen = torch.empty((k, d), device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    inertia, iters = lib.kmeans(torch.from_numpy(X).cuda(), k, draws, cen, lab)
+    C, labels, ref_inertia, _ = osel.kmeans(X.astype(np.float64), k, draws.astype(np.float64) / 2.0 ** 32)
+    assert np.array_equal(lab.cpu().numpy(), labels)
+    assert inertia == pytest.approx(ref_inertia, rel=1e-4)
+    assert np.allclose(cen.cpu().numpy(), C, atol=1e-5)
+
+
+def test_kmeans_seeding_picks_same_points(lib, torch):
+    X = planted(10, 4, 8, 0.05, 7)
+    draws = np.random.default_rng(3).integers(0, 2 ** 32, (1, 4), dtype=np.uint64).astype(np.uint32)
+    cen = torch.empty((4, 8), device="cuda")
+    lab = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
+    lib.kmeans(torch.from_numpy(X).cuda(), 4, draws, cen, lab, max_iter=1, tol=0.0)
+    C0 = osel.kmeanspp_init(X.astype(np.float64), 4, draws[0].astype(np.float64) / 2.0 ** 32)
+    C1, _, _, _ = osel.lloyd(X.astype(np.float64), C0, max_iter=1, tol=0.0)
+    assert np.allclose(cen.cpu().numpy(), C1, atol=1e-5)
+
+
+@pytest.mark.parametrize("which", ["deployed", "chosen", "all"])
+def test_score(lib, torch, which):
+    rng = np.random.default_rng(4)
+    perf = (rng.random((200, 64)) ** 2).astype(np.float32)
+    perf[3, :] = 0.0
+    tp = torch.from_numpy(perf).cuda()
+    dep = [3, 17, 40, 63]
+    chosen = rng.choice(dep, 200).astype(np.int32)
+    if which == "deployed":
+        got = lib.score(tp, dep)
+        want = osel.score(perf.astype(np.float64), deployed=np.array(dep))
+    elif which == "chosen":
+        got = lib.score(tp, dep, chosen=torch.from_numpy(chosen).cuda())
+        want = osel.score(perf.astype(np.float64), chosen=chosen)
+    else:
+        got = lib.score(tp)
+        want = osel.score(perf.astype(np.float64))
+    assert got["geomean"] == pytest.approx(want["geomean"], rel=1e-5)
+    assert got["mean"] == pytest.approx(want["mean"], rel=1e-5)
+    assert got["clamped"] == want["clamped"]

@@ -1,0 +1,87 @@
+"""Host-side pipeline functions of the library (no GPU needed) against the oracle.
+
+CART, representatives and Top-N are exact integer/index work: the library must
+reproduce the oracle's trees node for node and its column choices exactly."""
+import numpy as np
+import pytest
+
+from oracle import select as osel
+
+
+@pytest.fixture(scope="module")
+def ks():
+    from paper_2008_13145_gb300 import build
+    build.build_library()
+    from paper_2008_13145_gb300 import kselect
+    return kselect
+
+
+def same_tree(a, b):
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        assert (x["feature"], x["left"], x["right"], x["label"]) == (y["feature"], y["left"], y["right"], y["label"])
+        if x["feature"] >= 0:
+            assert x["threshold"] == y["threshold"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("tree", ["A", "B", "C"])
+def test_tree_matches_oracle_with_many_ties(ks, seed, tree):
+    rng = np.random.default_rng(seed)
+    n = 150
+    F = rng.integers(1, 7, (n, 4)).astype(np.float64)  # few distinct values: many tied splits
+    y = rng.integers(0, 5, n)
+    depth, leaf = osel.TREES[tree]
+    same_tree(ks.tree_train(F, y, 5, depth, leaf), osel.tree_train(F, y, 5, depth, leaf))
+
+
+@pytest.mark.parametrize("tree", ["A", "B", "C"])
+def test_tree_matches_oracle_on_grid_sizes(ks, tree):
+    from paper_2008_13145_gb300 import workloads as wl
+    g = wl.shape_grid(400, 21)
+    F = np.array([[s.M, s.N, s.K, s.batch] for s in g], np.float64)
+    y = ((F[:, 0] * F[:, 1] > 1e5).astype(int) + (F[:, 2] > 700).astype(int) * 2
+         + (np.random.default_rng(2).random(400) < 0.15))
+    depth, leaf = osel.TREES[tree]
+    same_tree(ks.tree_train(F, y, 5, depth, leaf), osel.tree_train(F, y, 5, depth, leaf))
+
+
+def test_tree_pure_and_single_sample(ks):
+    F = np.array([[1.0, 2, 3, 4]])
+    assert ks.tree_train(F, np.array([2]), 3) == [{"feature": -1, "threshold": 0.0, "left": -1, "right": -1,
+                                                    "label": 2}]
+    F = np.tile(np.array([[5.0, 5, 5, 5]]), (6, 1))
+    nodes = ks.tree_train(F, np.array([0, 1, 1, 0, 1, 0]), 2)
+    assert len(nodes) == 1 and nodes[0]["label"] == 0  # identical features: no split, tie -> lowest class
+
+
+def test_tree_rejects_bad_input(ks):
+    with pytest.raises(ks.KSelectError):
+        ks.tree_train(np.ones((3, 4)), np.array([0, 5, 1]), 2)
+    with pytest.raises(ks.KSelectError):
+        ks.tree_train(np.full((3, 4), np.nan), np.array([0, 1, 1]), 2)
+    with pytest.raises(ks.KSelectError) as e:  # too many nodes for the output buffer
+        ks.tree_train(np.arange(400, dtype=float).reshape(100, 4), np.arange(100) % 2, 2, max_nodes=5)
+    assert e.value.status == -2
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_representatives_match_oracle(ks, seed):
+    rng = np.random.default_rng(seed)
+    k, d, n = 6, 40, 90
+    centres = rng.random((k, d)).astype(np.float32)
+    centres[:, 3] += 0.8  # a shared favourite forces duplicates
+    labels = rng.integers(0, k, n)
+    for dedupe in (True, False):
+        got = ks.representatives(centres, labels, dedupe)
+        want = osel.representatives(centres.astype(np.float64), labels, dedupe)
+        assert list(got) == list(want)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_top_n_matches_oracle(ks, seed):
+    rng = np.random.default_rng(seed)
+    perf = rng.random((60, 30)).astype(np.float32) ** 3
+    perf[:, 7] *= 3.0
+    for n in (1, 4, 8, 15, 30):
+        assert list(ks.top_n(perf, n)) == list(osel.top_n(perf.astype(np.float64), n))
