@@ -1,0 +1,322 @@
+"""Benchmark: selected-kernel GEMM TFLOP/s over held-out shapes of the tuning grid.
+
+Workload: the 200 held-out sizes (80/20 seeded split) of the 1,000-shape
+FP32 tuning grid (M, N, K log-uniform in [16, 4096], batch in {1,..,16},
+transA/transB in {N, T}, uniform[-1, 1] data).  One step = for every held-out
+size, the deployed decision tree picks one of the deployed kernels and the
+library launches it (select_kernel + gemm through the C-ABI), with every
+input resident in HBM.  The step's inputs total ~7 GB, far above the 129 MB
+L2, so consecutive steps start from a cold L2.
+
+Also reported: the same metric end to end from pinned host buffers
+(gemm_host: H2D copies, GEMM, D2H copy inside the timed region); the share of
+the per-shape exhaustive optimum (each held-out size re-run with the best of
+all 576 configs from the GB300 sweep table, untimed pass); the dominant
+kernel's roofline; the FP64 CPU oracle timed on a bounded sample on the host
+cores (``cpu_baseline``).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2008_13145_gb300 import workloads as wl  # noqa: E402
+
+DEPLOY = os.path.join(ROOT, "paper_2008_13145_gb300", "deploy")
+METRIC = "selected-kernel GEMM TFLOP/s and % of per-shape exhaustive optimum, FP32 vs TC"
+WORKLOAD = "held-out 20% (200 shapes) of the 1000-shape FP32 tuning grid (seed 1)"
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
+
+
+def test_shapes():
+    g = wl.shape_grid(1000, 1)
+    _, te = wl.train_test_split(1000, 1)
+    return [g[i] for i in te], te
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and "Active" in r[3 + i]
+                          and "Not" not in r[3 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- reference arm: the CPU oracle
+def cpu_oracle_sample(shapes, budget_s: float, nthreads: int):
+    """FP64 oracle throughput on a bounded sample: per held-out shape in order,
+    the oracle computes 2 sampled rows x all columns of batch entry 0, until
+    the time budget is spent.  Returns (TFLOP/s, description)."""
+    from oracle import gemm as og
+    og.build()
+    flops, t_used, n_shapes, entries = 0, 0.0, 0, 0
+    for sh in shapes:
+        A, B, _ = wl.gemm_inputs(wl.Shape(sh.M, sh.N, sh.K, 1, sh.transA, sh.transB), seed=5)
+        rows = np.arange(min(2, sh.M))
+        pos = np.stack(np.meshgrid(np.zeros(1, np.int64), rows, np.arange(sh.N), indexing="ij"), -1).reshape(-1, 3)
+        t0 = time.perf_counter()
+        og.gemm_entries(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, B, 0.0, None, pos, nthreads=nthreads)
+        t_used += time.perf_counter() - t0
+        flops += 2 * sh.K * len(pos)
+        entries += len(pos)
+        n_shapes += 1
+        if t_used >= budget_s:
+            break
+    return flops / t_used / 1e12, (f"2 rows x all columns of batch entry 0 of the first {n_shapes} held-out shapes "
+                                   f"({entries} entries, {flops / 1e9:.2f} GFLOP, {t_used:.1f} s)")
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    shapes, _ = test_shapes()
+    steps, t_all, val = [], 0.0, None
+    from oracle import gemm as og
+    og.build()
+    nthreads = og.max_threads()
+    for s in range(args.warmup + args.steps):
+        v, desc = cpu_oracle_sample(shapes, args.ref_budget, nthreads)
+        if s >= args.warmup:
+            steps.append(v)
+    val = statistics.median(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "kind": "fp64 triple-loop CPU oracle"},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": nthreads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2008_13145_gb300 import kselect as ks
+    from paper_2008_13145_gb300 import tune
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    dep_path = os.path.join(DEPLOY, "f32.json")
+    dep = json.load(open(dep_path))
+    handle = ks.Handle(dep)
+    table_shapes, perf, table_ids, _ = tune.load_table(os.path.join(DEPLOY, "table_f32.npz"))
+    shapes, te = test_shapes()
+    assert [table_shapes[i] for i in te] == shapes, "sweep table does not match the workload grid"
+    best_cfg = [table_ids[int(np.argmax(perf[i]))] for i in te]
+
+    bufs = [tune.alloc_inputs(sh, ks.PREC_F32, 1000 + 7 * rank + i) for i, sh in enumerate(shapes)]
+    flops = sum(sh.flops for sh in shapes)
+    chosen = [ks.select_kernel(handle, sh.M, sh.N, sh.K, sh.batch) for sh in shapes]
+
+    def step(events=None, cfgs=None):
+        for i, (sh, (A, B, C, lda, ldb, ldc)) in enumerate(zip(shapes, bufs)):
+            if events is not None:
+                events[i][0].record(stream)
+            if cfgs is None:
+                ks.gemm(handle, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, lda, B, ldb, 0.0, C, ldc, sh.batch,
+                        stream)
+            else:
+                ks.gemm_with_config(cfgs[i], sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, lda, B, ldb, 0.0, C,
+                                    ldc, sh.batch, stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    def per_launch_ms(cfgs=None):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in shapes]
+        step(ev, cfgs)
+        torch.cuda.synchronize(dev)
+        return np.array([a.elapsed_time(b) for a, b in ev])
+
+    # Warm-up steps (selected kernels); the first one also times every launch.
+    sel_ms = per_launch_ms()
+    for _ in range(args.warmup - 1):
+        step()
+    # Untimed reference pass: every shape with its exhaustive-best config.
+    exh_ms = per_launch_ms(best_cfg)
+    ratio = np.minimum(exh_ms / sel_ms, 1.0)
+    live = {"geomean": float(np.exp(np.mean(np.log(ratio)))), "mean": float(np.mean(ratio)),
+            "source": "per-shape launch times this run: exhaustive-best config vs selected config"}
+    # Dominant kernel: the deployed config with the largest share of step time.
+    by_cfg = {}
+    for c, t, sh in zip(chosen, sel_ms, shapes):
+        a = by_cfg.setdefault(c, [0.0, 0, 0])
+        a[0] += t
+        a[1] += sh.flops
+        a[2] += 1
+    dom = max(by_cfg, key=lambda c: by_cfg[c][0])
+    dom_idx = [i for i, c in enumerate(chosen) if c == dom]
+
+    # Timed region: K steps, dominant-kernel launches bracketed by events.
+    dom_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in dom_idx]
+              for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for k in range(args.steps):
+            evs = {i: ev for i, ev in zip(dom_idx, dom_ev[k])}
+            for i, (sh, (A, B, C, lda, ldb, ldc)) in enumerate(zip(shapes, bufs)):
+                if i in evs:
+                    evs[i][0].record(stream)
+                ks.gemm(handle, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, lda, B, ldb, 0.0, C, ldc, sh.batch,
+                        stream)
+                if i in evs:
+                    evs[i][1].record(stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms_total = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = ws * flops * args.steps / (ms_total * 1e-3) / 1e12
+    dom_ms = sum(a.elapsed_time(b) for evs in dom_ev for a, b in evs) / (len(dom_idx) * args.steps)
+    dom_flops = by_cfg[dom][1] / by_cfg[dom][2]
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+
+    # End to end from pinned host buffers through gemm_host.
+    hosts = []
+    h2d = d2h = 0
+    for sh, (A, B, C, lda, ldb, ldc) in zip(shapes, bufs):
+        hA, hB = A.cpu().pin_memory(), B.cpu().pin_memory()
+        hC = torch.empty(C.numel(), dtype=torch.float32).pin_memory()
+        hosts.append((hA, hB, hC))
+        h2d += hA.numel() * hA.element_size() + hB.numel() * hB.element_size()
+        d2h += hC.numel() * 4
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for sh, (A, B, C, lda, ldb, ldc), (hA, hB, hC) in zip(shapes, bufs, hosts):
+            ks.gemm_host(handle, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, hA, lda, hB, ldb, 0.0, hC, ldc,
+                         sh.batch, A, B, C, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = ws * flops * args.steps / (ms_e2e * 1e-3) / 1e12
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        from oracle import gemm as og
+        v, desc = cpu_oracle_sample(shapes, args.ref_budget, og.max_threads())
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": og.max_threads(), "kind": "oracle", "sample": desc}
+    clocks = clk.summary()
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        t = json.load(open(tp)).get(str(dom))
+        traffic = t.get("bytes_per_launch") if t else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "family": "FP32 SIMT", "deployed_kernels": len(dep["config_ids"]),
+                   "selector": f"decision tree {dep['meta']['tree']}", "shapes_per_step": len(shapes),
+                   "gflop_per_step": flops / 1e9, "l2": "inputs 7 GB per step, larger than L2",
+                   "deployment": os.path.relpath(dep_path, ROOT)},
+        "pct_of_exhaustive_optimum": {"live": live, "sweep_table_test_split": dep["meta"]["scores"]["tree"]},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel_config": dom,
+                     "kernel_params": ks.config_params(dom), "share_of_step": by_cfg[dom][0] / float(sel_ms.sum())},
+        "e2e": {"value": e2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * len(shapes),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of CPU oracle work per sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -130,6 +130,16 @@ gemm_status_t gemm(gemm_handle_t handle, char transA, char transB, int64_t M, in
                    float alpha, const void* A_dev, int64_t lda, const void* B_dev, int64_t ldb,
                    float beta, float* C_dev, int64_t ldc, int64_t batch, void* stream);
 
+/* gemm() on host-resident data: copies A, B (and C when beta != 0) from the
+ * host into the caller's device staging buffers (A_dev, B_dev, C_dev, each at
+ * least the packed batch size), runs the selected kernel and copies C back,
+ * all enqueued on `stream` (pinned host memory makes the copies
+ * asynchronous; the caller synchronises before reading C_host). */
+gemm_status_t gemm_host(gemm_handle_t handle, char transA, char transB, int64_t M, int64_t N, int64_t K,
+                        float alpha, const void* A_host, int64_t lda, const void* B_host, int64_t ldb,
+                        float beta, float* C_host, int64_t ldc, int64_t batch, void* A_dev, void* B_dev,
+                        float* C_dev, void* stream);
+
 /* The same operation with an explicit config id (any family). */
 gemm_status_t gemm_with_config(int32_t config_id, char transA, char transB, int64_t M, int64_t N,
                                int64_t K, float alpha, const void* A_dev, int64_t lda,
@@ -220,6 +230,48 @@ gemm_status_t kselect_tree_train(int32_t n, const double* features, const int32_
                                  int32_t max_depth, int32_t min_leaf, gemm_tree_node_t* out_nodes,
                                  int32_t max_nodes, int32_t* out_n_nodes);
 
+/* ---------------------------------------------------------------- learned selector (MLP)
+ * A performance model beside the tree: 7 features of a GEMM -> 64 ReLU ->
+ * 64 ReLU -> 8 outputs, the predicted natural-log GFLOP/s of each deployed
+ * kernel (it replaces the paper's MLP classifier of Section 5.1 by a
+ * regressor).  Parameters are one FP32 vector of GEMM_MLP_PARAMS values:
+ * W1 (7 x 64, row = input), b1 (64), W2 (64 x 64), b2, W3 (64 x 8), b3 (8).
+ * Features of (M, N, K, batch, transA, transB, dtype):
+ *   [log2 M / 12, log2 N / 12, log2 K / 12, log2 batch / 4, transA, transB, dtype / 3].
+ * X_dev is n x 7 FP32 features, T_dev n x 8 targets, mask_dev n x 8 (1 =
+ * measured) or NULL for all measured.  All arrays are device, row-major. */
+
+/* Y_dev (n x 8) = network(X_dev). */
+gemm_status_t mlp_forward(int32_t n, const float* params_dev, const float* X_dev, float* Y_dev, void* stream);
+
+/* Mean squared error over the measured outputs and its gradient.  grad_dev
+ * receives GEMM_MLP_PARAMS values and loss_dev one value.  Per-block partial
+ * gradients are reduced in a fixed order (deterministic); their scratch is
+ * allocated and freed stream-ordered. */
+gemm_status_t mlp_loss_grad(int32_t n, const float* params_dev, const float* X_dev, const float* T_dev,
+                            const float* mask_dev, float* grad_dev, float* loss_dev, void* stream);
+
+/* One Adam step (Kingma & Ba, bias-corrected) at step t >= 1 on every parameter. */
+gemm_status_t mlp_adam_step(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int32_t t,
+                            float lr, float beta1, float beta2, float eps, void* stream);
+
+/* `steps` full-batch Adam steps starting at step t0 + 1, captured once in a
+ * CUDA graph and replayed; loss_hist_dev (steps values, or NULL) receives the
+ * loss before each update.  Synchronises `stream`. */
+gemm_status_t mlp_train(int32_t n, float* params_dev, const float* X_dev, const float* T_dev, const float* mask_dev,
+                        float* m_dev, float* v_dev, int32_t t0, int32_t steps, float lr, float beta1, float beta2,
+                        float eps, float* loss_hist_dev, void* stream);
+
+/* Batched runtime selection for a queue of GEMMs: shapes_dev holds n rows of
+ * 7 int64 (M, N, K, batch, transA, transB, dtype); the handle's MLP predicts
+ * every deployed kernel's throughput and ids_dev[i] receives the config id of
+ * the largest prediction among the handle's deployed kernels (lowest index on
+ * ties).  pred_dev (n x 8) receives the predictions, or may be NULL.  The
+ * handle must carry MLP parameters (else GEMM_ERR_UNSUPPORTED); they are
+ * copied to the device on the first call per device. */
+gemm_status_t select_kernels_batched(gemm_handle_t handle, int32_t n, const int64_t* shapes_dev, int32_t* ids_dev,
+                                     float* pred_dev, void* stream);
+
 /* ---------------------------------------------------------------- error check
  * The judge of every GEMM result: err = max over entries of
  * |C - C_ref| / den, reduced on the GPU in FP64, where C_ref and den are the
@@ -237,6 +289,14 @@ gemm_status_t gemm_error_check(int64_t rows, int64_t cols, int64_t batch, const 
                                int64_t ldc, int64_t strideC, int64_t n, const int64_t* pos_dev,
                                const double* Cref_dev, const double* den_dev, double* out_err,
                                void* stream);
+
+/* The tensor-core kernels' device status word for the current device: 0, or
+ * the code of the first bounded wait that gave up (1 TMA slice never landed,
+ * 2 slice never released, 3 accumulator never completed, 4 accumulator never
+ * drained).  The word is sticky -- once set, later tensor-core launches on
+ * that device wind down early -- until read with clear != 0.  Synchronises
+ * the device.  Returns GEMM_ERR_TIMEOUT when the word is nonzero. */
+gemm_status_t gemm_device_status(int32_t* out_status, int32_t clear);
 
 /* Fills a (batch, rows, ld) float array with uniform[lo, hi) values from a
  * counter-based hash of (seed, element index); padding columns get `pad`.

@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <vector>
+
 #include "../../include/kselect.h"
 
 namespace ks {
@@ -53,3 +56,18 @@ gemm_status_t tc_params(int id, int32_t out[8]);
 void set_last_cuda_error(cudaError_t e);
 
 }  // namespace ks
+
+// The library handle: an immutable deployment plus a per-device cache of the
+// MLP parameters (filled on first use by select_kernels_batched).
+struct kselect_library {
+  int precision;
+  std::vector<int32_t> ids;
+  std::vector<gemm_tree_node_t> nodes;
+  std::vector<float> mlp;  // empty when absent
+  std::mutex dev_mu;
+  float* dev_mlp[64] = {nullptr};
+  ~kselect_library() {
+    for (float* p : dev_mlp)
+      if (p) cudaFree(p);
+  }
+};

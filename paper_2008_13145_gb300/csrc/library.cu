@@ -128,13 +128,6 @@ gemm_status_t make_launch_args(int id, char transA, char transB, int64_t M, int6
 
 using namespace ks;
 
-// ------------------------------------------------------------------ handle
-struct kselect_library {
-  int precision;
-  std::vector<int32_t> ids;
-  std::vector<gemm_tree_node_t> nodes;
-  std::vector<float> mlp;  // empty when absent
-};
 
 extern "C" {
 
@@ -253,6 +246,36 @@ gemm_status_t gemm(gemm_handle_t h, char transA, char transB, int64_t M, int64_t
   const int32_t id = select_kernel(h, M, N, K, batch);
   if (id < 0) return (gemm_status_t)id;
   return gemm_with_config(id, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch, stream);
+}
+
+gemm_status_t gemm_host(gemm_handle_t h, char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha,
+                        const void* A_host, int64_t lda, const void* B_host, int64_t ldb, float beta, float* C_host,
+                        int64_t ldc, int64_t batch, void* A_dev, void* B_dev, float* C_dev, void* stream) {
+  if (!h) return GEMM_ERR_INVALID_ARG;
+  const int32_t id = select_kernel(h, M, N, K, batch);
+  if (id < 0) return (gemm_status_t)id;
+  GemmArgs a;
+  bool noop = false;
+  gemm_status_t st = make_args(transA, transB, M, N, K, alpha, A_dev, lda, B_dev, ldb, beta, C_dev, ldc, batch,
+                               elem_bytes_of(id), &a, &noop);
+  if (st != GEMM_OK || noop) return st;
+  if ((K > 0 && (!A_host || !B_host)) || !C_host) return GEMM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t elem = (size_t)elem_bytes_of(id);
+  const size_t bytesA = (size_t)a.strideA * batch * elem, bytesB = (size_t)a.strideB * batch * elem;
+  const size_t bytesC = (size_t)a.strideC * batch * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  if (K > 0) {
+    e = cudaMemcpyAsync(A_dev, A_host, bytesA, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B_dev, B_host, bytesB, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess && beta != 0.f) e = cudaMemcpyAsync(C_dev, C_host, bytesC, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+  st = launch_config(id, a, s);
+  if (st != GEMM_OK) return st;
+  e = cudaMemcpyAsync(C_host, C_dev, bytesC, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+  return GEMM_OK;
 }
 
 gemm_status_t gemm_benchmark(int32_t id, char transA, char transB, int64_t M, int64_t N, int64_t K,

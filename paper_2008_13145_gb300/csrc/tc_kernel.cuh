@@ -1,0 +1,225 @@
+// Persistent warp-specialised tcgen05 GEMM for sm_103a.
+//
+// C[b] = alpha * A[b] * B[b]^T + beta * C[b] with A (M x K) and B (N x K)
+// both K-contiguous in global memory (BF16, or FP32 read as TF32).  Tiles of
+// 128 x BN outputs are distributed over persistent CTAs; each CTA runs
+//   warp 4      : TMA producer (one elected lane) filling a STAGES-deep ring
+//                 of 128-byte-swizzled A/B slices, 128 bytes of K per slice;
+//   warp 5      : TMEM allocator and MMA issuer (one elected lane), 4
+//                 tcgen05.mma per slice into an FP32 accumulator in TMEM;
+//   warps 0..3  : epilogue, tcgen05.ld of their 32-lane quadrant, alpha/beta,
+//                 vector stores of C.
+// Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap
+// the MMAs of tile i+1.
+#pragma once
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+namespace ks {
+namespace tc {
+
+struct TcArgs {
+  int M, N, K, batch;
+  int tiles_m, tiles_n, num_tiles, k_blocks;
+  int raster;  // 0: consecutive tiles walk M (reuse the B slice), 1: walk N
+  float alpha, beta;
+  float* C;
+  int64_t ldc, strideC;
+  int vecC;
+  int* status;
+};
+
+constexpr int kThreads = 192;
+constexpr int kBM = 128;
+
+template <int BN, int STAGES, bool TF32>
+struct TcCfg {
+  static constexpr int ELEM = TF32 ? 4 : 2;
+  static constexpr int BK = 128 / ELEM;        // K elements per slice (one 128-byte row)
+  static constexpr int KMMA = TF32 ? 8 : 16;   // K per tcgen05.mma
+  static constexpr int A_BYTES = kBM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int TMEM_COLS = 2 * BN;     // 128, 256 or 512: power of two >= 32
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+};
+
+__device__ __forceinline__ void tile_coords(const TcArgs& p, int tile, int& b, int& tm, int& tn) {
+  const int per = p.tiles_m * p.tiles_n;
+  b = tile / per;
+  const int t = tile - b * per;
+  if (p.raster == 0) {
+    tm = t % p.tiles_m;
+    tn = t / p.tiles_m;
+  } else {
+    tn = t % p.tiles_n;
+    tm = t / p.tiles_n;
+  }
+}
+
+__device__ __forceinline__ void store_row32(const TcArgs& p, float* crow, int n0, const uint32_t (&r)[32]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int n = n0 + 4 * q;
+    float v[4] = {__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
+                  __uint_as_float(r[4 * q + 3])};
+    if (p.vecC && n + 3 < p.N) {
+      float4 o = make_float4(p.alpha * v[0], p.alpha * v[1], p.alpha * v[2], p.alpha * v[3]);
+      if (p.beta != 0.f) {
+        const float4 c = *reinterpret_cast<const float4*>(crow + n);
+        o.x = fmaf(p.beta, c.x, o.x); o.y = fmaf(p.beta, c.y, o.y);
+        o.z = fmaf(p.beta, c.z, o.z); o.w = fmaf(p.beta, c.w, o.w);
+      }
+      *reinterpret_cast<float4*>(crow + n) = o;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (n + e < p.N) {
+          float o = p.alpha * v[e];
+          if (p.beta != 0.f) o = fmaf(p.beta, crow[n + e], o);
+          crow[n + e] = o;
+        }
+      }
+    }
+  }
+}
+
+template <int BN, int STAGES, bool TF32>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs p) {
+  using Cfg = TcCfg<BN, STAGES, TF32>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accf_bar[a], 1);
+      mbar_init(&acce_bar[a], 128);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 4 && lane == 0) {
+    tma_prefetch(&tmA);
+    tma_prefetch(&tmB);
+  }
+  if (warp == 5) tmem_alloc<Cfg::TMEM_COLS>(&tmem_base_sh);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+
+  if (warp == 4) {
+    // ---------------------------------------------------------------- TMA producer
+    if (elect_one()) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
+        int b, tm, tn;
+        tile_coords(p, tile, b, tm, tn);
+        for (int kb = 0; kb < p.k_blocks; ++kb) {
+          if (!(ok = mbar_wait(&empty_bar[stage], phase ^ 1, p.status, kStatusTimeoutEmpty))) break;
+          uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
+          mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
+          tma_load_3d(sa, &tmA, &full_bar[stage], kb * Cfg::BK, tm * kBM, b);
+          tma_load_3d(sa + Cfg::A_BYTES, &tmB, &full_bar[stage], kb * Cfg::BK, tn * BN, b);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      // Wait (bounded) until every issued slice has landed before the CTA can exit.
+      if (ok) {
+        for (int s = 0; s < STAGES; ++s) {
+          if (!mbar_wait(&empty_bar[stage], phase ^ 1, p.status, kStatusTimeoutEmpty)) break;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (elect_one()) {
+      constexpr uint32_t idesc = instr_desc<TF32>(kBM, BN, false, false);
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
+        if (!(ok = mbar_wait(&acce_bar[acc], acc_phase ^ 1, p.status, kStatusTimeoutAccEmpty))) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        for (int kb = 0; kb < p.k_blocks; ++kb) {
+          if (!(ok = mbar_wait(&full_bar[stage], phase, p.status, kStatusTimeoutFull))) break;
+          tc_fence_after();
+          const uint32_t a_addr = smem_u32(smem + stage * Cfg::STAGE_BYTES);
+          const uint32_t b_addr = a_addr + Cfg::A_BYTES;
+#pragma unroll
+          for (int k = 0; k < Cfg::BK / Cfg::KMMA; ++k) {
+            const uint32_t koff = (uint32_t)(k * Cfg::KMMA * Cfg::ELEM);  // bytes along the swizzled row
+            const uint64_t ad = smem_desc_sw128(a_addr + koff, 16, 1024);
+            const uint64_t bd = smem_desc_sw128(b_addr + koff, 16, 1024);
+            mma<TF32>(d_tmem, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+          }
+          mma_commit(&empty_bar[stage]);  // frees the slice once these MMAs have read it
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&accf_bar[acc]);  // accumulator complete
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 0..3)
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+      if (!mbar_wait(&accf_bar[acc], acc_phase, p.status, kStatusTimeoutAcc)) break;
+      tc_fence_after();
+      int b, tm, tn;
+      tile_coords(p, tile, b, tm, tn);
+      const int row = tm * kBM + warp * 32 + lane;
+      float* crow = p.C + (int64_t)b * p.strideC + (int64_t)row * p.ldc;
+      const uint32_t tbase = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tbase + (uint32_t)c0, r);
+        tmem_ld_wait();
+        if (row < p.M && tn * BN + c0 < p.N) store_row32(p, crow, tn * BN + c0, r);
+      }
+      tc_fence_before();
+      mbar_arrive(&acce_bar[acc]);
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc<Cfg::TMEM_COLS>(tmem_base);
+  }
+}
+
+}  // namespace tc
+}  // namespace ks

@@ -57,10 +57,17 @@ _sig("select_kernel", i32, [vp, i64, i64, i64, i64])
 _GEMM_ARGS = [ch, ch, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i64, vp]
 _sig("gemm", i32, [vp] + _GEMM_ARGS)
 _sig("gemm_with_config", i32, [i32] + _GEMM_ARGS)
+_sig("gemm_host", i32, [vp, ch, ch, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i64, vp, vp, vp, vp])
 _sig("gemm_benchmark", i32, [i32, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64, i64, i32, i32, i32, f64,
                              ctypes.POINTER(f64), vp])
 _sig("gemm_error_check", i32, [i64, i64, i64, vp, i64, i64, i64, vp, vp, vp, ctypes.POINTER(f64), vp])
 _sig("kselect_fill_uniform", i32, [vp, i64, i64, i64, i64, u64, f32, f32, f32, vp])
+_sig("gemm_device_status", i32, [ctypes.POINTER(i32), i32])
+_sig("mlp_forward", i32, [i32, vp, vp, vp, vp])
+_sig("mlp_loss_grad", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
+_sig("mlp_adam_step", i32, [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp])
+_sig("mlp_train", i32, [i32, vp, vp, vp, vp, vp, vp, i32, i32, f32, f32, f32, f32, vp, vp])
+_sig("select_kernels_batched", i32, [vp, i32, vp, vp, vp, vp])
 _sig("gemm_benchmark_configs", i32, [i32, ctypes.POINTER(i32), ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64,
                                      i64, i32, i32, i32, f64, f64, ctypes.POINTER(f64), ctypes.POINTER(i32), vp])
 _sig("kselect_normalise", i32, [i64, i32, vp, vp, i32, vp])
@@ -183,6 +190,14 @@ def gemm(handle: Handle, transA: str, transB: str, M, N, K, alpha, A, lda, B, ld
                     ptr(C), ldc, batch, stream_handle(stream)), "gemm")
 
 
+def gemm_host(handle: Handle, transA: str, transB: str, M, N, K, alpha, A_host, lda, B_host, ldb, beta, C_host, ldc,
+              batch, A_dev, B_dev, C_dev, stream=None) -> None:
+    """gemm() on host buffers (pinned torch tensors or raw host pointers) through device staging buffers."""
+    check(_lib.gemm_host(handle.value, _c(transA), _c(transB), M, N, K, alpha, ptr(A_host), lda, ptr(B_host), ldb,
+                         beta, ptr(C_host), ldc, batch, ptr(A_dev), ptr(B_dev), ptr(C_dev), stream_handle(stream)),
+          "gemm_host")
+
+
 def gemm_with_config(cid: int, transA: str, transB: str, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch=1,
                      stream=None) -> None:
     check(_lib.gemm_with_config(cid, _c(transA), _c(transB), M, N, K, alpha, ptr(A), lda, ptr(B), ldb, beta,
@@ -213,6 +228,15 @@ def error_check(C, Cref, den, rows=0, cols=0, batch=0, ldc=0, strideC=0, pos=Non
     check(_lib.gemm_error_check(rows, cols, batch, ptr(C), ldc, strideC, n, ptr(pos), ptr(Cref), ptr(den),
                                 ctypes.byref(out), stream_handle(stream)), "gemm_error_check")
     return out.value
+
+
+def device_status(clear: bool = True) -> int:
+    """The tensor-core status word (0 = no bounded wait gave up); synchronises the device."""
+    v = i32()
+    st = _lib.gemm_device_status(ctypes.byref(v), int(clear))
+    if st not in (GEMM_OK, -5):
+        raise KSelectError(st, "gemm_device_status")
+    return v.value
 
 
 def fill_uniform(dst, rows, cols, ld, batch, seed, lo=-1.0, hi=1.0, pad=0.0, stream=None) -> None:
@@ -298,10 +322,38 @@ def tree_train(features: np.ndarray, labels: np.ndarray, n_classes: int, max_dep
              "right": nodes[j].right, "label": nodes[j].label} for j in range(cnt.value)]
 
 
+# ---------------------------------------------------------------- learned selector
+def mlp_forward(params, X, Y, stream=None) -> None:
+    check(_lib.mlp_forward(X.shape[0], ptr(params), ptr(X), ptr(Y), stream_handle(stream)), "mlp_forward")
+
+
+def mlp_loss_grad(params, X, T, mask, grad, loss, stream=None) -> None:
+    check(_lib.mlp_loss_grad(X.shape[0], ptr(params), ptr(X), ptr(T), ptr(mask), ptr(grad), ptr(loss),
+                             stream_handle(stream)), "mlp_loss_grad")
+
+
+def mlp_adam_step(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+    check(_lib.mlp_adam_step(ptr(params), ptr(grad), ptr(m), ptr(v), t, lr, beta1, beta2, eps, stream_handle(stream)),
+          "mlp_adam_step")
+
+
+def mlp_train(params, X, T, mask, m, v, t0, steps, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, loss_hist=None,
+              stream=None) -> None:
+    check(_lib.mlp_train(X.shape[0], ptr(params), ptr(X), ptr(T), ptr(mask), ptr(m), ptr(v), t0, steps, lr, beta1,
+                         beta2, eps, ptr(loss_hist), stream_handle(stream)), "mlp_train")
+
+
+def select_kernels_batched(handle: Handle, shapes, ids_out, pred=None, stream=None) -> None:
+    """shapes: (n, 7) int64 device tensor (M, N, K, batch, transA, transB, dtype)."""
+    check(_lib.select_kernels_batched(handle.value, shapes.shape[0], ptr(shapes), ptr(ids_out), ptr(pred),
+                                      stream_handle(stream)), "select_kernels_batched")
+
+
 def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points this binding expects."""
     return ["gemm_status_string", "gemm_last_cuda_error", "gemm_config_count", "gemm_config_id",
             "gemm_config_params", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
-            "gemm_with_config", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
-            "gemm_benchmark_configs", "kselect_normalise", "kselect_kmeans", "kselect_score",
-            "kselect_representatives", "kselect_top_n", "kselect_tree_train"]
+            "gemm_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
+            "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
+            "kselect_representatives", "kselect_top_n", "kselect_tree_train", "mlp_forward", "mlp_loss_grad",
+            "mlp_adam_step", "mlp_train", "select_kernels_batched"]

@@ -1,0 +1,224 @@
+"""Tuning driver: benchmark every configuration over a shape grid, prune the
+set by k-means, train the runtime classifier, and write a deployment.
+
+Each numeric step runs in the library (GPU kernels for benchmarking,
+normalisation, clustering and scoring; the library's host code for CART and
+representatives); this module sequences the calls and reads/writes files.
+
+    python -m paper_2008_13145_gb300.tune sweep  --precision f32 --n 1000 --seed 1 --out sweep_f32.jsonl
+    python -m paper_2008_13145_gb300.tune deploy --sweep sweep_f32.jsonl --k 8 --tree B --out f32.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+from . import workloads as wl
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEPLOY_DIR = os.path.join(HERE, "deploy")
+TREES = {"A": (None, 1), "B": (6, 3), "C": (3, 4)}  # Section 5.1: (max depth, min samples per leaf)
+
+
+def _ks():
+    from . import kselect
+    return kselect
+
+
+def ld_multiple(precision: int) -> int:
+    return 8 if precision == 2 else 4
+
+
+def alloc_inputs(shape: wl.Shape, precision: int, seed: int, device="cuda"):
+    """Device buffers (A, B, C, lda, ldb, ldc) for one shape, A and B uniform[-1,1)
+    from the library's counter-based fill (BF16 for the BF16 family)."""
+    import torch
+    ks = _ks()
+    m = ld_multiple(precision)
+    ar, ac = shape.stored_a()
+    br, bc = shape.stored_b()
+    lda, ldb, ldc = wl.round_up(ac, m), wl.round_up(bc, m), wl.round_up(shape.N, 4)
+    A = torch.empty(shape.batch * ar * lda, device=device)
+    B = torch.empty(shape.batch * br * ldb, device=device)
+    ks.fill_uniform(A, shape.batch * ar, ac, lda, 1, 2 * seed + 1)
+    ks.fill_uniform(B, shape.batch * br, bc, ldb, 1, 2 * seed + 2)
+    if precision == 2:
+        A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
+    C = torch.empty(shape.batch * shape.M * ldc, device=device)
+    return A, B, C, lda, ldb, ldc
+
+
+# ---------------------------------------------------------------- Section 3.1
+def sweep(shapes: list[wl.Shape], precision: int, out_path: str, seed: int = 0, refine_ratio: float = 2.0,
+          min_total_ms: float = 2.0, config_ids: list[int] | None = None, log=sys.stderr) -> np.ndarray:
+    """Benchmark every config on every shape; append one JSON line per shape
+    to out_path and skip shapes already there (resume).  Returns GFLOP/s (n x c)."""
+    import torch
+    ks = _ks()
+    ids = list(config_ids) if config_ids is not None else ks.config_ids(precision)
+    done = {}
+    if os.path.exists(out_path):
+        for line in open(out_path):
+            if line.strip():
+                r = json.loads(line)
+                if r["config_ids"] == ids:
+                    done[r["i"]] = r
+    t0 = time.time()
+    with open(out_path, "a") as f:
+        for i, sh in enumerate(shapes):
+            if i in done:
+                continue
+            A, B, C, lda, ldb, ldc = alloc_inputs(sh, precision, seed + i)
+            ms, st = ks.benchmark_configs(ids, sh.transA, sh.transB, sh.M, sh.N, sh.K, A, lda, B, ldb, C, ldc,
+                                          sh.batch, refine_ratio=refine_ratio, min_total_ms=min_total_ms)
+            rec = {"i": i, "shape": [sh.M, sh.N, sh.K, sh.batch, sh.transA, sh.transB], "precision": precision,
+                   "config_ids": ids, "ms": [round(float(x), 6) for x in ms], "status": [int(s) for s in st]}
+            f.write(json.dumps(rec) + "\n")
+            f.flush()
+            done[i] = rec
+            del A, B, C
+            if log and (i % 50 == 0 or i == len(shapes) - 1):
+                best = max(sh.flops / (m * 1e9) for m, s in zip(ms, st) if s == 0 and m > 0) if any(
+                    s == 0 for s in st) else 0.0
+                log.write(f"[sweep] {i + 1}/{len(shapes)} {sh} best {best:.1f} TFLOP/s  {time.time() - t0:.0f}s\n")
+                log.flush()
+        torch.cuda.synchronize()
+    return table_from_records([done[i] for i in range(len(shapes))], shapes)
+
+
+def table_from_records(records, shapes) -> np.ndarray:
+    """GFLOP/s per (shape, config); failed configs are 0 (Section 3 reading: a
+    configuration that cannot run a size has no throughput)."""
+    perf = np.zeros((len(records), len(records[0]["ms"])))
+    for r, (rec, sh) in enumerate(zip(records, shapes)):
+        ms = np.asarray(rec["ms"], np.float64)
+        ok = (np.asarray(rec["status"]) == 0) & (ms > 0)
+        perf[r, ok] = sh.flops / (ms[ok] * 1e6)
+    return perf
+
+
+def load_sweep(path: str):
+    recs = [json.loads(l) for l in open(path) if l.strip()]
+    recs.sort(key=lambda r: r["i"])
+    shapes = [wl.Shape(int(r["shape"][0]), int(r["shape"][1]), int(r["shape"][2]), int(r["shape"][3]),
+                       r["shape"][4], r["shape"][5]) for r in recs]
+    return recs, shapes, table_from_records(recs, shapes)
+
+
+def save_table(path: str, shapes, perf, config_ids, precision):
+    np.savez_compressed(path, perf=perf.astype(np.float32), config_ids=np.asarray(config_ids, np.int32),
+                        shapes=np.array([[s.M, s.N, s.K, s.batch, s.transA == "T", s.transB == "T"] for s in shapes],
+                                        np.int64), precision=precision)
+
+
+def load_table(path: str):
+    z = np.load(path)
+    shapes = [wl.Shape(int(a), int(b), int(c), int(d), "NT"[int(e)], "NT"[int(f)]) for a, b, c, d, e, f in z["shapes"]]
+    return shapes, z["perf"].astype(np.float64), [int(x) for x in z["config_ids"]], int(z["precision"])
+
+
+# ---------------------------------------------------------------- Sections 3.4 and 4
+def kmeans_draws(n_init: int, k: int, seed: int) -> np.ndarray:
+    """The seeding draws (uint32) the clustering consumes: an input, not computed by it."""
+    return wl.rng_for(seed, 31).integers(0, 2 ** 32, (n_init, k), dtype=np.uint64).astype(np.uint32)
+
+
+def prune(perf_train: np.ndarray, k: int, seed: int = 0, norm: str = "standard", n_init: int = 10) -> dict:
+    """k-means over the normalised performance vectors of the training sizes;
+    the deployed set is each centre's best configuration (Sections 3.4, 4.1-4.2)."""
+    import torch
+    ks = _ks()
+    P = torch.from_numpy(np.ascontiguousarray(perf_train, np.float32)).cuda()
+    X = torch.empty_like(P)
+    ks.normalise(P, X, norm)
+    n, d = X.shape
+    cen = torch.empty((k, d), device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    inertia, iters = ks.kmeans(X, k, kmeans_draws(n_init, k, seed), cen, lab)
+    cols = ks.representatives(cen.cpu().numpy(), lab.cpu().numpy(), dedupe=True)
+    return {"cols": [int(c) for c in cols], "inertia": inertia, "iters": iters,
+            "labels": lab.cpu().numpy().tolist()}
+
+
+def features(shapes) -> np.ndarray:
+    return np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
+
+
+def train_tree(perf_train: np.ndarray, shapes_train, cols: list[int], tree: str = "B") -> list[dict]:
+    """Section 5.1: label each training size with its best deployed kernel and fit the tree."""
+    ks = _ks()
+    y = np.argmax(perf_train[:, cols], axis=1).astype(np.int32)
+    depth, leaf = TREES[tree]
+    return ks.tree_train(features(shapes_train), y, len(cols), depth, leaf)
+
+
+def evaluate(perf_test: np.ndarray, shapes_test, deployment: dict, all_ids: list[int]) -> dict:
+    """Section 4.3 scores on held-out sizes, computed by the library's score kernel."""
+    import torch
+    ks = _ks()
+    h = ks.Handle(deployment)
+    col_of = {cid: j for j, cid in enumerate(all_ids)}
+    chosen = np.array([col_of[ks.select_kernel(h, s.M, s.N, s.K, s.batch)] for s in shapes_test], np.int32)
+    P = torch.from_numpy(np.ascontiguousarray(perf_test, np.float32)).cuda()
+    dep_cols = [col_of[c] for c in deployment["config_ids"]]
+    return {"deployed_max": ks.score(P, dep_cols),
+            "tree": ks.score(P, dep_cols, chosen=torch.from_numpy(chosen).cuda()),
+            "exhaustive": ks.score(P),
+            "chosen_cols": chosen.tolist()}
+
+
+def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard", split_seed: int = 1) -> dict:
+    shapes, perf, ids, precision = load_table(table_path)
+    tr, te = wl.train_test_split(len(shapes), split_seed)
+    pr = prune(perf[tr], k, seed, norm)
+    nodes = train_tree(perf[tr], [shapes[i] for i in tr], pr["cols"], tree)
+    dep = {"precision": precision, "config_ids": [ids[c] for c in pr["cols"]], "nodes": nodes}
+    ev = evaluate(perf[te], [shapes[i] for i in te], dep, ids)
+    ks = _ks()
+    topn = [int(c) for c in ks.top_n(perf[tr].astype(np.float32), len(pr["cols"]))]
+    import torch
+    ev["top_n"] = ks.score(torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda(), topn)
+    dep["meta"] = {"k": k, "tree": tree, "norm": norm, "kmeans_seed": seed, "split_seed": split_seed,
+                   "n_train": len(tr), "n_test": len(te), "inertia": pr["inertia"],
+                   "scores": {key: v for key, v in ev.items() if key != "chosen_cols"}}
+    return dep
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    s = sub.add_parser("sweep")
+    s.add_argument("--precision", default="f32")
+    s.add_argument("--n", type=int, default=1000)
+    s.add_argument("--seed", type=int, default=1)
+    s.add_argument("--out", required=True)
+    s.add_argument("--table", default=None)
+    d = sub.add_parser("deploy")
+    d.add_argument("--table", required=True)
+    d.add_argument("--k", type=int, default=8)
+    d.add_argument("--tree", default="B")
+    d.add_argument("--norm", default="standard")
+    d.add_argument("--seed", type=int, default=0)
+    d.add_argument("--out", required=True)
+    a = ap.parse_args(argv)
+    ks = _ks()
+    if a.cmd == "sweep":
+        prec = ks.PRECISIONS[a.precision]
+        shapes = wl.shape_grid(a.n, a.seed)
+        perf = sweep(shapes, prec, a.out)
+        if a.table:
+            save_table(a.table, shapes, perf, ks.config_ids(prec), prec)
+    else:
+        dep = deploy(a.table, a.k, a.tree, a.seed, a.norm)
+        with open(a.out, "w") as f:
+            json.dump(dep, f, indent=1)
+        print(json.dumps(dep["meta"]["scores"], indent=1))
+
+
+if __name__ == "__main__":
+    main()

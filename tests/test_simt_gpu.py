@@ -9,33 +9,11 @@ import pytest
 
 from oracle import gemm as og
 from paper_2008_13145_gb300 import workloads as wl
+from tests.gpu_helpers import GUARD, SENTINEL, Out
 
 pytestmark = pytest.mark.gpu
 TOL_F32 = 1e-5
-SENTINEL = 7777.0
-GUARD = 64
 TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
-
-
-class Out:
-    """C buffer (batch, M, ldc) inside a flat tensor with guard regions."""
-
-    def __init__(self, torch, C0, beta, N):
-        self.batch, self.M, self.ldc = C0.shape
-        flat = np.full(GUARD + C0.size + GUARD, SENTINEL, np.float32)
-        body = C0.copy()
-        if beta == 0:
-            body[:, :, :N] = np.nan
-        flat[GUARD:GUARD + C0.size] = body.ravel()
-        self.flat = torch.from_numpy(flat).cuda()
-        self.ptr = self.flat.data_ptr() + 4 * GUARD
-
-    def result(self, N):
-        f = self.flat.cpu().numpy()
-        assert np.all(f[:GUARD] == SENTINEL) and np.all(f[GUARD + self.batch * self.M * self.ldc:] == SENTINEL)
-        body = f[GUARD:GUARD + self.batch * self.M * self.ldc].reshape(self.batch, self.M, self.ldc)
-        assert np.all(body[:, :, N:] == SENTINEL), "write into ldc padding"
-        return body[:, :, :N]
 
 
 def pad_c(C0, ldc_extra=3):

@@ -1,0 +1,144 @@
+"""GPU parity of the tensor-core families (tcgen05 + TMA + TMEM) against the FP64 oracle.
+
+Tolerances on max |C - C_ref| / (|alpha||A||B| + |beta||C0|):
+  TF32  5e-3 (inputs truncated to 10-bit mantissas: <= 2^-9 per product),
+  BF16  2e-2 (BF16 inputs: products exact in FP32, only accumulation rounds),
+  F32X3 1e-5 (hi*hi + hi*lo + lo*hi misses lo*lo and the split residuals,
+        <= 3 * 2^-16 per product in the worst case; on uniform data with
+        K >= 16 the averaged error stays well below 1e-5)."""
+import numpy as np
+import pytest
+
+from oracle import gemm as og
+from paper_2008_13145_gb300 import workloads as wl
+from tests.gpu_helpers import Out
+
+pytestmark = pytest.mark.gpu
+FAMILIES = {"tf32": (1, 5e-3), "bf16": (2, 2e-2), "f32x3": (3, 1e-5)}
+TRANS = [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def to_dev(torch, x, bf16):
+    t = torch.from_numpy(x).cuda()
+    return t.to(torch.bfloat16) if bf16 else t
+
+
+def host_values(t):
+    """What the kernel actually reads (BF16 values widened exactly), for the oracle."""
+    return t.float().cpu().numpy()
+
+
+def tc_ids(ks, fam):
+    return ks.config_ids(FAMILIES[fam][0])
+
+
+def run(ks, torch, cid, fam, shape, alpha, beta, seed, ld_multiple=8, kind="uniform", bound=8):
+    bf16 = fam == "bf16"
+    A, B, C0 = wl.gemm_inputs(shape, seed=seed, beta_nonzero=beta != 0, ld_multiple=ld_multiple, kind=kind,
+                              bound=bound)
+    tA, tB = to_dev(torch, A, bf16), to_dev(torch, B, bf16)
+    out = Out(torch, C0, beta, shape.N)
+    ks.gemm_with_config(cid, shape.transA, shape.transB, shape.M, shape.N, shape.K, alpha, tA, A.shape[2], tB,
+                        B.shape[2], beta, out.ptr, C0.shape[2], shape.batch)
+    torch.cuda.synchronize()
+    C = out.result(shape.N)
+    ref, den = og.gemm(shape.transA, shape.transB, shape.M, shape.N, shape.K, alpha, host_values(tA).reshape(A.shape),
+                       host_values(tB).reshape(B.shape), beta, C0)
+    return C, ref, den
+
+
+@pytest.mark.parametrize("fam", list(FAMILIES))
+def test_tn_single_tile_family(lib, torch, fam):
+    """One 128 x 128 tile, both operands K-contiguous (no pre-pass)."""
+    ks = lib
+    cid = tc_ids(ks, fam)[8]  # BN 128, 3 stages, M-major raster
+    assert ks.config_params(cid)[2] == 128
+    C, ref, den = run(ks, torch, cid, fam, wl.Shape(128, 128, 128, 1, "N", "T"), 1.0, 0.0, seed=1)
+    assert og.error_ratio(C, ref, den) <= FAMILIES[fam][1]
+    assert ks.device_status() == 0
+
+
+@pytest.mark.parametrize("fam", list(FAMILIES))
+def test_every_config_ragged(lib, torch, fam):
+    """All 18 configs: several tiles in M and N with ragged tails, K not a multiple of the slice."""
+    ks = lib
+    bad = []
+    for cid in tc_ids(ks, fam):
+        C, ref, den = run(ks, torch, cid, fam, wl.Shape(300, 333, 136, 2, "N", "T"), -0.5, 0.25, seed=2)
+        err = og.error_ratio(C, ref, den)
+        if not err <= FAMILIES[fam][1]:
+            bad.append((cid, ks.config_params(cid), err))
+    assert not bad, bad
+    assert ks.device_status() == 0
+
+
+@pytest.mark.parametrize("fam", list(FAMILIES))
+@pytest.mark.parametrize("ta,tb", TRANS)
+def test_layouts_and_unaligned_ld(lib, torch, fam, ta, tb):
+    """Every transpose combination, with 16-byte aligned and unaligned leading dimensions."""
+    ks = lib
+    ids = tc_ids(ks, fam)
+    for cid, ldm in ((ids[1], 8), (ids[17], 1)):
+        C, ref, den = run(ks, torch, cid, fam, wl.Shape(190, 77, 99, 3, ta, tb), 1.5, -1.0, seed=3, ld_multiple=ldm)
+        assert og.error_ratio(C, ref, den) <= FAMILIES[fam][1], (cid, ldm)
+
+
+@pytest.mark.parametrize("fam,bound", [("tf32", 64), ("bf16", 16), ("f32x3", 128)])
+def test_integer_inputs_exact(lib, torch, fam, bound):
+    """Integers small enough to be exact in the operand format, with exact FP32 sums."""
+    ks = lib
+    cid = tc_ids(ks, fam)[4]
+    C, ref, _ = run(ks, torch, cid, fam, wl.Shape(160, 200, 256, 2, "T", "N"), 1.0, 1.0, seed=4, kind="integer",
+                    bound=bound)
+    assert np.array_equal(C.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("fam", list(FAMILIES))
+def test_degenerate_sizes(lib, torch, fam):
+    ks = lib
+    cid = tc_ids(ks, fam)[0]
+    for M, N, K in [(1, 1, 1), (1, 300, 20), (300, 1, 20), (5, 7, 4099)]:
+        C, ref, den = run(ks, torch, cid, fam, wl.Shape(M, N, K, 2, "N", "N"), 1.0, 0.5, seed=5)
+        tol = FAMILIES[fam][1] if (fam != "f32x3" or K >= 16) else 5e-5
+        assert og.error_ratio(C, ref, den) <= tol, (M, N, K)
+
+
+@pytest.mark.parametrize("fam", list(FAMILIES))
+def test_full_size_sampled(lib, torch, fam):
+    """4096^3 in the largest tile config, checked on sampled entries by the GPU FP64 reduction."""
+    ks = lib
+    bf16 = fam == "bf16"
+    cid = tc_ids(ks, fam)[16]  # BN 256, 4 stages
+    shape = wl.Shape(4096, 4096, 4096, 1, "N", "N")
+    A, B, _ = wl.gemm_inputs(shape, seed=6, ld_multiple=8)
+    tA, tB = to_dev(torch, A, bf16), to_dev(torch, B, bf16)
+    C = torch.empty((4096, 4096), device="cuda")
+    ks.gemm_with_config(cid, "N", "N", 4096, 4096, 4096, 1.0, tA, A.shape[2], tB, B.shape[2], 0.0, C, 4096, 1)
+    pos = wl.sample_positions(shape, 4, 4, seed=7)
+    ref, den = og.gemm_entries("N", "N", 4096, 4096, 4096, 1.0, host_values(tA).reshape(A.shape),
+                               host_values(tB).reshape(B.shape), 0.0, None, pos, nthreads=og.max_threads())
+    err = ks.error_check(C, torch.from_numpy(ref).cuda(), torch.from_numpy(den).cuda(), pos=torch.from_numpy(pos).cuda(),
+                         ldc=4096, strideC=4096 * 4096)
+    assert err <= FAMILIES[fam][1], err
+    assert ks.device_status() == 0
+
+
+def test_misaligned_direct_operand_is_rewritten(lib, torch):
+    """A pointer 4 bytes off a 16-byte boundary takes the pre-pass instead of failing TMA alignment."""
+    ks = lib
+    M, N, K = 130, 64, 96
+    rng = np.random.default_rng(8)
+    A = rng.uniform(-1, 1, (M, K)).astype(np.float32)
+    B = rng.uniform(-1, 1, (N, K)).astype(np.float32)
+    fa = torch.from_numpy(np.concatenate([[0.0], A.ravel()]).astype(np.float32)).cuda()
+    tB = torch.from_numpy(B).cuda()
+    C = torch.empty((M, N), device="cuda")
+    ks.gemm_with_config(tc_ids(ks, "tf32")[0], "N", "T", M, N, K, 1.0, fa.data_ptr() + 4, K, tB, K, 0.0, C, N, 1)
+    ref, den = og.gemm("N", "T", M, N, K, 1.0, A[None], B[None])
+    assert og.error_ratio(C.cpu().numpy()[None], ref, den) <= 5e-3
