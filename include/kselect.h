@@ -146,6 +146,44 @@ gemm_status_t gemm_with_config(int32_t config_id, char transA, char transB, int6
                                const void* B_dev, int64_t ldb, float beta, float* C_dev, int64_t ldc,
                                int64_t batch, void* stream);
 
+/* ---------------------------------------------------------------- grouped GEMM
+ * An uneven group of independent GEMMs in ONE persistent tensor-core launch:
+ * every problem is cut into 128 x BN tiles, the tiles of all problems are
+ * numbered consecutively, and each CTA walks the global tile index with a
+ * fixed stride, mapping it to (problem, tile) by binary search over the
+ * problems' first-tile offsets.  Per-problem TMA descriptors live in device
+ * memory.  Problems use the row-major conventions above; K >= 1.  Operands
+ * that are not K-contiguous (transA 'T', transB 'N'), not 16-byte aligned,
+ * and every operand of the F32X3 family are first rewritten by one grouped
+ * pre-pass launch into plan-owned scratch.
+ *
+ * A plan validates the problems, encodes their descriptors, uploads them and
+ * allocates its scratch once (gemm_grouped_plan_create synchronises
+ * `stream`); gemm_grouped_run then only launches kernels -- no allocation,
+ * copy or host synchronisation -- so it can be captured in a CUDA graph and
+ * replayed.  A, B and C of every problem must stay valid for the plan's life. */
+typedef struct {
+  int64_t M, N, K;
+  char transA, transB;
+  float alpha, beta;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  float* C;
+  int64_t ldc;
+} gemm_problem_t;
+
+typedef struct kselect_grouped_plan* gemm_grouped_plan_t;
+
+gemm_status_t gemm_grouped_plan_create(int32_t config_id, int32_t count, const gemm_problem_t* problems,
+                                       void* stream, gemm_grouped_plan_t* out);
+gemm_status_t gemm_grouped_run(gemm_grouped_plan_t plan, void* stream);
+void gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
+
+/* One-shot form: plan, run, synchronise `stream`, release the plan. */
+gemm_status_t gemm_grouped(int32_t config_id, int32_t count, const gemm_problem_t* problems, void* stream);
+
 /* Section 3.1 (data collection): warm-up launches, then timed repetitions.
  * Runs `warmup` untimed launches and one timed probe launch, then times one
  * back-to-back run of R launches between two CUDA events, R = min_total_ms /

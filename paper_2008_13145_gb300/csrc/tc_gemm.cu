@@ -1,20 +1,24 @@
-// Tensor-core GEMM families on sm_103a: TF32, BF16 and split-BF16 x3.
+// Tensor-core GEMM families on sm_103a: TF32, BF16 and split-BF16 x3, for a
+// single batched GEMM and for an uneven group of GEMMs in one launch.
 //
 // The kernel (tc_kernel.cuh) consumes two K-contiguous operands.  op(A) = A
 // with A stored M x K is used in place, op(B) = B^T with B stored N x K too;
 // other layouts, and operands whose rows are not 16-byte aligned, are first
-// rewritten K-contiguous by a tiled transpose pre-pass into stream-ordered
-// scratch.  The x3 family splits each FP32 value x into hi = bf16(x) and
-// lo = bf16(x - hi) in the same pre-pass and lays the K dimension out as three
-// segments, A' = [hi | hi | lo] and B' = [hi | lo | hi], so one BF16 GEMM over
-// K' = 3 K accumulates hi*hi + hi*lo + lo*hi in FP32.
+// rewritten K-contiguous by a tiled transpose pre-pass into scratch.  The x3
+// family splits each FP32 value x into hi = bf16(x) and lo = bf16(x - hi) in
+// the same pre-pass and lays K out as three segments, A' = [hi | hi | lo] and
+// B' = [hi | lo | hi], so one BF16 GEMM over K' = 3 K accumulates
+// hi*hi + hi*lo + lo*hi in FP32.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "tc_kernel.cuh"
@@ -88,56 +92,102 @@ int* status_word() {
 }
 
 // ---------------------------------------------------------------- K-contiguous pre-pass
-// out[b][r][seg * Kp + k] for r < R, k < Kp (zero for k >= K) from an input
-// whose element (r, k) sits at in[b * in_stride + r * rs + k * ks].
-// MODE 0: copy (same element type); MODE 1: x3 split of FP32 into BF16 with
-// segment pattern `pattern` (bit s set = segment s holds lo, else hi).
-template <typename TIn, typename TOut, int MODE>
-__global__ void kmajor_kernel(const TIn* __restrict__ in, int64_t in_stride, int64_t rs, int64_t ks, int R, int K,
-                              int Kp, int nseg, int pattern, TOut* __restrict__ out, int64_t ld_out) {
+// One rewrite job: out[b][r][seg * Kp + k] for r < R, k < Kp (zero for k >= K)
+// from the logical R x K operand whose element (r, k) of batch entry b sits at
+// in[b * in_stride + r * rs + k * ks].  Copy (nseg 1, same type) or x3 split
+// (FP32 in, BF16 out; bit s of `pattern` set = segment s holds lo, else hi).
+struct PrepJob {
+  const void* in;
+  int64_t in_stride, rs, ks;
+  void* out;
+  int64_t ld_out;
+  int R, K, Kp, nseg, pattern;
+  int tiles_k, tiles_r, block_start;  // 32 x 32 tiles; first block of this job (grouped form)
+};
+
+template <typename TIn, typename TOut, bool SPLIT>
+__device__ __forceinline__ void prep_tile(const PrepJob& j, int b, int tr, int tk) {
   __shared__ float tile[32][33];
-  const int b = blockIdx.z;
-  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-  const TIn* src = in + (int64_t)b * in_stride;
-  const bool k_fast = (ks == 1);
-  // load 32 x 32 (coalesced along whichever index is contiguous in memory)
+  const int r0 = tr * 32, k0 = tk * 32;
+  const TIn* src = static_cast<const TIn*>(j.in) + (int64_t)b * j.in_stride;
+  const bool k_fast = (j.ks == 1);
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     int r, k;
     if (k_fast) { r = r0 + i; k = k0 + threadIdx.x; } else { k = k0 + i; r = r0 + threadIdx.x; }
     float v = 0.f;
-    if (r < R && k < K) {
-      if constexpr (sizeof(TIn) == 2) v = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(src + r * rs + k * ks));
-      else v = (float)src[r * rs + k * ks];
+    if (r < j.R && k < j.K) {
+      if constexpr (sizeof(TIn) == 2) v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(src)[r * j.rs + k * j.ks]);
+      else v = (float)src[r * j.rs + k * j.ks];
     }
     if (k_fast) tile[i][threadIdx.x] = v; else tile[threadIdx.x][i] = v;
   }
   __syncthreads();
-  TOut* dst = out + (int64_t)b * R * ld_out;
+  TOut* dst = static_cast<TOut*>(j.out) + (int64_t)b * j.R * j.ld_out;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int r = r0 + i, k = k0 + threadIdx.x;
-    if (r >= R || k >= Kp) continue;
+    if (r >= j.R || k >= j.Kp) continue;
     const float x = tile[i][threadIdx.x];
-    if constexpr (MODE == 0) {
+    if constexpr (!SPLIT) {
       if constexpr (sizeof(TOut) == 2) {
-        reinterpret_cast<__nv_bfloat16*>(dst)[(int64_t)r * ld_out + k] = __float2bfloat16_rn(x);
+        reinterpret_cast<__nv_bfloat16*>(dst)[(int64_t)r * j.ld_out + k] = __float2bfloat16_rn(x);
       } else {
-        dst[(int64_t)r * ld_out + k] = x;
+        dst[(int64_t)r * j.ld_out + k] = x;
       }
     } else {
       const __nv_bfloat16 hi = __float2bfloat16_rn(x);
       const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-      __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(dst) + (int64_t)r * ld_out + k;
-      for (int s = 0; s < nseg; ++s) o[(int64_t)s * Kp] = ((pattern >> s) & 1) ? lo : hi;
+      __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(dst) + (int64_t)r * j.ld_out + k;
+      for (int s = 0; s < j.nseg; ++s) o[(int64_t)s * j.Kp] = ((j.pattern >> s) & 1) ? lo : hi;
     }
   }
 }
 
-template <int BN, int STAGES, bool TF32>
-cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc::TcArgs& a, cudaStream_t s) {
+// Batched form: grid (tiles_k, tiles_r, batch).
+template <typename TIn, typename TOut, bool SPLIT>
+__global__ void prep_kernel(const PrepJob j) {
+  prep_tile<TIn, TOut, SPLIT>(j, blockIdx.z, blockIdx.y, blockIdx.x);
+}
+
+// Grouped form: one block per (job, tile); jobs sorted by block_start.
+template <typename TIn, typename TOut, bool SPLIT>
+__global__ void prep_group_kernel(const PrepJob* jobs, int n_jobs) {
+  const int blk = blockIdx.x;
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].block_start <= blk) lo = mid; else hi = mid - 1;
+  }
+  const PrepJob j = jobs[lo];
+  const int t = blk - j.block_start;
+  prep_tile<TIn, TOut, SPLIT>(j, 0, t / j.tiles_k, t % j.tiles_k);
+}
+
+cudaError_t launch_prep(int family, const PrepJob& j, int batch, cudaStream_t s) {
+  dim3 block(32, 8), grid((unsigned)j.tiles_k, (unsigned)j.tiles_r, (unsigned)batch);
+  if (family == GEMM_PREC_F32X3) prep_kernel<float, __nv_bfloat16, true><<<grid, block, 0, s>>>(j);
+  else if (family == GEMM_PREC_BF16) prep_kernel<__nv_bfloat16, __nv_bfloat16, false><<<grid, block, 0, s>>>(j);
+  else prep_kernel<float, float, false><<<grid, block, 0, s>>>(j);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_group(int family, const PrepJob* jobs, int n_jobs, int blocks, cudaStream_t s) {
+  if (n_jobs == 0) return cudaSuccess;
+  dim3 block(32, 8);
+  if (family == GEMM_PREC_F32X3) prep_group_kernel<float, __nv_bfloat16, true><<<blocks, block, 0, s>>>(jobs, n_jobs);
+  else if (family == GEMM_PREC_BF16)
+    prep_group_kernel<__nv_bfloat16, __nv_bfloat16, false><<<blocks, block, 0, s>>>(jobs, n_jobs);
+  else prep_group_kernel<float, float, false><<<blocks, block, 0, s>>>(jobs, n_jobs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- main kernel launch
+template <int BN, int STAGES, bool TF32, bool GROUPED>
+cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc::TcArgs& a, const tc::GroupArgs& g,
+                          cudaStream_t s) {
   using Cfg = tc::TcCfg<BN, STAGES, TF32>;
-  auto kern = tc::tc_gemm_kernel<BN, STAGES, TF32>;
+  auto kern = tc::tc_gemm_kernel<BN, STAGES, TF32, GROUPED>;
   static unsigned long long done_mask = 0;
-  static int occ_cache[64] = {0};
+  static int slots_cache[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
@@ -148,22 +198,22 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, tc::kThreads, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    occ = occ < 512 / Cfg::TMEM_COLS ? occ : 512 / Cfg::TMEM_COLS;  // every resident CTA must fit in TMEM
-    occ_cache[dev & 63] = (occ < 1 ? 1 : occ) * sms;
+    occ = std::min(occ, 512 / Cfg::TMEM_COLS);  // every resident CTA must fit in TMEM
+    slots_cache[dev & 63] = std::max(occ, 1) * sms;
     __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);
   }
-  const int slots = occ_cache[dev & 63];
-  const int grid = a.num_tiles < slots ? a.num_tiles : slots;
-  kern<<<grid, tc::kThreads, Cfg::SMEM_BYTES, s>>>(ma, mb, a);
+  const int grid = std::min(a.num_tiles, slots_cache[dev & 63]);
+  kern<<<grid, tc::kThreads, Cfg::SMEM_BYTES, s>>>(ma, mb, a, g);
   return cudaGetLastError();
 }
 
-using TcLaunch = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const tc::TcArgs&, cudaStream_t);
+using TcLaunch = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const tc::TcArgs&, const tc::GroupArgs&,
+                                 cudaStream_t);
 
-template <bool TF32>
+template <bool TF32, bool GROUPED>
 TcLaunch pick(int bn, int stages) {
 #define KS_TC_CASE(B, S) \
-  if (bn == B && stages == S) return &launch_kernel<B, S, TF32>;
+  if (bn == B && stages == S) return &launch_kernel<B, S, TF32, GROUPED>;
   KS_TC_CASE(64, 2) KS_TC_CASE(64, 3) KS_TC_CASE(64, 4)
   KS_TC_CASE(128, 2) KS_TC_CASE(128, 3) KS_TC_CASE(128, 4)
   KS_TC_CASE(256, 2) KS_TC_CASE(256, 3) KS_TC_CASE(256, 4)
@@ -171,11 +221,43 @@ TcLaunch pick(int bn, int stages) {
   return nullptr;
 }
 
+TcLaunch pick_launch(const TcConfig& c, bool grouped) {
+  const bool tf32 = c.family == GEMM_PREC_TF32;
+  if (grouped) return tf32 ? pick<true, true>(c.bn, c.stages) : pick<false, true>(c.bn, c.stages);
+  return tf32 ? pick<true, false>(c.bn, c.stages) : pick<false, false>(c.bn, c.stages);
+}
+
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 gemm_status_t fail(cudaError_t e) {
   set_last_cuda_error(e);
   return GEMM_ERR_CUDA;
+}
+
+// How one operand reaches the kernel: in place, or through a rewrite job.
+struct OperandPlan {
+  bool direct;
+  int64_t ld;      // leading dimension the kernel reads
+  int64_t bytes;   // scratch bytes (0 when direct)
+  PrepJob job;     // filled when !direct (out set later)
+};
+
+// Operand of logical shape R x K (rows of op(A), or columns of op(B) = rows of
+// B^T).  `kcontig` says whether it is stored R x K (K contiguous).
+OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t stride, bool kcontig, int R, int K,
+                         int batch, int pattern) {
+  const bool x3 = c.family == GEMM_PREC_F32X3;
+  const int64_t in_elem = c.family == GEMM_PREC_BF16 ? 2 : 4;
+  const int64_t op_elem = c.family == GEMM_PREC_TF32 ? 4 : 2;
+  OperandPlan o;
+  o.direct = !x3 && kcontig && ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0);
+  const int nseg = x3 ? 3 : 1;
+  const int64_t Kp = x3 ? round_up(K, 64) : round_up(K, 16 / op_elem);
+  o.ld = o.direct ? ld : nseg * Kp;
+  o.bytes = o.direct ? 0 : (int64_t)batch * R * o.ld * op_elem;
+  o.job = PrepJob{ptr, stride, kcontig ? ld : 1, kcontig ? 1 : ld, nullptr, o.ld, R, K, (int)Kp, nseg, pattern,
+                  (int)((Kp + 31) / 32), (R + 31) / 32, 0};
+  return o;
 }
 
 }  // namespace
@@ -197,67 +279,38 @@ gemm_status_t tc_params(int id, int32_t out[8]) {
 gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
   TcConfig c;
   if (!decode(id, &c)) return GEMM_ERR_NO_KERNEL;
-  const bool tf32 = (c.family == GEMM_PREC_TF32);
-  const bool x3 = (c.family == GEMM_PREC_F32X3);
-  const bool in_bf16 = (c.family == GEMM_PREC_BF16);
-  const bool op_bf16 = !tf32;  // element type the tensor core reads
-  const int64_t in_elem = in_bf16 ? 2 : 4, op_elem = op_bf16 ? 2 : 4;
-  TcLaunch fn = tf32 ? pick<true>(c.bn, c.stages) : pick<false>(c.bn, c.stages);
+  const bool op_bf16 = c.family != GEMM_PREC_TF32;
+  TcLaunch fn = pick_launch(c, false);
   if (!fn) return GEMM_ERR_NO_KERNEL;
   if (!encode_fn()) return GEMM_ERR_UNSUPPORTED;
   int* status = status_word();
   if (!status) return fail(cudaGetLastError());
 
-  // Operand layout: A as (batch, M, K) K-contiguous, B as (batch, N, K).
-  const int per16 = (int)(16 / in_elem);
-  const bool a_direct = !x3 && !g.transA && ((uintptr_t)g.A % 16 == 0) && (g.lda % per16 == 0);
-  const bool b_direct = !x3 && g.transB && ((uintptr_t)g.B % 16 == 0) && (g.ldb % per16 == 0);
-  const int nseg = x3 ? 3 : 1;
-  const int64_t Kp = x3 ? round_up(g.K, 64) : round_up(g.K, 16 / op_elem);
-  const int64_t ldA = a_direct ? g.lda : nseg * Kp, ldB = b_direct ? g.ldb : nseg * Kp;
-  const int64_t bytesA = a_direct ? 0 : (int64_t)g.batch * g.M * ldA * op_elem;
-  const int64_t bytesB = b_direct ? 0 : (int64_t)g.batch * g.N * ldB * op_elem;
+  // op(A) rows are M, stored M x K when transA = 0; op(B)^T rows are N, stored N x K when transB = 1.
+  OperandPlan pa = plan_operand(c, g.A, g.lda, g.strideA, !g.transA, g.M, g.K, g.batch, /*hi,hi,lo*/ 0b100);
+  OperandPlan pb = plan_operand(c, g.B, g.ldb, g.strideB, g.transB != 0, g.N, g.K, g.batch, /*hi,lo,hi*/ 0b010);
   char* scratch = nullptr;
-  if (bytesA + bytesB > 0) {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytesA + bytesB + 256, s);
+  if (pa.bytes + pb.bytes > 0) {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), pa.bytes + pb.bytes + 256, s);
     if (e != cudaSuccess) return fail(e);
   }
-  const void* Aop = a_direct ? g.A : scratch;
-  const void* Bop = b_direct ? g.B : scratch + round_up(bytesA, 256);
+  const void* Aop = pa.direct ? g.A : scratch;
+  const void* Bop = pb.direct ? g.B : scratch + round_up(pa.bytes, 256);
   cudaError_t e = cudaSuccess;
-  auto prep = [&](const void* in, int64_t in_stride, int trans, int64_t ld, int R, void* out, int64_t ld_out,
-                  int pattern) {
-    // element (r, k) of the logical R x K operand: stored R x K (trans 0) or K x R (trans 1)
-    const int64_t rs = trans ? 1 : ld, kst = trans ? ld : 1;
-    dim3 block(32, 8), grid((unsigned)((Kp + 31) / 32), (unsigned)((R + 31) / 32), (unsigned)g.batch);
-    if (x3) {
-      kmajor_kernel<float, __nv_bfloat16, 1><<<grid, block, 0, s>>>(
-          static_cast<const float*>(in), in_stride, rs, kst, R, g.K, (int)Kp, nseg, pattern,
-          static_cast<__nv_bfloat16*>(out), ld_out);
-    } else if (in_bf16) {
-      kmajor_kernel<__nv_bfloat16, __nv_bfloat16, 0><<<grid, block, 0, s>>>(
-          static_cast<const __nv_bfloat16*>(in), in_stride, rs, kst, R, g.K, (int)Kp, 1, 0,
-          static_cast<__nv_bfloat16*>(out), ld_out);
-    } else {
-      kmajor_kernel<float, float, 0><<<grid, block, 0, s>>>(static_cast<const float*>(in), in_stride, rs, kst, R,
-                                                             g.K, (int)Kp, 1, 0, static_cast<float*>(out), ld_out);
-    }
-    return cudaGetLastError();
-  };
-  // op(A) rows are M: stored M x K when transA = 0.  op(B)^T rows are N: B is
-  // stored N x K when transB = 1, i.e. "transposed" relative to (N, K) when 0.
-  if (!a_direct) e = prep(g.A, g.strideA, g.transA, g.lda, g.M, const_cast<void*>(Aop), ldA, /*hi,hi,lo*/ 0b100);
-  if (e == cudaSuccess && !b_direct)
-    e = prep(g.B, g.strideB, g.transB ? 0 : 1, g.ldb, g.N, const_cast<void*>(Bop), ldB, /*hi,lo,hi*/ 0b010);
-  gemm_status_t st = GEMM_OK;
-  if (e != cudaSuccess) st = fail(e);
-  const int64_t Kop = x3 ? 3 * Kp : g.K;
-  CUtensorMap ma, mb;
-  if (st == GEMM_OK) {
-    if (!make_map(&ma, Aop, op_bf16, Kop, g.M, ldA, g.batch, tc::kBM) ||
-        !make_map(&mb, Bop, op_bf16, Kop, g.N, ldB, g.batch, c.bn))
-      st = GEMM_ERR_MISALIGNED;
+  if (!pa.direct) {
+    pa.job.out = const_cast<void*>(Aop);
+    e = launch_prep(c.family, pa.job, g.batch, s);
   }
+  if (e == cudaSuccess && !pb.direct) {
+    pb.job.out = const_cast<void*>(Bop);
+    e = launch_prep(c.family, pb.job, g.batch, s);
+  }
+  gemm_status_t st = e == cudaSuccess ? GEMM_OK : fail(e);
+  const int64_t Kop = c.family == GEMM_PREC_F32X3 ? 3 * round_up(g.K, 64) : g.K;
+  CUtensorMap ma, mb;
+  if (st == GEMM_OK && (!make_map(&ma, Aop, op_bf16, Kop, g.M, pa.ld, g.batch, tc::kBM) ||
+                        !make_map(&mb, Bop, op_bf16, Kop, g.N, pb.ld, g.batch, c.bn)))
+    st = GEMM_ERR_MISALIGNED;
   if (st == GEMM_OK) {
     tc::TcArgs a;
     a.M = g.M; a.N = g.N; a.K = (int)Kop; a.batch = g.batch;
@@ -269,7 +322,8 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
     a.alpha = g.alpha; a.beta = g.beta;
     a.C = g.C; a.ldc = g.ldc; a.strideC = g.strideC; a.vecC = g.vecC;
     a.status = status;
-    e = fn(ma, mb, a, s);
+    tc::GroupArgs none{nullptr, 0};
+    e = fn(ma, mb, a, none, s);
     if (e != cudaSuccess) st = fail(e);
   }
   if (scratch) cudaFreeAsync(scratch, s);
@@ -278,15 +332,176 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
 
 }  // namespace ks
 
-extern "C" gemm_status_t gemm_device_status(int32_t* out_status, int32_t clear) {
+// ------------------------------------------------------------------ grouped plans
+struct kselect_grouped_plan {
+  ks::TcConfig cfg;
+  int count = 0, total_tiles = 0, n_jobs = 0, prep_blocks = 0;
+  ks::tc::GroupDesc* descs = nullptr;  // device
+  ks::PrepJob* jobs = nullptr;          // device
+  char* scratch = nullptr;              // device
+  int device = 0;
+};
+
+namespace {
+void plan_free(kselect_grouped_plan* p) {
+  if (!p) return;
+  if (p->descs) cudaFree(p->descs);
+  if (p->jobs) cudaFree(p->jobs);
+  if (p->scratch) cudaFree(p->scratch);
+  delete p;
+}
+}  // namespace
+
+using namespace ks;
+
+extern "C" {
+
+gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_problem_t* probs, void* stream,
+                                       gemm_grouped_plan_t* out) {
+  if (!out) return GEMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  TcConfig c;
+  if (!decode(id, &c)) return GEMM_ERR_NO_KERNEL;
+  if (count < 1 || !probs) return GEMM_ERR_INVALID_ARG;
+  if (!encode_fn()) return GEMM_ERR_UNSUPPORTED;
+  if (!status_word()) return fail(cudaGetLastError());  // made now, so that runs never allocate
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool op_bf16 = c.family != GEMM_PREC_TF32;
+  const int64_t op_elem = op_bf16 ? 2 : 4;
+  std::vector<tc::GroupDesc> descs(count);
+  std::vector<PrepJob> jobs;
+  std::vector<OperandPlan> pa(count), pb(count);
+  int64_t scratch_bytes = 0, tiles = 0;
+  std::vector<int64_t> offA(count, -1), offB(count, -1);
+  for (int i = 0; i < count; ++i) {
+    const gemm_problem_t& q = probs[i];
+    int ta, tb;
+    auto tr = [](char t, int* o) {
+      if (t == 'N' || t == 'n') { *o = 0; return true; }
+      if (t == 'T' || t == 't') { *o = 1; return true; }
+      return false;
+    };
+    if (!tr(q.transA, &ta) || !tr(q.transB, &tb)) return GEMM_ERR_INVALID_ARG;
+    if (q.M < 0 || q.N < 0 || q.K < 1 || q.M >= (1ll << 31) || q.N >= (1ll << 31) || q.K >= (1ll << 31))
+      return GEMM_ERR_INVALID_ARG;
+    if (!q.A || !q.B || !q.C || q.ldc < q.N) return GEMM_ERR_INVALID_ARG;
+    if (q.lda < (ta ? q.M : q.K) || q.ldb < (tb ? q.K : q.N)) return GEMM_ERR_INVALID_ARG;
+    pa[i] = plan_operand(c, q.A, q.lda, 0, !ta, (int)q.M, (int)q.K, 1, 0b100);
+    pb[i] = plan_operand(c, q.B, q.ldb, 0, tb != 0, (int)q.N, (int)q.K, 1, 0b010);
+    if (!pa[i].direct) { offA[i] = scratch_bytes; scratch_bytes += round_up(pa[i].bytes, 256); }
+    if (!pb[i].direct) { offB[i] = scratch_bytes; scratch_bytes += round_up(pb[i].bytes, 256); }
+    const int tm = (int)((q.M + tc::kBM - 1) / tc::kBM), tn = (int)((q.N + c.bn - 1) / c.bn);
+    tiles += (int64_t)tm * tn;
+    if (tiles >= (1ll << 31)) return GEMM_ERR_UNSUPPORTED;
+  }
+  kselect_grouped_plan* p = new (std::nothrow) kselect_grouped_plan();
+  if (!p) return GEMM_ERR_UNSUPPORTED;
+  p->cfg = c;
+  p->count = count;
+  cudaGetDevice(&p->device);
+  cudaError_t e = cudaSuccess;
+  if (scratch_bytes > 0) e = cudaMalloc(reinterpret_cast<void**>(&p->scratch), scratch_bytes);
+  if (e != cudaSuccess) { plan_free(p); return fail(e); }
+  int tile_start = 0, blocks = 0;
+  for (int i = 0; i < count; ++i) {
+    const gemm_problem_t& q = probs[i];
+    const void* Aop = pa[i].direct ? q.A : p->scratch + offA[i];
+    const void* Bop = pb[i].direct ? q.B : p->scratch + offB[i];
+    if (!pa[i].direct) {
+      pa[i].job.out = const_cast<void*>(Aop);
+      pa[i].job.block_start = blocks;
+      blocks += pa[i].job.tiles_k * pa[i].job.tiles_r;
+      jobs.push_back(pa[i].job);
+    }
+    if (!pb[i].direct) {
+      pb[i].job.out = const_cast<void*>(Bop);
+      pb[i].job.block_start = blocks;
+      blocks += pb[i].job.tiles_k * pb[i].job.tiles_r;
+      jobs.push_back(pb[i].job);
+    }
+    const int64_t Kop = c.family == GEMM_PREC_F32X3 ? 3 * round_up(q.K, 64) : q.K;
+    tc::GroupDesc& d = descs[i];
+    std::memset(&d, 0, sizeof(d));
+    if (!make_map(&d.tmA, Aop, op_bf16, Kop, q.M > 0 ? q.M : 1, pa[i].ld, 1, tc::kBM) ||
+        !make_map(&d.tmB, Bop, op_bf16, Kop, q.N > 0 ? q.N : 1, pb[i].ld, 1, c.bn)) {
+      plan_free(p);
+      return GEMM_ERR_MISALIGNED;
+    }
+    d.C = q.C;
+    d.ldc = q.ldc;
+    d.M = (int)q.M;
+    d.N = (int)q.N;
+    d.k_blocks = (int)((Kop * op_elem + 127) / 128);
+    d.tiles_m = (int)((q.M + tc::kBM - 1) / tc::kBM);
+    d.tiles_n = (int)((q.N + c.bn - 1) / c.bn);
+    d.tile_start = tile_start;
+    d.vecC = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0);
+    d.alpha = q.alpha;
+    d.beta = q.beta;
+    tile_start += d.tiles_m * d.tiles_n;
+  }
+  p->total_tiles = tile_start;
+  p->n_jobs = (int)jobs.size();
+  p->prep_blocks = blocks;
+  e = cudaMalloc(reinterpret_cast<void**>(&p->descs), sizeof(tc::GroupDesc) * count);
+  if (e == cudaSuccess && !jobs.empty()) e = cudaMalloc(reinterpret_cast<void**>(&p->jobs), sizeof(PrepJob) * jobs.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->descs, descs.data(), sizeof(tc::GroupDesc) * count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !jobs.empty())
+    e = cudaMemcpyAsync(p->jobs, jobs.data(), sizeof(PrepJob) * jobs.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { plan_free(p); return fail(e); }
+  *out = p;
+  return GEMM_OK;
+}
+
+gemm_status_t gemm_grouped_run(gemm_grouped_plan_t p, void* stream) {
+  if (!p) return GEMM_ERR_INVALID_ARG;
+  if (p->total_tiles == 0) return GEMM_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* status = status_word();
+  if (!status) return fail(cudaGetLastError());
+  cudaError_t e = launch_prep_group(p->cfg.family, p->jobs, p->n_jobs, p->prep_blocks, s);
+  if (e != cudaSuccess) return fail(e);
+  TcLaunch fn = pick_launch(p->cfg, true);
+  if (!fn) return GEMM_ERR_NO_KERNEL;
+  tc::TcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.num_tiles = p->total_tiles;
+  a.raster = p->cfg.raster;
+  a.status = status;
+  tc::GroupArgs g{p->descs, p->count};
+  CUtensorMap dummy;
+  std::memset(&dummy, 0, sizeof(dummy));
+  e = fn(dummy, dummy, a, g, s);
+  return e == cudaSuccess ? GEMM_OK : fail(e);
+}
+
+void gemm_grouped_plan_destroy(gemm_grouped_plan_t p) { plan_free(p); }
+
+gemm_status_t gemm_grouped(int32_t id, int32_t count, const gemm_problem_t* probs, void* stream) {
+  gemm_grouped_plan_t p = nullptr;
+  gemm_status_t st = gemm_grouped_plan_create(id, count, probs, stream, &p);
+  if (st != GEMM_OK) return st;
+  st = gemm_grouped_run(p, stream);
+  // The plan's device buffers are released once the launch has finished.
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  plan_free(p);
+  if (st == GEMM_OK && e != cudaSuccess) st = fail(e);
+  return st;
+}
+
+gemm_status_t gemm_device_status(int32_t* out_status, int32_t clear) {
   if (!out_status) return GEMM_ERR_INVALID_ARG;
-  int* w = ks::status_word();
-  if (!w) return ks::fail(cudaGetLastError());
+  int* w = status_word();
+  if (!w) return fail(cudaGetLastError());
   int v = 0;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && clear) e = cudaMemset(w, 0, sizeof(int));
-  if (e != cudaSuccess) return ks::fail(e);
+  if (e != cudaSuccess) return fail(e);
   *out_status = v;
   return v == 0 ? GEMM_OK : GEMM_ERR_TIMEOUT;
 }
+
+}  // extern "C"

@@ -10,7 +10,10 @@
 //   warps 0..3  : epilogue, tcgen05.ld of their 32-lane quadrant, alpha/beta,
 //                 vector stores of C.
 // Two TMEM accumulators (2 x BN columns) let the epilogue of tile i overlap
-// the MMAs of tile i+1.
+// the MMAs of tile i+1.  With GROUPED, the launch covers an uneven group of
+// problems: the global tile index is mapped to (problem, tile) by binary
+// search over the problems' first-tile offsets, and each problem brings its
+// own tensor maps, C and K.
 #pragma once
 #include "common.cuh"
 #include "tc_ptx.cuh"
@@ -27,6 +30,22 @@ struct TcArgs {
   int64_t ldc, strideC;
   int vecC;
   int* status;
+};
+
+// One problem of a grouped launch, in device memory: its two tensor maps
+// (64-byte aligned, as TMA requires), its C, and its first global tile index.
+struct alignas(64) GroupDesc {
+  CUtensorMap tmA;
+  CUtensorMap tmB;
+  float* C;
+  int64_t ldc;
+  int M, N, k_blocks, tiles_m, tiles_n, tile_start, vecC;
+  float alpha, beta;
+};
+
+struct GroupArgs {
+  const GroupDesc* descs;
+  int count;  // problems; descs[i].tile_start is ascending
 };
 
 constexpr int kThreads = 192;
@@ -57,7 +76,41 @@ __device__ __forceinline__ void tile_coords(const TcArgs& p, int tile, int& b, i
   }
 }
 
-__device__ __forceinline__ void store_row32(const TcArgs& p, float* crow, int n0, const uint32_t (&r)[32]) {
+// Where tile `tile` of the launch lives: operand maps, C and its geometry.
+struct TileLoc {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  float* C;
+  int64_t ldc, strideC;
+  int M, N, k_blocks, b, tm, tn, vecC;
+  float alpha, beta;
+};
+
+template <bool GROUPED>
+__device__ __forceinline__ TileLoc locate(const TcArgs& p, const GroupArgs& g, const CUtensorMap* ma,
+                                          const CUtensorMap* mb, int tile) {
+  TileLoc L;
+  if constexpr (GROUPED) {
+    int lo = 0, hi = g.count - 1;  // last problem whose tile_start <= tile
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (g.descs[mid].tile_start <= tile) lo = mid; else hi = mid - 1;
+    }
+    const GroupDesc& d = g.descs[lo];
+    const int t = tile - d.tile_start;
+    L.ma = &d.tmA; L.mb = &d.tmB; L.C = d.C; L.ldc = d.ldc; L.strideC = 0;
+    L.M = d.M; L.N = d.N; L.k_blocks = d.k_blocks; L.b = 0; L.vecC = d.vecC;
+    L.alpha = d.alpha; L.beta = d.beta;
+    if (p.raster == 0) { L.tm = t % d.tiles_m; L.tn = t / d.tiles_m; } else { L.tn = t % d.tiles_n; L.tm = t / d.tiles_n; }
+  } else {
+    L.ma = ma; L.mb = mb; L.C = p.C; L.ldc = p.ldc; L.strideC = p.strideC;
+    L.M = p.M; L.N = p.N; L.k_blocks = p.k_blocks; L.vecC = p.vecC; L.alpha = p.alpha; L.beta = p.beta;
+    tile_coords(p, tile, L.b, L.tm, L.tn);
+  }
+  return L;
+}
+
+__device__ __forceinline__ void store_row32(const TileLoc& p, float* crow, int n0, const uint32_t (&r)[32]) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int n = n0 + 4 * q;
@@ -84,9 +137,10 @@ __device__ __forceinline__ void store_row32(const TcArgs& p, float* crow, int n0
   }
 }
 
-template <int BN, int STAGES, bool TF32>
+template <int BN, int STAGES, bool TF32, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs p) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs p,
+                   const GroupArgs g) {
   using Cfg = TcCfg<BN, STAGES, TF32>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
@@ -105,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     fence_barrier_init();
   }
-  if (warp == 4 && lane == 0) {
+  if (!GROUPED && warp == 4 && lane == 0) {
     tma_prefetch(&tmA);
     tma_prefetch(&tmB);
   }
@@ -122,14 +176,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
-        int b, tm, tn;
-        tile_coords(p, tile, b, tm, tn);
-        for (int kb = 0; kb < p.k_blocks; ++kb) {
+        const TileLoc L = locate<GROUPED>(p, g, &tmA, &tmB, tile);
+        for (int kb = 0; kb < L.k_blocks; ++kb) {
           if (!(ok = mbar_wait(&empty_bar[stage], phase ^ 1, p.status, kStatusTimeoutEmpty))) break;
           uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
           mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
-          tma_load_3d(sa, &tmA, &full_bar[stage], kb * Cfg::BK, tm * kBM, b);
-          tma_load_3d(sa + Cfg::A_BYTES, &tmB, &full_bar[stage], kb * Cfg::BK, tn * BN, b);
+          tma_load_3d(sa, L.ma, &full_bar[stage], kb * Cfg::BK, L.tm * kBM, L.b);
+          tma_load_3d(sa + Cfg::A_BYTES, L.mb, &full_bar[stage], kb * Cfg::BK, L.tn * BN, L.b);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1;
@@ -157,10 +210,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t acc_phase = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
+        const int k_blocks = GROUPED ? locate<true>(p, g, &tmA, &tmB, tile).k_blocks : p.k_blocks;
         if (!(ok = mbar_wait(&acce_bar[acc], acc_phase ^ 1, p.status, kStatusTimeoutAccEmpty))) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-        for (int kb = 0; kb < p.k_blocks; ++kb) {
+        for (int kb = 0; kb < k_blocks; ++kb) {
           if (!(ok = mbar_wait(&full_bar[stage], phase, p.status, kStatusTimeoutFull))) break;
           tc_fence_after();
           const uint32_t a_addr = smem_u32(smem + stage * Cfg::STAGE_BYTES);
@@ -193,17 +247,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
       if (!mbar_wait(&accf_bar[acc], acc_phase, p.status, kStatusTimeoutAcc)) break;
       tc_fence_after();
-      int b, tm, tn;
-      tile_coords(p, tile, b, tm, tn);
-      const int row = tm * kBM + warp * 32 + lane;
-      float* crow = p.C + (int64_t)b * p.strideC + (int64_t)row * p.ldc;
+      const TileLoc L = locate<GROUPED>(p, g, &tmA, &tmB, tile);
+      const int row = L.tm * kBM + warp * 32 + lane;
+      float* crow = L.C + (int64_t)L.b * L.strideC + (int64_t)row * L.ldc;
       const uint32_t tbase = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
         tmem_ld_32x32b_x32(tbase + (uint32_t)c0, r);
         tmem_ld_wait();
-        if (row < p.M && tn * BN + c0 < p.N) store_row32(p, crow, tn * BN + c0, r);
+        if (row < L.M && L.tn * BN + c0 < L.N) store_row32(L, crow, L.tn * BN + c0, r);
       }
       tc_fence_before();
       mbar_arrive(&acce_bar[acc]);

@@ -34,6 +34,11 @@ class TreeNode(ctypes.Structure):
     _fields_ = [("feature", i32), ("left", i32), ("right", i32), ("label", i32), ("threshold", f64)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("M", i64), ("N", i64), ("K", i64), ("transA", ch), ("transB", ch), ("alpha", f32), ("beta", f32),
+                ("A", vp), ("lda", i64), ("B", vp), ("ldb", i64), ("C", vp), ("ldc", i64)]
+
+
 class Deployment(ctypes.Structure):
     _fields_ = [("precision", i32), ("n_configs", i32), ("config_ids", ctypes.POINTER(i32)),
                 ("n_nodes", i32), ("nodes", ctypes.POINTER(TreeNode)), ("mlp_params", ctypes.POINTER(f32))]
@@ -63,6 +68,10 @@ _sig("gemm_benchmark", i32, [i32, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i
 _sig("gemm_error_check", i32, [i64, i64, i64, vp, i64, i64, i64, vp, vp, vp, ctypes.POINTER(f64), vp])
 _sig("kselect_fill_uniform", i32, [vp, i64, i64, i64, i64, u64, f32, f32, f32, vp])
 _sig("gemm_device_status", i32, [ctypes.POINTER(i32), i32])
+_sig("gemm_grouped_plan_create", i32, [i32, i32, ctypes.POINTER(Problem), vp, ctypes.POINTER(vp)])
+_sig("gemm_grouped_run", i32, [vp, vp])
+_sig("gemm_grouped_plan_destroy", None, [vp])
+_sig("gemm_grouped", i32, [i32, i32, ctypes.POINTER(Problem), vp])
 _sig("mlp_forward", i32, [i32, vp, vp, vp, vp])
 _sig("mlp_loss_grad", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
 _sig("mlp_adam_step", i32, [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp])
@@ -322,6 +331,47 @@ def tree_train(features: np.ndarray, labels: np.ndarray, n_classes: int, max_dep
              "right": nodes[j].right, "label": nodes[j].label} for j in range(cnt.value)]
 
 
+# ---------------------------------------------------------------- grouped GEMM
+def _problems(problems):
+    """problems: iterable of dicts with M, N, K, transA, transB, alpha, beta, A, lda, B, ldb, C, ldc."""
+    arr = (Problem * len(problems))()
+    for i, q in enumerate(problems):
+        arr[i] = Problem(q["M"], q["N"], q["K"], _c(q.get("transA", "N")), _c(q.get("transB", "T")),
+                         q.get("alpha", 1.0), q.get("beta", 0.0), ptr(q["A"]), q["lda"], ptr(q["B"]), q["ldb"],
+                         ptr(q["C"]), q["ldc"])
+    return arr
+
+
+class GroupedPlan:
+    """A validated group with device-resident descriptors; run() only launches (graph-capturable)."""
+
+    def __init__(self, cid: int, problems, stream=None):
+        self._arr = _problems(problems)
+        h = vp()
+        check(_lib.gemm_grouped_plan_create(cid, len(problems), self._arr, stream_handle(stream), ctypes.byref(h)),
+              "gemm_grouped_plan_create")
+        self.value = h.value
+
+    def run(self, stream=None) -> None:
+        check(_lib.gemm_grouped_run(self.value, stream_handle(stream)), "gemm_grouped_run")
+
+    def close(self):
+        if self.value:
+            _lib.gemm_grouped_plan_destroy(self.value)
+            self.value = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_grouped(cid: int, problems, stream=None) -> None:
+    arr = _problems(problems)
+    check(_lib.gemm_grouped(cid, len(problems), arr, stream_handle(stream)), "gemm_grouped")
+
+
 # ---------------------------------------------------------------- learned selector
 def mlp_forward(params, X, Y, stream=None) -> None:
     check(_lib.mlp_forward(X.shape[0], ptr(params), ptr(X), ptr(Y), stream_handle(stream)), "mlp_forward")
@@ -356,4 +406,5 @@ def exported_symbols() -> list[str]:
             "gemm_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
             "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
             "kselect_representatives", "kselect_top_n", "kselect_tree_train", "mlp_forward", "mlp_loss_grad",
-            "mlp_adam_step", "mlp_train", "select_kernels_batched"]
+            "mlp_adam_step", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
+            "gemm_grouped_plan_destroy", "gemm_grouped"]
