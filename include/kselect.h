@@ -279,6 +279,10 @@ gemm_status_t kselect_tree_train(int32_t n, const double* features, const int32_
  * X_dev is n x 7 FP32 features, T_dev n x 8 targets, mask_dev n x 8 (1 =
  * measured) or NULL for all measured.  All arrays are device, row-major. */
 
+/* X_dev (n x 7) = features of the n GEMMs in shapes_dev (rows of 7 int64:
+ * M, N, K, batch, transA, transB, dtype), as select_kernels_batched computes them. */
+gemm_status_t mlp_features(int32_t n, const int64_t* shapes_dev, float* X_dev, void* stream);
+
 /* Y_dev (n x 8) = network(X_dev). */
 gemm_status_t mlp_forward(int32_t n, const float* params_dev, const float* X_dev, float* Y_dev, void* stream);
 

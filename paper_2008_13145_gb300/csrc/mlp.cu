@@ -194,6 +194,13 @@ __device__ __forceinline__ float feature(int q, const int64_t* sh) {
   }
 }
 
+__global__ void mlp_features_kernel(int n, const int64_t* shapes, float* X) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+#pragma unroll
+  for (int q = 0; q < NI; ++q) X[(int64_t)r * NI + q] = feature(q, shapes + (int64_t)r * 7);
+}
+
 // One thread per row: y = network(x); optionally pick argmax over the first n_out outputs.
 template <bool FROM_SHAPES>
 __global__ void __launch_bounds__(128) mlp_forward_kernel(int n, const float* Pg, const float* X, const int64_t* shapes,
@@ -297,6 +304,14 @@ using namespace ks;
 using namespace ks::mlp;
 
 extern "C" {
+
+gemm_status_t mlp_features(int32_t n, const int64_t* shapes, float* X, void* stream) {
+  if (n < 0 || (n > 0 && (!shapes || !X))) return GEMM_ERR_INVALID_ARG;
+  if (n == 0) return GEMM_OK;
+  mlp_features_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(n, shapes, X);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GEMM_OK : fail(e);
+}
 
 gemm_status_t mlp_forward(int32_t n, const float* P, const float* X, float* Y, void* stream) {
   if (n < 0 || (n > 0 && (!P || !X || !Y))) return GEMM_ERR_INVALID_ARG;

@@ -72,6 +72,7 @@ _sig("gemm_grouped_plan_create", i32, [i32, i32, ctypes.POINTER(Problem), vp, ct
 _sig("gemm_grouped_run", i32, [vp, vp])
 _sig("gemm_grouped_plan_destroy", None, [vp])
 _sig("gemm_grouped", i32, [i32, i32, ctypes.POINTER(Problem), vp])
+_sig("mlp_features", i32, [i32, vp, vp, vp])
 _sig("mlp_forward", i32, [i32, vp, vp, vp, vp])
 _sig("mlp_loss_grad", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
 _sig("mlp_adam_step", i32, [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp])
@@ -142,6 +143,10 @@ def config_id(precision: int, index: int) -> int:
 
 def config_ids(precision: int) -> list[int]:
     return [config_id(precision, i) for i in range(config_count(precision))]
+
+
+def family_of(cid: int) -> int:
+    return config_params(cid)[0]
 
 
 def config_params(cid: int) -> list[int]:
@@ -373,6 +378,10 @@ def gemm_grouped(cid: int, problems, stream=None) -> None:
 
 
 # ---------------------------------------------------------------- learned selector
+def mlp_features(shapes, X, stream=None) -> None:
+    check(_lib.mlp_features(shapes.shape[0], ptr(shapes), ptr(X), stream_handle(stream)), "mlp_features")
+
+
 def mlp_forward(params, X, Y, stream=None) -> None:
     check(_lib.mlp_forward(X.shape[0], ptr(params), ptr(X), ptr(Y), stream_handle(stream)), "mlp_forward")
 
@@ -405,6 +414,6 @@ def exported_symbols() -> list[str]:
             "gemm_config_params", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
             "gemm_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
             "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
-            "kselect_representatives", "kselect_top_n", "kselect_tree_train", "mlp_forward", "mlp_loss_grad",
+            "kselect_representatives", "kselect_top_n", "kselect_tree_train", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
             "gemm_grouped_plan_destroy", "gemm_grouped"]

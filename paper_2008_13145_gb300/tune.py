@@ -189,6 +189,96 @@ def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard"
     return dep
 
 
+# ---------------------------------------------------------------- learned selector
+def shape_rows(shapes, dtype: int = 0) -> np.ndarray:
+    return np.array([[s.M, s.N, s.K, s.batch, s.transA == "T", s.transB == "T", dtype] for s in shapes], np.int64)
+
+
+def mlp_features(shapes, dtype: int = 0):
+    """Model inputs (device, n x 7), computed by the library's feature kernel."""
+    import torch
+    ks = _ks()
+    sh = torch.from_numpy(shape_rows(shapes, dtype)).cuda()
+    X = torch.empty((len(shapes), 7), device="cuda")
+    ks.mlp_features(sh, X)
+    return X
+
+
+def mlp_targets(perf: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Natural-log GFLOP/s per deployed kernel and the mask of measured entries."""
+    mask = (perf > 0).astype(np.float32)
+    t = np.where(perf > 0, np.log(np.maximum(perf, 1e-30)), 0.0).astype(np.float32)
+    return t, mask
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """He-uniform weights from seeded draws (the draws are the model's input), zero biases."""
+    from . import kselect as ks
+    u = wl.rng_for(seed, 41).random(ks.MLP_PARAMS)
+    sizes = [(7, 64), (64,), (64, 64), (64,), (64, 8), (8,)]
+    out, o = [], 0
+    for sz in sizes:
+        n = int(np.prod(sz))
+        out.append((2 * u[o:o + n] - 1) * np.sqrt(6.0 / sz[0]) if len(sz) == 2 else np.zeros(n))
+        o += n
+    return np.concatenate(out).astype(np.float32)
+
+
+def mlp_train_params(X, T, mask, steps=3000, lr=3e-3, seed=0, log=None) -> tuple[np.ndarray, list]:
+    """Full-batch Adam training by the library's kernels; returns (params, loss history)."""
+    import torch
+    ks = _ks()
+    P = torch.from_numpy(mlp_init(seed)).cuda()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    hist = torch.empty(steps, device="cuda")
+    Xd = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+    Td, Md = (torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in (T, mask))
+    ks.mlp_train(P, Xd, Td, Md, m, v, 0, steps, lr=lr, loss_hist=hist)
+    h = hist.cpu().numpy().tolist()
+    return P.cpu().numpy(), h
+
+
+def mlp_choose(params: np.ndarray, shapes, config_ids) -> np.ndarray:
+    """Config ids the batched selection kernel picks for these shapes."""
+    import torch
+    ks = _ks()
+    h = ks.Handle({"precision": ks.family_of(config_ids[0]), "config_ids": config_ids, "nodes": [],
+                   "mlp_params": params})
+    sh = torch.from_numpy(shape_rows(shapes)).cuda()
+    out = torch.empty(len(shapes), dtype=torch.int32, device="cuda")
+    ks.select_kernels_batched(h, sh, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def mlp_study(deploy_path: str, sweep_path: str, n: int = 2500, seed: int = 4, steps: int = 3000) -> dict:
+    """Learned selector over the deployed set: sweep n seed-`seed` shapes over
+    the deployed kernels, train on 80 %, compare MLP, tree and exhaustive on
+    the held-out 20 % (fractions of the best deployed kernel)."""
+    import torch
+    ks = _ks()
+    dep = json.load(open(deploy_path))
+    ids = dep["config_ids"]
+    shapes = wl.shape_grid(n, seed)
+    perf = sweep(shapes, dep["precision"], sweep_path, config_ids=ids)
+    tr, te = wl.train_test_split(n, seed)
+    X = mlp_features([shapes[i] for i in tr])
+    T, M = mlp_targets(perf)
+    params, hist = mlp_train_params(X, T[tr], M[tr], steps=steps)
+    te_shapes = [shapes[i] for i in te]
+    col = {c: j for j, c in enumerate(ids)}
+    mlp_cols = np.array([col[c] for c in mlp_choose(params, te_shapes, ids)], np.int32)
+    h = ks.Handle(dep)
+    tree_cols = np.array([col[ks.select_kernel(h, s.M, s.N, s.K, s.batch)] for s in te_shapes], np.int32)
+    P = torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda()
+    res = {"n_train": len(tr), "n_test": len(te), "loss_first": hist[0], "loss_last": hist[-1],
+           "mlp": ks.score(P, chosen=torch.from_numpy(mlp_cols).cuda()),
+           "tree": ks.score(P, chosen=torch.from_numpy(tree_cols).cuda()),
+           "exhaustive_deployed": ks.score(P)}
+    return {"params": params.tolist(), "study": res}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -198,6 +288,12 @@ def main(argv=None):
     s.add_argument("--seed", type=int, default=1)
     s.add_argument("--out", required=True)
     s.add_argument("--table", default=None)
+    ml = sub.add_parser("mlp")
+    ml.add_argument("--deploy", required=True)
+    ml.add_argument("--sweep", required=True)
+    ml.add_argument("--n", type=int, default=2500)
+    ml.add_argument("--steps", type=int, default=3000)
+    ml.add_argument("--out", required=True)
     d = sub.add_parser("deploy")
     d.add_argument("--table", required=True)
     d.add_argument("--k", type=int, default=8)
@@ -207,6 +303,15 @@ def main(argv=None):
     d.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     ks = _ks()
+    if a.cmd == "mlp":
+        r = mlp_study(a.deploy, a.sweep, a.n, steps=a.steps)
+        dep = json.load(open(a.deploy))
+        dep["mlp_params"] = r["params"]
+        dep.setdefault("meta", {})["mlp_study"] = r["study"]
+        with open(a.out, "w") as f:
+            json.dump(dep, f, indent=1)
+        print(json.dumps(r["study"], indent=1))
+        return
     if a.cmd == "sweep":
         prec = ks.PRECISIONS[a.precision]
         shapes = wl.shape_grid(a.n, a.seed)

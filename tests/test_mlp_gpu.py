@@ -122,3 +122,11 @@ def test_batched_selection(lib, torch):
     got = out.cpu().numpy()
     assert np.array_equal(got[clear], np.array(ids)[pick[clear]])
     assert set(got.tolist()) <= set(ids)
+
+
+def test_features_kernel(lib, torch):
+    _, _, _, shapes = data(777, 9)
+    X = torch.empty((777, 7), device="cuda")
+    lib.mlp_features(dev(torch, shapes, np.int64), X)
+    ref = om.features(*[shapes[:, i] for i in range(7)])
+    assert np.max(np.abs(X.cpu().numpy() - ref)) <= 1e-6
