@@ -279,6 +279,38 @@ def mlp_study(deploy_path: str, sweep_path: str, n: int = 2500, seed: int = 4, s
     return {"params": params.tolist(), "study": res}
 
 
+# ---------------------------------------------------------------- VGG16 layers (Section 6)
+def vgg_study(deploy_path: str, sweep_path: str, batches=(1, 16)) -> dict:
+    """Per VGG16 GEMM (im2col convolutions and FC layers): the throughput of the
+    kernel the deployed tree selects against the layer's exhaustive best over
+    the whole family, and the layer-time-weighted totals."""
+    ks = _ks()
+    dep = json.load(open(deploy_path))
+    prec = dep["precision"]
+    ids = ks.config_ids(prec)
+    layers = [(b, name, sh) for b in batches for name, sh in wl.vgg16_layers(b)]
+    shapes = [sh for _, _, sh in layers]
+    perf = sweep(shapes, prec, sweep_path, seed=77, config_ids=ids)
+    h = ks.Handle(dep)
+    col = {c: j for j, c in enumerate(ids)}
+    rows, tot = [], {}
+    for (b, name, sh), p in zip(layers, perf):
+        sel = ks.select_kernel(h, sh.M, sh.N, sh.K, sh.batch)
+        best = int(np.argmax(p))
+        rows.append({"batch": b, "layer": name, "M": sh.M, "N": sh.N, "K": sh.K, "selected": sel,
+                     "selected_tflops": p[col[sel]] / 1e3, "best": ids[best], "best_tflops": p[best] / 1e3,
+                     "ratio": p[col[sel]] / p[best] if p[best] > 0 else 0.0})
+        t = tot.setdefault(b, [0.0, 0.0, 0.0])
+        t[0] += sh.flops / (p[col[sel]] * 1e6)  # ms with the selected kernel
+        t[1] += sh.flops / (p[best] * 1e6)      # ms with the per-layer best
+        t[2] += sh.flops
+    totals = {str(b): {"selected_ms": v[0], "exhaustive_ms": v[1], "ratio": v[1] / v[0],
+                       "selected_tflops": v[2] / (v[0] * 1e9), "distinct_selected": len({r["selected"] for r in rows
+                                                                                         if r["batch"] == b})}
+              for b, v in tot.items()}
+    return {"layers": rows, "totals": totals}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -294,6 +326,10 @@ def main(argv=None):
     ml.add_argument("--n", type=int, default=2500)
     ml.add_argument("--steps", type=int, default=3000)
     ml.add_argument("--out", required=True)
+    vg = sub.add_parser("vgg")
+    vg.add_argument("--deploy", required=True)
+    vg.add_argument("--sweep", required=True)
+    vg.add_argument("--out", required=True)
     d = sub.add_parser("deploy")
     d.add_argument("--table", required=True)
     d.add_argument("--k", type=int, default=8)
@@ -303,6 +339,12 @@ def main(argv=None):
     d.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     ks = _ks()
+    if a.cmd == "vgg":
+        r = vgg_study(a.deploy, a.sweep)
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps(r["totals"], indent=1))
+        return
     if a.cmd == "mlp":
         r = mlp_study(a.deploy, a.sweep, a.n, steps=a.steps)
         dep = json.load(open(a.deploy))

@@ -30,7 +30,8 @@ def test_normalise(lib, torch, mode):
     got = out.cpu().numpy().astype(np.float64)
     want = osel.normalise(perf.astype(np.float64), mode)
     assert np.allclose(got, want, rtol=1e-6, atol=1e-6)
-    assert np.all(got[5] == want[5])
+    if mode != "sigmoid":  # an all-zero row maps to exact zeros (the sigmoid maps it to f(0) ~ 3.5e-19)
+        assert np.all(got[5] == 0.0)
 
 
 def planted(n_per, k, d, spread, seed):
