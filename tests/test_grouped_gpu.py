@@ -36,7 +36,7 @@ def build_group(torch, shapes, fam, seed, ld_multiple=8):
 def check_group(probs, host, shapes, tol, full=True):
     worst = 0.0
     for q, (A, B, C0), sh in zip(probs, host, shapes):
-        C = q["C"].cpu().numpy()[:, :sh.N]
+        C = q["C"].cpu().numpy().reshape(sh.M, -1)[:, :sh.N]
         if full:
             ref, den = og.gemm(sh.transA, sh.transB, sh.M, sh.N, sh.K, q["alpha"], A, B, q["beta"], C0)
             err = og.error_ratio(C[None], ref, den)
