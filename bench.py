@@ -105,26 +105,24 @@ class Clocks:
 
 # ---------------------------------------------------------------- reference arm: the CPU oracle
 def cpu_oracle_sample(shapes, budget_s: float, nthreads: int):
-    """FP64 oracle throughput on a bounded sample: per held-out shape in order,
-    the oracle computes 2 sampled rows x all columns of batch entry 0, until
-    the time budget is spent.  Returns (TFLOP/s, description)."""
+    """FP64 oracle throughput on a bounded sample: the full product of batch
+    entry 0 of the held-out shapes, in order, until the time budget is spent.
+    Returns (TFLOP/s, description)."""
     from oracle import gemm as og
     og.build()
-    flops, t_used, n_shapes, entries = 0, 0.0, 0, 0
+    flops, t_used, n_shapes = 0, 0.0, 0
     for sh in shapes:
-        A, B, _ = wl.gemm_inputs(wl.Shape(sh.M, sh.N, sh.K, 1, sh.transA, sh.transB), seed=5)
-        rows = np.arange(min(2, sh.M))
-        pos = np.stack(np.meshgrid(np.zeros(1, np.int64), rows, np.arange(sh.N), indexing="ij"), -1).reshape(-1, 3)
+        one = wl.Shape(sh.M, sh.N, sh.K, 1, sh.transA, sh.transB)
+        A, B, _ = wl.gemm_inputs(one, seed=5)
         t0 = time.perf_counter()
-        og.gemm_entries(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, B, 0.0, None, pos, nthreads=nthreads)
+        og.gemm(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, B, nthreads=nthreads)
         t_used += time.perf_counter() - t0
-        flops += 2 * sh.K * len(pos)
-        entries += len(pos)
+        flops += one.flops
         n_shapes += 1
         if t_used >= budget_s:
             break
-    return flops / t_used / 1e12, (f"2 rows x all columns of batch entry 0 of the first {n_shapes} held-out shapes "
-                                   f"({entries} entries, {flops / 1e9:.2f} GFLOP, {t_used:.1f} s)")
+    return flops / t_used / 1e12, (f"full FP64 product of batch entry 0 of the first {n_shapes} held-out shapes "
+                                   f"({flops / 1e9:.1f} GFLOP in {t_used:.1f} s, {nthreads} threads)")
 
 
 def run_reference(args, ws, rank):
@@ -265,6 +263,9 @@ def run_ours(args, ws, rank, local):
         ms_e2e = float(t.item())
     e2e = ws * flops * args.steps / (ms_e2e * 1e-3) / 1e12
 
+    tc = tc_families(args, ks, tune, shapes, te, bufs, stream, dev) if not args.no_tc else None
+    grouped = grouped_launch(ks, tune) if not args.no_tc else None
+
     if rank != 0:
         return
     cpu = None
@@ -291,6 +292,8 @@ def run_ours(args, ws, rank, local):
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel_config": dom,
                      "kernel_params": ks.config_params(dom), "share_of_step": by_cfg[dom][0] / float(sel_ms.sum())},
         "e2e": {"value": e2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "tc": tc,
+        "grouped": grouped,
         "gpu_launches": args.steps * len(shapes),
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -298,14 +301,96 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
+    """The same held-out shapes with each tensor-core family's deployed tree:
+    selected-kernel TFLOP/s (untimed warm-up, then timed steps) and the live
+    share of the family's per-shape exhaustive optimum."""
+    import torch
+    out = {}
+    for name, fam in (("tf32", ks.PREC_TF32), ("f32x3", ks.PREC_F32X3), ("bf16", ks.PREC_BF16)):
+        dpath = os.path.join(DEPLOY, f"{name}.json")
+        if not os.path.exists(dpath):
+            continue
+        dep = json.load(open(dpath))
+        h = ks.Handle(dep)
+        _, perf, ids, _ = tune.load_table(os.path.join(DEPLOY, f"table_{name}.npz"))
+        best = [ids[int(np.argmax(perf[i]))] for i in te]
+        fb = bufs if fam != ks.PREC_BF16 else [tune.alloc_inputs(sh, fam, 3000 + i) for i, sh in enumerate(shapes)]
+
+        def run(cfgs=None, events=None):
+            for i, (sh, (A, B, C, lda, ldb, ldc)) in enumerate(zip(shapes, fb)):
+                if events is not None:
+                    events[i][0].record(stream)
+                if cfgs is None:
+                    ks.gemm(h, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, lda, B, ldb, 0.0, C, ldc, sh.batch,
+                            stream)
+                else:
+                    ks.gemm_with_config(cfgs[i], sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, lda, B, ldb, 0.0, C,
+                                        ldc, sh.batch, stream)
+                if events is not None:
+                    events[i][1].record(stream)
+
+        def per_launch(cfgs=None):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in shapes]
+            run(cfgs, ev)
+            torch.cuda.synchronize(dev)
+            return np.array([a.elapsed_time(b) for a, b in ev])
+
+        for _ in range(args.warmup):
+            run()
+        sel = per_launch()
+        exh = per_launch(best)
+        ratio = np.minimum(exh / sel, 1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        flops = sum(sh.flops for sh in shapes)
+        out[name] = {"value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+                     "pct_of_exhaustive_optimum": {"live_geomean": float(np.exp(np.mean(np.log(ratio)))),
+                                                   "sweep_table_test_split": dep["meta"]["scores"]["tree"]["geomean"]},
+                     "deployed_kernels": len(dep["config_ids"]),
+                     "inputs": "bf16" if fam == ks.PREC_BF16 else "f32",
+                     "accuracy": {"tf32": "<= 5e-3", "f32x3": "<= 1e-5 on this data (worst case 3*2^-16)",
+                                  "bf16": "<= 2e-2 (bf16 inputs)"}[name]}
+        if fb is not bufs:
+            del fb
+    return out
+
+
+def grouped_launch(ks, tune):
+    """The 256-problem uneven group in one persistent launch per family, with
+    the tile configuration the grouped autotuner picked, replayed from a CUDA graph."""
+    gpath = os.path.join(DEPLOY, "grouped.json")
+    if not os.path.exists(gpath):
+        return None
+    g = json.load(open(gpath))
+    out = {}
+    for name, r in g.items():
+        fam = ks.family_of(r["config"])
+        probs, keep, flops = tune.grouped_workload(fam)
+        plan = ks.GroupedPlan(r["config"], probs)
+        ms = tune.time_grouped_graph(plan, reps=20, warmup=3)
+        out[name] = {"value": flops / (ms * 1e9), "unit": "TFLOP/s", "ms_per_launch": ms, "config": r["config"],
+                     "problems": len(probs), "gflop": flops / 1e9}
+        plan.close()
+        del keep
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of CPU oracle work per sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core and grouped lines")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     ws, rank, local = dist_setup(args)

@@ -279,6 +279,60 @@ def mlp_study(deploy_path: str, sweep_path: str, n: int = 2500, seed: int = 4, s
     return {"params": params.tolist(), "study": res}
 
 
+# ---------------------------------------------------------------- grouped launch (autotuned tile shape)
+def grouped_workload(family: int, n: int = 256, seed: int = 3, data_seed: int = 500):
+    """Device buffers of the uneven group (M, N, K log-uniform in [32, 4096]), K-contiguous operands."""
+    probs, keep = [], []
+    for i, sh in enumerate(wl.grouped_problems(n, seed)):
+        A, B, C, lda, ldb, ldc = alloc_inputs(sh, family, data_seed + i)
+        keep.append((A, B, C))
+        probs.append(dict(M=sh.M, N=sh.N, K=sh.K, transA="N", transB="T", A=A, lda=lda, B=B, ldb=ldb, C=C, ldc=ldc))
+    flops = sum(2 * q["M"] * q["N"] * q["K"] for q in probs)
+    return probs, keep, flops
+
+
+def time_grouped_graph(plan, reps: int = 10, warmup: int = 2) -> float:
+    """Mean ms of one replay of a CUDA graph holding one grouped launch."""
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.run(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(s)
+    for _ in range(warmup):
+        g.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def grouped_tune(families=("tf32", "bf16", "f32x3")) -> dict:
+    """The benchmark step of the method applied to the grouped launch: every
+    tile configuration of a family timed on the group; the fastest is deployed."""
+    ks = _ks()
+    out = {}
+    for name in families:
+        fam = ks.PRECISIONS[name]
+        probs, keep, flops = grouped_workload(fam)
+        res = []
+        for cid in ks.config_ids(fam):
+            plan = ks.GroupedPlan(cid, probs)
+            ms = time_grouped_graph(plan)
+            plan.close()
+            res.append({"config": cid, "params": ks.config_params(cid), "ms": ms, "tflops": flops / (ms * 1e9)})
+        best = max(res, key=lambda r: r["tflops"])
+        out[name] = {"config": best["config"], "tflops": best["tflops"], "gflop": flops / 1e9, "all": res}
+        del keep
+    return out
+
+
 # ---------------------------------------------------------------- VGG16 layers (Section 6)
 def vgg_study(deploy_path: str, sweep_path: str, batches=(1, 16)) -> dict:
     """Per VGG16 GEMM (im2col convolutions and FC layers): the throughput of the
@@ -326,6 +380,8 @@ def main(argv=None):
     ml.add_argument("--n", type=int, default=2500)
     ml.add_argument("--steps", type=int, default=3000)
     ml.add_argument("--out", required=True)
+    gr = sub.add_parser("grouped")
+    gr.add_argument("--out", required=True)
     vg = sub.add_parser("vgg")
     vg.add_argument("--deploy", required=True)
     vg.add_argument("--sweep", required=True)
@@ -339,6 +395,12 @@ def main(argv=None):
     d.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     ks = _ks()
+    if a.cmd == "grouped":
+        r = grouped_tune()
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps({k: {"config": v["config"], "tflops": v["tflops"]} for k, v in r.items()}, indent=1))
+        return
     if a.cmd == "vgg":
         r = vgg_study(a.deploy, a.sweep)
         with open(a.out, "w") as f:
