@@ -297,6 +297,39 @@ cudaError_t ws_alloc(int nblocks, cudaStream_t s, Workspace* w) {
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------- allocation-free loss/gradient
+// Scratch of mlp_loss_grad_noalloc: per-block gradient partials for up to
+// kNoAllocMaxSamples samples, then the per-block losses, then the count of
+// measured outputs.  Every device that loads the library holds this array
+// (about 5.3 MB) until the process exits.
+constexpr int kNoAllocMaxSamples = 8192;
+constexpr int kNoAllocMaxBlocks = kNoAllocMaxSamples / kChunk;
+constexpr size_t kNoAllocFloats = (size_t)kNoAllocMaxBlocks * NP + kNoAllocMaxBlocks + 64;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+// Device address of the scratch array on the current device.  In host code
+// g_noalloc_scratch names a host-side stand-in, so the address is looked up
+// once per device and cached.
+float* noalloc_scratch(cudaError_t* err) {
+  static float* addr[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return nullptr;
+  if (dev < 0 || dev >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<float*>(p);
+  }
+  return addr[dev];
+}
+
 }  // namespace mlp
 }  // namespace ks
 
@@ -337,6 +370,29 @@ gemm_status_t mlp_loss_grad(int32_t n, const float* P, const float* X, const flo
   mlp_reduce_kernel<<<(NP + 255) / 256, 256, 0, s>>>(w.partials, w.loss_part, nb, grad, loss, nullptr, nullptr, 0);
   e = cudaGetLastError();
   cudaFreeAsync(w.base, s);
+  return e == cudaSuccess ? GEMM_OK : fail(e);
+}
+
+gemm_status_t mlp_loss_grad_noalloc(int32_t n, const float* P, const float* X, const float* T, const float* mask,
+                                    float* grad, float* loss, void* stream) {
+  if (n < 1 || !P || !X || !T || !grad || !loss) return GEMM_ERR_INVALID_ARG;
+  if (n > kNoAllocMaxSamples) return GEMM_ERR_UNSUPPORTED;  // beyond the static scratch
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = ensure_attr();
+  if (e != cudaSuccess) return fail(e);
+  float* base = noalloc_scratch(&e);
+  if (!base) return fail(e);
+  float* partials = base;
+  float* loss_part = base + (size_t)kNoAllocMaxBlocks * NP;
+  float* count = loss_part + kNoAllocMaxBlocks;
+  // Every scratch value read below is written earlier in this call (count, then
+  // the partials and losses of blocks 0..nb-1), so nothing needs clearing.
+  const int nb = (n + kChunk - 1) / kChunk;
+  mlp_count_kernel<<<1, 256, 0, s>>>(mask, (int64_t)n * NO, count);
+  GradArgs a{n, P, X, T, mask, count, partials, loss_part, nullptr};
+  mlp_grad_kernel<<<nb, kThreads, kGradSmem, s>>>(a);
+  mlp_reduce_kernel<<<(NP + 255) / 256, 256, 0, s>>>(partials, loss_part, nb, grad, loss, nullptr, nullptr, 0);
+  e = cudaGetLastError();
   return e == cudaSuccess ? GEMM_OK : fail(e);
 }
 

@@ -76,6 +76,7 @@ _sig("mlp_features", i32, [i32, vp, vp, vp])
 _sig("mlp_forward", i32, [i32, vp, vp, vp, vp])
 _sig("mlp_loss_grad", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
 _sig("mlp_adam_step", i32, [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp])
+_sig("mlp_loss_grad_noalloc", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
 _sig("mlp_train", i32, [i32, vp, vp, vp, vp, vp, vp, i32, i32, f32, f32, f32, f32, vp, vp])
 _sig("select_kernels_batched", i32, [vp, i32, vp, vp, vp, vp])
 _sig("gemm_benchmark_configs", i32, [i32, ctypes.POINTER(i32), ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64,
@@ -391,6 +392,12 @@ def mlp_loss_grad(params, X, T, mask, grad, loss, stream=None) -> None:
                              stream_handle(stream)), "mlp_loss_grad")
 
 
+def mlp_loss_grad_noalloc(params, X, T, mask, grad, loss, stream=None) -> None:
+    """mlp_loss_grad without device allocation (fixed in-library scratch, n <= 8192)."""
+    check(_lib.mlp_loss_grad_noalloc(X.shape[0], ptr(params), ptr(X), ptr(T), ptr(mask), ptr(grad), ptr(loss),
+                                     stream_handle(stream)), "mlp_loss_grad_noalloc")
+
+
 def mlp_adam_step(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
     check(_lib.mlp_adam_step(ptr(params), ptr(grad), ptr(m), ptr(v), t, lr, beta1, beta2, eps, stream_handle(stream)),
           "mlp_adam_step")
@@ -415,5 +422,5 @@ def exported_symbols() -> list[str]:
             "gemm_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
             "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
             "kselect_representatives", "kselect_top_n", "kselect_tree_train", "mlp_features", "mlp_forward", "mlp_loss_grad",
-            "mlp_adam_step", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
+            "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
             "gemm_grouped_plan_destroy", "gemm_grouped"]
