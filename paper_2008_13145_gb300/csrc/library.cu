@@ -45,6 +45,17 @@ static int family_of(int id) {
   return -1;
 }
 
+// Families a handle of precision class `cls` may deploy: its own, plus those
+// that read the same input type at least as accurately (FP32 SIMT and the
+// split-BF16 x3 family both take FP32 inputs at FP32-level accuracy; a TF32
+// handle may also use either of them).
+static bool family_allowed(int cls, int fam) {
+  if (fam == cls) return true;
+  if (cls == GEMM_PREC_F32 || cls == GEMM_PREC_F32X3) return fam == GEMM_PREC_F32 || fam == GEMM_PREC_F32X3;
+  if (cls == GEMM_PREC_TF32) return fam == GEMM_PREC_F32 || fam == GEMM_PREC_F32X3;
+  return false;
+}
+
 static bool is_trans(char t, int* out) {
   if (t == 'N' || t == 'n') { *out = 0; return true; }
   if (t == 'T' || t == 't') { *out = 1; return true; }
@@ -178,7 +189,8 @@ gemm_status_t gemm_library_create(const gemm_deployment_t* d, gemm_handle_t* out
   if (d->n_nodes < 0 || d->n_nodes > GEMM_MAX_TREE_NODES || (d->n_nodes > 0 && !d->nodes))
     return GEMM_ERR_INVALID_ARG;
   for (int i = 0; i < d->n_configs; ++i)
-    if (family_of(d->config_ids[i]) != d->precision) return GEMM_ERR_NO_KERNEL;
+    if (family_of(d->config_ids[i]) < 0 || !family_allowed(d->precision, family_of(d->config_ids[i])))
+      return GEMM_ERR_NO_KERNEL;
   // Tree: children in range, every node reached at most once from the root
   // (so no cycles and no sharing), leaf labels inside the deployed set.
   if (d->n_nodes > 0) {

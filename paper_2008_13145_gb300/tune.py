@@ -122,6 +122,18 @@ def load_table(path: str):
     return shapes, z["perf"].astype(np.float64), [int(x) for x in z["config_ids"]], int(z["precision"])
 
 
+def combine_tables(paths: list[str], out_path: str, precision: int) -> None:
+    """Concatenate sweep tables of the same shapes column-wise (a precision
+    class whose candidates span several kernel families)."""
+    tabs = [load_table(p) for p in paths]
+    shapes = tabs[0][0]
+    for t in tabs[1:]:
+        assert t[0] == shapes, "tables cover different shapes"
+    perf = np.concatenate([t[1] for t in tabs], axis=1)
+    ids = [c for t in tabs for c in t[2]]
+    save_table(out_path, shapes, perf, ids, precision)
+
+
 # ---------------------------------------------------------------- Sections 3.4 and 4
 def kmeans_draws(n_init: int, k: int, seed: int) -> np.ndarray:
     """The seeding draws (uint32) the clustering consumes: an input, not computed by it."""
@@ -380,6 +392,10 @@ def main(argv=None):
     ml.add_argument("--n", type=int, default=2500)
     ml.add_argument("--steps", type=int, default=3000)
     ml.add_argument("--out", required=True)
+    cb = sub.add_parser("combine")
+    cb.add_argument("--tables", nargs="+", required=True)
+    cb.add_argument("--precision", default="f32")
+    cb.add_argument("--out", required=True)
     gr = sub.add_parser("grouped")
     gr.add_argument("--out", required=True)
     vg = sub.add_parser("vgg")
@@ -395,6 +411,9 @@ def main(argv=None):
     d.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     ks = _ks()
+    if a.cmd == "combine":
+        combine_tables(a.tables, a.out, ks.PRECISIONS[a.precision])
+        return
     if a.cmd == "grouped":
         r = grouped_tune()
         with open(a.out, "w") as f:

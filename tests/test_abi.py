@@ -109,6 +109,10 @@ def test_deployment_validation(ks):
     with pytest.raises(ks.KSelectError) as e:
         ks.Handle({"precision": 0, "config_ids": [], "nodes": []})
     assert e.value.status == -6
+    # an FP32-input handle may mix the SIMT and split-BF16 x3 families, not TF32 or BF16
+    assert ks.Handle({"precision": 0, "config_ids": [5, 1201], "nodes": []}).ids == [5, 1201]
+    with pytest.raises(ks.KSelectError):
+        ks.Handle({"precision": 3, "config_ids": [1101], "nodes": []})
     h0 = ks.Handle({"precision": 0, "config_ids": [42], "nodes": []})
     assert ks.select_kernel(h0, 1, 1, 1, 1) == 42
 
