@@ -302,12 +302,15 @@ def run_ours(args, ws, rank, local):
 
 
 def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
-    """The same held-out shapes with each tensor-core family's deployed tree:
+    """The same held-out shapes with each tensor-core family's deployed tree
+    (and the FP32-input class whose deployment mixes SIMT and split-BF16x3
+    kernels, "f32mix"):
     selected-kernel TFLOP/s (untimed warm-up, then timed steps) and the live
     share of the family's per-shape exhaustive optimum."""
     import torch
     out = {}
-    for name, fam in (("tf32", ks.PREC_TF32), ("f32x3", ks.PREC_F32X3), ("bf16", ks.PREC_BF16)):
+    for name, fam in (("tf32", ks.PREC_TF32), ("f32x3", ks.PREC_F32X3), ("bf16", ks.PREC_BF16),
+                      ("f32mix", ks.PREC_F32)):
         dpath = os.path.join(DEPLOY, f"{name}.json")
         if not os.path.exists(dpath):
             continue
@@ -356,7 +359,10 @@ def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
                      "deployed_kernels": len(dep["config_ids"]),
                      "inputs": "bf16" if fam == ks.PREC_BF16 else "f32",
                      "accuracy": {"tf32": "<= 5e-3", "f32x3": "<= 1e-5 on this data (worst case 3*2^-16)",
-                                  "bf16": "<= 2e-2 (bf16 inputs)"}[name]}
+                                  "bf16": "<= 2e-2 (bf16 inputs)",
+                                  "f32mix": "FP32 SIMT or split-BF16x3, <= 1e-5 on this data"}[name]}
+        if name == "f32mix":
+            out[name]["families_deployed"] = sorted({ks.family_of(c) for c in dep["config_ids"]})
         if fb is not bufs:
             del fb
     return out

@@ -40,6 +40,12 @@ struct SimtCfg {
   static constexpr int RB = (CHB + T - 1) / T;
   __device__ static constexpr int row(int i, int ty) { return (i / CM) * (WY * CM) + ty * CM + (i % CM); }
   __device__ static constexpr int col(int j, int tx) { return (j / CN) * (WX * CN) + tx * CN + (j % CN); }
+  // Shared-memory position of column m of slice row k: the 4-float chunk index
+  // is XORed with (k / 4) masked to the row's chunk count, which spreads the
+  // transposing stores over the banks while every 4-aligned chunk stays
+  // contiguous for the vector reads.
+  __device__ static constexpr int swz_a(int m, int k) { return (((m >> 2) ^ ((k >> 2) & (BM / 4 - 1))) << 2) | (m & 3); }
+  __device__ static constexpr int swz_b(int n, int k) { return (((n >> 2) ^ ((k >> 2) & (BN / 4 - 1))) << 2) | (n & 3); }
 };
 
 template <int W>
@@ -175,7 +181,8 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, float* Cb, int m0, i
 }
 
 // ---------------------------------------------------------------- staged slice copy
-template <class Cfg>
+// FAST: the whole slice is inside op(A) and 16-byte loads are legal (interior tile).
+template <class Cfg, bool FAST>
 __device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArgs& p, const float* Ab,
                                              int m0, int k0, int tid) {
   constexpr int BK = Cfg::BK, BM = Cfg::BM;
@@ -187,10 +194,18 @@ __device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArg
       if (!p.transA) {  // stored M x K: chunk of 4 along k
         const int m = c / (BK / 4), kq = (c % (BK / 4)) * 4;
         const int gm = m0 + m, gk = k0 + kq;
+        if (FAST) {
+          r[u] = __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gm * p.lda + gk));
+          continue;
+        }
         if (gm < p.M) load_vec_global<4>(v, Ab + (int64_t)gm * p.lda + gk, p.K - gk, p.vecA);
       } else {  // stored K x M: chunk of 4 along m
         const int k = c / (BM / 4), mq = (c % (BM / 4)) * 4;
         const int gk = k0 + k, gm = m0 + mq;
+        if (FAST) {
+          r[u] = __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gk * p.lda + gm));
+          continue;
+        }
         if (gk < p.K) load_vec_global<4>(v, Ab + (int64_t)gk * p.lda + gm, p.M - gm, p.vecA);
       }
     }
@@ -207,19 +222,20 @@ __device__ __forceinline__ void store_slice_a(const float4 (&r)[Cfg::RA], const 
     if (c < Cfg::CHA) {
       if (!p.transA) {
         const int m = c / (BK / 4), kq = (c % (BK / 4)) * 4;
-        As[(kq + 0) * L + m] = r[u].x;
-        As[(kq + 1) * L + m] = r[u].y;
-        As[(kq + 2) * L + m] = r[u].z;
-        As[(kq + 3) * L + m] = r[u].w;
+        const int pm = Cfg::swz_a(m, kq);  // same chunk XOR for the 4 rows kq..kq+3
+        As[(kq + 0) * L + pm] = r[u].x;
+        As[(kq + 1) * L + pm] = r[u].y;
+        As[(kq + 2) * L + pm] = r[u].z;
+        As[(kq + 3) * L + pm] = r[u].w;
       } else {
         const int k = c / (BM / 4), mq = (c % (BM / 4)) * 4;
-        *reinterpret_cast<float4*>(As + k * L + mq) = r[u];
+        *reinterpret_cast<float4*>(As + k * L + Cfg::swz_a(mq, k)) = r[u];
       }
     }
   }
 }
 
-template <class Cfg>
+template <class Cfg, bool FAST>
 __device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArgs& p, const float* Bb,
                                              int n0, int k0, int tid) {
   constexpr int BK = Cfg::BK, BN = Cfg::BN;
@@ -231,10 +247,18 @@ __device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArg
       if (!p.transB) {  // stored K x N: chunk along n
         const int k = c / (BN / 4), nq = (c % (BN / 4)) * 4;
         const int gk = k0 + k, gn = n0 + nq;
+        if (FAST) {
+          r[u] = __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gk * p.ldb + gn));
+          continue;
+        }
         if (gk < p.K) load_vec_global<4>(v, Bb + (int64_t)gk * p.ldb + gn, p.N - gn, p.vecB);
       } else {  // stored N x K: chunk along k
         const int n = c / (BK / 4), kq = (c % (BK / 4)) * 4;
         const int gn = n0 + n, gk = k0 + kq;
+        if (FAST) {
+          r[u] = __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gn * p.ldb + gk));
+          continue;
+        }
         if (gn < p.N) load_vec_global<4>(v, Bb + (int64_t)gn * p.ldb + gk, p.K - gk, p.vecB);
       }
     }
@@ -251,13 +275,14 @@ __device__ __forceinline__ void store_slice_b(const float4 (&r)[Cfg::RB], const 
     if (c < Cfg::CHB) {
       if (!p.transB) {
         const int k = c / (BN / 4), nq = (c % (BN / 4)) * 4;
-        *reinterpret_cast<float4*>(Bs + k * L + nq) = r[u];
+        *reinterpret_cast<float4*>(Bs + k * L + Cfg::swz_b(nq, k)) = r[u];
       } else {
         const int n = c / (BK / 4), kq = (c % (BK / 4)) * 4;
-        Bs[(kq + 0) * L + n] = r[u].x;
-        Bs[(kq + 1) * L + n] = r[u].y;
-        Bs[(kq + 2) * L + n] = r[u].z;
-        Bs[(kq + 3) * L + n] = r[u].w;
+        const int pn = Cfg::swz_b(n, kq);
+        Bs[(kq + 0) * L + pn] = r[u].x;
+        Bs[(kq + 1) * L + pn] = r[u].y;
+        Bs[(kq + 2) * L + pn] = r[u].z;
+        Bs[(kq + 3) * L + pn] = r[u].w;
       }
     }
   }
@@ -285,8 +310,15 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
   if constexpr (Cfg::STAGED) {
     extern __shared__ __align__(16) float smem[];
     float4 ra[Cfg::RA], rb[Cfg::RB];
-    load_slice_a<Cfg>(ra, p, Ab, m0, 0, tid);
-    load_slice_b<Cfg>(rb, p, Bb, n0, 0, tid);
+    // Interior tiles with 16-byte-loadable operands skip every bounds check.
+    const bool fast_mn = (m0 + Cfg::BM <= p.M) && (n0 + Cfg::BN <= p.N) && p.vecA && p.vecB;
+    if (fast_mn && BK <= p.K) {
+      load_slice_a<Cfg, true>(ra, p, Ab, m0, 0, tid);
+      load_slice_b<Cfg, true>(rb, p, Bb, n0, 0, tid);
+    } else {
+      load_slice_a<Cfg, false>(ra, p, Ab, m0, 0, tid);
+      load_slice_b<Cfg, false>(rb, p, Bb, n0, 0, tid);
+    }
     store_slice_a<Cfg>(ra, p, smem, tid);
     store_slice_b<Cfg>(rb, p, smem + BK * Cfg::LDS_A, tid);
     __syncthreads();
@@ -295,18 +327,24 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
       const float* Bs = As + BK * Cfg::LDS_A;
       const bool more = kt + 1 < nk;
       if (more) {
-        load_slice_a<Cfg>(ra, p, Ab, m0, (kt + 1) * BK, tid);
-        load_slice_b<Cfg>(rb, p, Bb, n0, (kt + 1) * BK, tid);
+        const int kn = (kt + 1) * BK;
+        if (fast_mn && kn + BK <= p.K) {
+          load_slice_a<Cfg, true>(ra, p, Ab, m0, kn, tid);
+          load_slice_b<Cfg, true>(rb, p, Bb, n0, kn, tid);
+        } else {
+          load_slice_a<Cfg, false>(ra, p, Ab, m0, kn, tid);
+          load_slice_b<Cfg, false>(rb, p, Bb, n0, kn, tid);
+        }
       }
 #pragma unroll
       for (int k = 0; k < BK; ++k) {
         float a[TM], bv[TN];
 #pragma unroll
         for (int ic = 0; ic < TM / CM; ++ic)
-          load_vec_smem<CM>(a + ic * CM, As + k * Cfg::LDS_A + ic * (Cfg::WY * CM) + ty * CM);
+          load_vec_smem<CM>(a + ic * CM, As + k * Cfg::LDS_A + Cfg::swz_a(ic * (Cfg::WY * CM) + ty * CM, k));
 #pragma unroll
         for (int jc = 0; jc < TN / CN; ++jc)
-          load_vec_smem<CN>(bv + jc * CN, Bs + k * Cfg::LDS_B + jc * (Cfg::WX * CN) + tx * CN);
+          load_vec_smem<CN>(bv + jc * CN, Bs + k * Cfg::LDS_B + Cfg::swz_b(jc * (Cfg::WX * CN) + tx * CN, k));
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
