@@ -368,5 +368,17 @@ def pca_explained_variance(X: np.ndarray) -> np.ndarray:
     return ev / ev.sum() if ev.sum() > 0 else ev
 
 
+def pca_top(X: np.ndarray, r: int):
+    """Mean, the r largest eigenvalues (descending) and unit eigenvectors (d x r)
+    of the sample covariance, and its trace (the total variance)."""
+    X = np.asarray(X, np.float64)
+    mean = X.mean(axis=0)
+    Xc = X - mean
+    cov = Xc.T @ Xc / max(X.shape[0] - 1, 1)
+    w, v = np.linalg.eigh(cov)
+    order = np.argsort(w)[::-1][:r]
+    return mean, w[order], v[:, order], float(np.trace(cov))
+
+
 def components_for(explained: np.ndarray, frac: float) -> int:
     return int(np.searchsorted(np.cumsum(explained), frac - 1e-12) + 1)

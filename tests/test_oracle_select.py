@@ -193,3 +193,13 @@ def test_pca_matches_svd():
     assert np.allclose(ev, s ** 2 / np.sum(s ** 2), rtol=1e-10, atol=1e-14)
     assert osel.components_for(np.array([0.5, 0.3, 0.15, 0.05]), 0.8) == 2
     assert osel.components_for(np.array([0.5, 0.3, 0.15, 0.05]), 0.95) == 3
+
+
+def test_pca_top_eigenpairs():
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((80, 6)) @ np.diag([4, 3, 2, 1, 0.5, 0.1])
+    mean, w, v, tot = osel.pca_top(X, 3)
+    cov = np.cov(X.T)
+    assert np.allclose(cov @ v, v * w, atol=1e-10)
+    assert np.allclose(v.T @ v, np.eye(3), atol=1e-12)
+    assert tot == pytest.approx(np.trace(cov)) and np.all(np.diff(w) <= 0)
