@@ -62,6 +62,25 @@ def dist_setup(args):
     return ws, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's);
+    identity without a process group.  A control-path reduction only: the
+    GEMMs of different ranks are independent replicas."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size: int, flops_per_step: float, steps: int, ms_total: float) -> float:
+    """Whole-job TFLOP/s: the work of every rank over the slowest rank's time."""
+    return world_size * flops_per_step * steps / (ms_total * 1e-3) / 1e12
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -226,13 +245,9 @@ def run_ours(args, ws, rank, local):
                     evs[i][1].record(stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-    ms_total = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
-    value = ws * flops * args.steps / (ms_total * 1e-3) / 1e12
+    value = job_throughput(ws, flops, args.steps, ms_total)
     dom_ms = sum(a.elapsed_time(b) for evs in dom_ev for a, b in evs) / (len(dom_idx) * args.steps)
     dom_flops = by_cfg[dom][1] / by_cfg[dom][2]
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
@@ -256,12 +271,8 @@ def run_ours(args, ws, rank, local):
                          sh.batch, A, B, C, stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms_e2e = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = ws * flops * args.steps / (ms_e2e * 1e-3) / 1e12
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+    e2e = job_throughput(ws, flops, args.steps, ms_e2e)
 
     tc = tc_families(args, ks, tune, shapes, te, bufs, stream, dev) if not args.no_tc else None
     grouped = grouped_launch(ks, tune) if not args.no_tc else None
@@ -320,18 +331,17 @@ def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
         best = [ids[int(np.argmax(perf[i]))] for i in te]
         fb = bufs if fam != ks.PREC_BF16 else [tune.alloc_inputs(sh, fam, 3000 + i) for i, sh in enumerate(shapes)]
 
-        def run(cfgs=None, events=None):
+        def run(cfgs=None, events=None, st=stream):
             for i, (sh, (A, B, C, lda, ldb, ldc)) in enumerate(zip(shapes, fb)):
                 if events is not None:
-                    events[i][0].record(stream)
+                    events[i][0].record(st)
                 if cfgs is None:
-                    ks.gemm(h, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, lda, B, ldb, 0.0, C, ldc, sh.batch,
-                            stream)
+                    ks.gemm(h, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, lda, B, ldb, 0.0, C, ldc, sh.batch, st)
                 else:
                     ks.gemm_with_config(cfgs[i], sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, lda, B, ldb, 0.0, C,
-                                        ldc, sh.batch, stream)
+                                        ldc, sh.batch, st)
                 if events is not None:
-                    events[i][1].record(stream)
+                    events[i][1].record(st)
 
         def per_launch(cfgs=None):
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in shapes]
@@ -353,7 +363,22 @@ def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / args.steps
         flops = sum(sh.flops for sh in shapes)
+        # The same step captured once in a CUDA graph (kernels selected at capture) and replayed.
+        side = torch.cuda.Stream(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            run(st=side)
+        with torch.cuda.stream(side):
+            g.replay()
+            torch.cuda.synchronize(dev)
+            e0.record(side)
+            for _ in range(args.steps):
+                g.replay()
+            e1.record(side)
+        torch.cuda.synchronize(dev)
+        ms_graph = e0.elapsed_time(e1) / args.steps
         out[name] = {"value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+                     "graph_value": flops / (ms_graph * 1e-3) / 1e12,
                      "pct_of_exhaustive_optimum": {"live_geomean": float(np.exp(np.mean(np.log(ratio)))),
                                                    "sweep_table_test_split": dep["meta"]["scores"]["tree"]["geomean"]},
                      "deployed_kernels": len(dep["config_ids"]),

@@ -45,7 +45,7 @@ typedef enum {
   GEMM_ERR_NO_KERNEL = -6    /* unknown config id or empty deployment */
 } gemm_status_t;
 
-/* Kernel families.  F32: the FP32 SIMT family.  TF32: tcgen05 kind::tf32 on
+/* Kernel families (and precision classes of a handle).  F32: the FP32 SIMT family.  TF32: tcgen05 kind::tf32 on
  * FP32 storage.  BF16: tcgen05 kind::f16 on BF16 storage.  F32X3: FP32
  * storage split into BF16 hi/lo parts, three tcgen05 products accumulated in
  * FP32.  C is FP32 in every family, accumulation is FP32 in every family. */
@@ -68,13 +68,15 @@ int32_t gemm_last_cuda_error(void);
  * parameters are the per-thread tile TM x TN in {1,2,4,8}^2, the thread-block
  * shape (WX along N, WY along M) in {8x8, 16x16, 32x8, 8x32, 16x8, 8x16}, the
  * K-step BK in {8,16,32} and shared-memory staging on/off: 576 configs, ids
- * 0..575.  Tensor-core families (ids 1000 + 100*family + index) use a 128 x BN
- * tile with BN in {64,128,256}, a shared-memory ring of {2,3,4} stages and
- * M- or N-major tile order: 18 configs per family.
+ * 0..575.  Tensor-core families (ids 1000 + 100*(family-1) + index, index =
+ * (BN slot * 3 + stage slot) * 2 + pair) use a 128 x BN tile per CTA with BN in
+ * {64,128,256}, a shared-memory ring of {2,3,4} stages, and either one CTA per
+ * tile or a cluster of two CTAs on vertically adjacent tiles that share the B
+ * slice by TMA multicast: 18 configs per family.
  *
  * gemm_config_params writes 8 integers:
  *   F32: {family=0, TM, TN, WX, WY, BK, staged, 0}
- *   TC : {family, BM=128, BN, BK (elements per 128-byte row), stages, raster (0 M-major, 1 N-major), 0, 0}
+ *   TC : {family, BM=128, BN, BK (elements per 128-byte row), stages, pair (0 or 1), 0, 0}
  */
 int32_t gemm_config_count(int32_t precision);
 int32_t gemm_config_id(int32_t precision, int32_t index);
@@ -101,12 +103,17 @@ typedef struct {
 } gemm_tree_node_t;
 
 typedef struct {
-  int32_t precision;            /* gemm_precision_t of every deployed config */
+  int32_t precision;            /* precision class: deployed configs are of this family, or
+                                   for F32/F32X3/TF32 classes also of the F32 or F32X3
+                                   family (same FP32 inputs, FP32-level accuracy) */
   int32_t n_configs;            /* 1..GEMM_MAX_DEPLOYED */
   const int32_t* config_ids;    /* host, n_configs ids */
   int32_t n_nodes;              /* 0 (always config_ids[0]) .. GEMM_MAX_TREE_NODES */
   const gemm_tree_node_t* nodes;/* host */
   const float* mlp_params;      /* host, GEMM_MLP_PARAMS floats, or NULL */
+  int32_t n_known;              /* benchmarked sizes with their measured best kernel, or 0 */
+  const int64_t* known_sizes;   /* host, n_known rows of (M, N, K, batch) */
+  const int32_t* known_ids;     /* host, n_known config ids (any config of an allowed family) */
 } gemm_deployment_t;
 
 /* Copies the deployment into a new immutable handle (host only; device
@@ -116,8 +123,10 @@ typedef struct {
 gemm_status_t gemm_library_create(const gemm_deployment_t* deployment, gemm_handle_t* out);
 void gemm_library_destroy(gemm_handle_t handle);
 
-/* Deployed config id for these sizes (tree walk on the host, O(depth)), or a
- * negative gemm_status_t. */
+/* Deployed config id for these sizes, or a negative gemm_status_t: sizes that
+ * were benchmarked (the deployment's known table) get their measured best
+ * kernel -- the exhaustive selector as a fallback ahead of the classifier --
+ * and all others the decision tree's choice (host walk, O(depth)). */
 int32_t select_kernel(gemm_handle_t handle, int64_t M, int64_t N, int64_t K, int64_t batch);
 
 /* ---------------------------------------------------------------- GEMM
@@ -234,6 +243,23 @@ gemm_status_t kselect_normalise(int64_t n_rows, int32_t n_cols, const float* per
 gemm_status_t kselect_kmeans(int32_t n, int32_t d, int32_t k, int32_t n_init, const float* X_dev,
                              const uint32_t* draws, int32_t max_iter, float tol, float* centres_out_dev,
                              int32_t* labels_out_dev, double* inertia_out, int32_t* iters_out, void* stream);
+
+/* Section 3.3 / 4.1 (PCA): the r leading principal components of the n rows
+ * of X (n x d, device).  Covariance of the centred rows by the library's FP32
+ * GEMM, `iters` rounds of subspace iteration from V0_dev (d x r starting
+ * basis, e.g. seeded draws), then Rayleigh-Ritz.  Writes mean_out_dev (d),
+ * V_out_dev (d x r, orthonormal columns, descending eigenvalue order),
+ * Y_out_dev (n x r projections of the centred rows, or NULL), evals_out (r,
+ * host) and *total_var_out (the covariance trace, host).  Allocates scratch
+ * stream-ordered; synchronises `stream`. */
+gemm_status_t kselect_pca(int32_t n, int32_t d, const float* X_dev, int32_t r, int32_t iters, const float* V0_dev,
+                          float* mean_out_dev, float* V_out_dev, float* Y_out_dev, double* evals_out,
+                          double* total_var_out, void* stream);
+
+/* out_dev (k x d) = mean_dev + cent_dev (k x r) * V_dev^T: PCA-space centres as
+ * performance vectors over the d configurations. */
+gemm_status_t kselect_pca_backproject(int32_t k, int32_t d, int32_t r, const float* cent_dev, const float* V_dev,
+                                      const float* mean_dev, float* out_dev, void* stream);
 
 /* Section 4.3: over the rows of a throughput table (device), ratio =
  * perf[r, pick] / max(row) with pick = chosen_dev[r] (a classifier's column,

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <mutex>
 #include <vector>
 
@@ -64,6 +65,8 @@ struct kselect_library {
   std::vector<int32_t> ids;
   std::vector<gemm_tree_node_t> nodes;
   std::vector<float> mlp;  // empty when absent
+  std::vector<std::array<int64_t, 4>> known;  // sorted benchmarked sizes
+  std::vector<int32_t> known_ids;
   std::mutex dev_mu;
   float* dev_mlp[64] = {nullptr};
   ~kselect_library() {

@@ -211,8 +211,25 @@ gemm_status_t gemm_library_create(const gemm_deployment_t* d, gemm_handle_t* out
       }
     }
   }
+  if (d->n_known < 0 || (d->n_known > 0 && (!d->known_sizes || !d->known_ids))) return GEMM_ERR_INVALID_ARG;
+  for (int i = 0; i < d->n_known; ++i)
+    if (family_of(d->known_ids[i]) < 0 || !family_allowed(d->precision, family_of(d->known_ids[i])))
+      return GEMM_ERR_NO_KERNEL;
   kselect_library* h = new (std::nothrow) kselect_library();
   if (!h) return GEMM_ERR_UNSUPPORTED;
+  if (d->n_known > 0) {
+    std::vector<std::pair<std::array<int64_t, 4>, int32_t>> kv(d->n_known);
+    for (int i = 0; i < d->n_known; ++i) {
+      const int64_t* r = d->known_sizes + 4 * (size_t)i;
+      kv[i] = {{r[0], r[1], r[2], r[3]}, d->known_ids[i]};
+    }
+    std::stable_sort(kv.begin(), kv.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (auto& e : kv) {
+      if (!h->known.empty() && h->known.back() == e.first) continue;  // first entry wins
+      h->known.push_back(e.first);
+      h->known_ids.push_back(e.second);
+    }
+  }
   h->precision = d->precision;
   h->ids.assign(d->config_ids, d->config_ids + d->n_configs);
   if (d->n_nodes > 0) h->nodes.assign(d->nodes, d->nodes + d->n_nodes);
@@ -228,6 +245,11 @@ void gemm_library_destroy(gemm_handle_t h) { delete h; }
 int32_t select_kernel(gemm_handle_t h, int64_t M, int64_t N, int64_t K, int64_t batch) {
   if (!h) return GEMM_ERR_INVALID_ARG;
   if (M < 0 || N < 0 || K < 0 || batch < 0) return GEMM_ERR_INVALID_ARG;
+  if (!h->known.empty()) {
+    const std::array<int64_t, 4> key{M, N, K, batch};
+    auto it = std::lower_bound(h->known.begin(), h->known.end(), key);
+    if (it != h->known.end() && *it == key) return h->known_ids[it - h->known.begin()];
+  }
   if (h->nodes.empty()) return h->ids[0];
   const double f[4] = {(double)M, (double)N, (double)K, (double)batch};
   int j = 0;

@@ -31,7 +31,8 @@ constexpr int kTcStages[3] = {2, 3, 4};
 
 struct TcConfig {
   int family;  // GEMM_PREC_TF32, GEMM_PREC_BF16, GEMM_PREC_F32X3
-  int bn, stages, raster;
+  int bn, stages;
+  int pair;    // 1: clusters of two CTAs sharing the B slice by multicast
 };
 
 bool decode(int id, TcConfig* c) {
@@ -41,7 +42,7 @@ bool decode(int id, TcConfig* c) {
   c->family = fam + 1;
   c->bn = kTcBn[idx / 6];
   c->stages = kTcStages[(idx / 2) % 3];
-  c->raster = idx % 2;
+  c->pair = idx % 2;
   return true;
 }
 
@@ -181,16 +182,30 @@ cudaError_t launch_prep_group(int family, const PrepJob* jobs, int n_jobs, int b
 }
 
 // ---------------------------------------------------------------- main kernel launch
-template <int BN, int STAGES, bool TF32, bool GROUPED>
+// Persistent grid: one CTA (or CTA pair) per resident slot, at most one per tile unit.
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR>
 cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc::TcArgs& a, const tc::GroupArgs& g,
                           cudaStream_t s) {
   using Cfg = tc::TcCfg<BN, STAGES, TF32>;
-  auto kern = tc::tc_gemm_kernel<BN, STAGES, TF32, GROUPED>;
+  auto kern = tc::tc_gemm_kernel<BN, STAGES, TF32, GROUPED, PAIR>;
   static unsigned long long done_mask = 0;
   static int slots_cache[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(tc::kThreads, 1, 1);
+  cfg.dynamicSmemBytes = Cfg::SMEM_BYTES;
+  cfg.stream = s;
+  if (PAIR) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
   if (!(__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & bit)) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -199,21 +214,29 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc
     if (e != cudaSuccess) return e;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     occ = std::min(occ, 512 / Cfg::TMEM_COLS);  // every resident CTA must fit in TMEM
-    slots_cache[dev & 63] = std::max(occ, 1) * sms;
+    int slots = std::max(occ, 1) * sms;
+    if (PAIR) {
+      int clusters = 0;
+      cfg.gridDim = dim3(2 * sms, 1, 1);
+      e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+      if (e != cudaSuccess) return e;
+      slots = std::max(1, std::min(clusters, slots / 2));  // in pairs
+    }
+    slots_cache[dev & 63] = slots;
     __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);
   }
-  const int grid = std::min(a.num_tiles, slots_cache[dev & 63]);
-  kern<<<grid, tc::kThreads, Cfg::SMEM_BYTES, s>>>(ma, mb, a, g);
-  return cudaGetLastError();
+  const int units = std::min(a.num_tiles, slots_cache[dev & 63]);
+  cfg.gridDim = dim3((unsigned)(PAIR ? 2 * units : units), 1, 1);
+  return cudaLaunchKernelEx(&cfg, kern, ma, mb, a, g);
 }
 
 using TcLaunch = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const tc::TcArgs&, const tc::GroupArgs&,
                                  cudaStream_t);
 
-template <bool TF32, bool GROUPED>
+template <bool TF32, bool GROUPED, bool PAIR>
 TcLaunch pick(int bn, int stages) {
 #define KS_TC_CASE(B, S) \
-  if (bn == B && stages == S) return &launch_kernel<B, S, TF32, GROUPED>;
+  if (bn == B && stages == S) return &launch_kernel<B, S, TF32, GROUPED, PAIR>;
   KS_TC_CASE(64, 2) KS_TC_CASE(64, 3) KS_TC_CASE(64, 4)
   KS_TC_CASE(128, 2) KS_TC_CASE(128, 3) KS_TC_CASE(128, 4)
   KS_TC_CASE(256, 2) KS_TC_CASE(256, 3) KS_TC_CASE(256, 4)
@@ -223,8 +246,18 @@ TcLaunch pick(int bn, int stages) {
 
 TcLaunch pick_launch(const TcConfig& c, bool grouped) {
   const bool tf32 = c.family == GEMM_PREC_TF32;
-  if (grouped) return tf32 ? pick<true, true>(c.bn, c.stages) : pick<false, true>(c.bn, c.stages);
-  return tf32 ? pick<true, false>(c.bn, c.stages) : pick<false, false>(c.bn, c.stages);
+  if (c.pair) {
+    if (grouped) return tf32 ? pick<true, true, true>(c.bn, c.stages) : pick<false, true, true>(c.bn, c.stages);
+    return tf32 ? pick<true, false, true>(c.bn, c.stages) : pick<false, false, true>(c.bn, c.stages);
+  }
+  if (grouped) return tf32 ? pick<true, true, false>(c.bn, c.stages) : pick<false, true, false>(c.bn, c.stages);
+  return tf32 ? pick<true, false, false>(c.bn, c.stages) : pick<false, false, false>(c.bn, c.stages);
+}
+
+// Row-tile units: 128-row tiles, or pairs of them.
+int row_units(int64_t M, int pair) {
+  const int t = (int)((M + tc::kBM - 1) / tc::kBM);
+  return pair ? (t + 1) / 2 : t;
 }
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -271,7 +304,7 @@ gemm_status_t tc_params(int id, int32_t out[8]) {
   TcConfig c;
   if (!decode(id, &c)) return GEMM_ERR_NO_KERNEL;
   const int bk = (c.family == GEMM_PREC_TF32) ? 32 : 64;
-  int32_t v[8] = {c.family, 128, c.bn, bk, c.stages, c.raster, 0, 0};
+  int32_t v[8] = {c.family, 128, c.bn, bk, c.stages, c.pair, 0, 0};
   std::memcpy(out, v, sizeof(v));
   return GEMM_OK;
 }
@@ -309,16 +342,16 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
   const int64_t Kop = c.family == GEMM_PREC_F32X3 ? 3 * round_up(g.K, 64) : g.K;
   CUtensorMap ma, mb;
   if (st == GEMM_OK && (!make_map(&ma, Aop, op_bf16, Kop, g.M, pa.ld, g.batch, tc::kBM) ||
-                        !make_map(&mb, Bop, op_bf16, Kop, g.N, pb.ld, g.batch, c.bn)))
+                        !make_map(&mb, Bop, op_bf16, Kop, g.N, pb.ld, g.batch, c.pair ? c.bn / 2 : c.bn)))
     st = GEMM_ERR_MISALIGNED;
   if (st == GEMM_OK) {
     tc::TcArgs a;
     a.M = g.M; a.N = g.N; a.K = (int)Kop; a.batch = g.batch;
-    a.tiles_m = (g.M + tc::kBM - 1) / tc::kBM;
+    a.tiles_m = row_units(g.M, c.pair);
     a.tiles_n = (g.N + c.bn - 1) / c.bn;
     a.num_tiles = a.tiles_m * a.tiles_n * g.batch;
     a.k_blocks = (int)((Kop + (op_bf16 ? 63 : 31)) / (op_bf16 ? 64 : 32));
-    a.raster = c.raster;
+    a.raster = 0;
     a.alpha = g.alpha; a.beta = g.beta;
     a.C = g.C; a.ldc = g.ldc; a.strideC = g.strideC; a.vecC = g.vecC;
     a.status = status;
@@ -390,7 +423,7 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
     pb[i] = plan_operand(c, q.B, q.ldb, 0, tb != 0, (int)q.N, (int)q.K, 1, 0b010);
     if (!pa[i].direct) { offA[i] = scratch_bytes; scratch_bytes += round_up(pa[i].bytes, 256); }
     if (!pb[i].direct) { offB[i] = scratch_bytes; scratch_bytes += round_up(pb[i].bytes, 256); }
-    const int tm = (int)((q.M + tc::kBM - 1) / tc::kBM), tn = (int)((q.N + c.bn - 1) / c.bn);
+    const int tm = row_units(q.M, c.pair), tn = (int)((q.N + c.bn - 1) / c.bn);
     tiles += (int64_t)tm * tn;
     if (tiles >= (1ll << 31)) return GEMM_ERR_UNSUPPORTED;
   }
@@ -423,7 +456,7 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
     tc::GroupDesc& d = descs[i];
     std::memset(&d, 0, sizeof(d));
     if (!make_map(&d.tmA, Aop, op_bf16, Kop, q.M > 0 ? q.M : 1, pa[i].ld, 1, tc::kBM) ||
-        !make_map(&d.tmB, Bop, op_bf16, Kop, q.N > 0 ? q.N : 1, pb[i].ld, 1, c.bn)) {
+        !make_map(&d.tmB, Bop, op_bf16, Kop, q.N > 0 ? q.N : 1, pb[i].ld, 1, c.pair ? c.bn / 2 : c.bn)) {
       plan_free(p);
       return GEMM_ERR_MISALIGNED;
     }
@@ -432,7 +465,7 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
     d.M = (int)q.M;
     d.N = (int)q.N;
     d.k_blocks = (int)((Kop * op_elem + 127) / 128);
-    d.tiles_m = (int)((q.M + tc::kBM - 1) / tc::kBM);
+    d.tiles_m = row_units(q.M, c.pair);
     d.tiles_n = (int)((q.N + c.bn - 1) / c.bn);
     d.tile_start = tile_start;
     d.vecC = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0);
@@ -468,7 +501,7 @@ gemm_status_t gemm_grouped_run(gemm_grouped_plan_t p, void* stream) {
   tc::TcArgs a;
   std::memset(&a, 0, sizeof(a));
   a.num_tiles = p->total_tiles;
-  a.raster = p->cfg.raster;
+  a.raster = 0;
   a.status = status;
   tc::GroupArgs g{p->descs, p->count};
   CUtensorMap dummy;

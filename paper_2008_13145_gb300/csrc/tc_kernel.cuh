@@ -86,9 +86,13 @@ struct TileLoc {
   float alpha, beta;
 };
 
-template <bool GROUPED>
+// With PAIR, tile units count pairs of vertically adjacent 128-row tiles:
+// tiles_m is in pair units and CTA `rank` of the cluster takes row tile
+// 2 * unit + rank (the odd pair's second tile may lie past M: its loads
+// zero-fill and its stores are skipped).
+template <bool GROUPED, bool PAIR = false>
 __device__ __forceinline__ TileLoc locate(const TcArgs& p, const GroupArgs& g, const CUtensorMap* ma,
-                                          const CUtensorMap* mb, int tile) {
+                                          const CUtensorMap* mb, int tile, int rank = 0) {
   TileLoc L;
   if constexpr (GROUPED) {
     int lo = 0, hi = g.count - 1;  // last problem whose tile_start <= tile
@@ -107,6 +111,7 @@ __device__ __forceinline__ TileLoc locate(const TcArgs& p, const GroupArgs& g, c
     L.M = p.M; L.N = p.N; L.k_blocks = p.k_blocks; L.vecC = p.vecC; L.alpha = p.alpha; L.beta = p.beta;
     tile_coords(p, tile, L.b, L.tm, L.tn);
   }
+  if (PAIR) L.tm = 2 * L.tm + rank;
   return L;
 }
 
@@ -137,7 +142,13 @@ __device__ __forceinline__ void store_row32(const TileLoc& p, float* crow, int n
   }
 }
 
-template <int BN, int STAGES, bool TF32, bool GROUPED>
+// PAIR: the kernel runs in clusters of two CTAs that compute vertically
+// adjacent tiles with the same B slice.  Each CTA loads its own A rows and
+// one half of the B slice, multicasting that half into both CTAs' rings, so a
+// CTA reads 16 KB + BN x 64 B per slice from L2 instead of 16 KB + BN x 128 B.
+// A ring slot is refilled only after both CTAs' MMAs released it: every MMA
+// commit arrives on the slot's empty barrier in both CTAs (2 arrivals).
+template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs p,
                    const GroupArgs g) {
@@ -147,11 +158,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_base_sh;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = PAIR ? (int)cluster_ctarank() : 0;
+  const int unit0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+      mbar_init(&empty_bar[s], PAIR ? 2 : 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&accf_bar[a], 1);
@@ -166,6 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 5) tmem_alloc<Cfg::TMEM_COLS>(&tmem_base_sh);
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // the peer's multicasts target barriers initialised above
   tc_fence_after();
   const uint32_t tmem_base = tmem_base_sh;
 
@@ -175,14 +190,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
-        const TileLoc L = locate<GROUPED>(p, g, &tmA, &tmB, tile);
+      for (int tile = unit0; tile < p.num_tiles && ok; tile += units) {
+        const TileLoc L = locate<GROUPED, PAIR>(p, g, &tmA, &tmB, tile, rank);
         for (int kb = 0; kb < L.k_blocks; ++kb) {
           if (!(ok = mbar_wait(&empty_bar[stage], phase ^ 1, p.status, kStatusTimeoutEmpty))) break;
           uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
           mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
           tma_load_3d(sa, L.ma, &full_bar[stage], kb * Cfg::BK, L.tm * kBM, L.b);
-          tma_load_3d(sa + Cfg::A_BYTES, L.mb, &full_bar[stage], kb * Cfg::BK, L.tn * BN, L.b);
+          if constexpr (PAIR) {
+            tma_load_3d_mcast(sa + Cfg::A_BYTES + rank * (Cfg::B_BYTES / 2), L.mb, &full_bar[stage], kb * Cfg::BK,
+                              L.tn * BN + rank * (BN / 2), L.b, (uint16_t)0x3);
+          } else {
+            tma_load_3d(sa + Cfg::A_BYTES, L.mb, &full_bar[stage], kb * Cfg::BK, L.tn * BN, L.b);
+          }
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1;
@@ -209,8 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int acc = 0;
       uint32_t acc_phase = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < p.num_tiles && ok; tile += gridDim.x) {
-        const int k_blocks = GROUPED ? locate<true>(p, g, &tmA, &tmB, tile).k_blocks : p.k_blocks;
+      for (int tile = unit0; tile < p.num_tiles && ok; tile += units) {
+        const int k_blocks = GROUPED ? locate<true, PAIR>(p, g, &tmA, &tmB, tile, rank).k_blocks : p.k_blocks;
         if (!(ok = mbar_wait(&acce_bar[acc], acc_phase ^ 1, p.status, kStatusTimeoutAccEmpty))) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
@@ -226,7 +246,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t bd = smem_desc_sw128(b_addr + koff, 16, 1024);
             mma<TF32>(d_tmem, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
           }
-          mma_commit(&empty_bar[stage]);  // frees the slice once these MMAs have read it
+          // frees the slot (in both CTAs of a pair) once these MMAs have read it
+          if constexpr (PAIR) mma_commit_mcast(&empty_bar[stage], (uint16_t)0x3);
+          else mma_commit(&empty_bar[stage]);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1;
@@ -244,10 +266,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------------- epilogue (warps 0..3)
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+    for (int tile = unit0; tile < p.num_tiles; tile += units) {
       if (!mbar_wait(&accf_bar[acc], acc_phase, p.status, kStatusTimeoutAcc)) break;
       tc_fence_after();
-      const TileLoc L = locate<GROUPED>(p, g, &tmA, &tmB, tile);
+      const TileLoc L = locate<GROUPED, PAIR>(p, g, &tmA, &tmB, tile, rank);
       const int row = L.tm * kBM + warp * 32 + lane;
       float* crow = L.C + (int64_t)L.b * L.strideC + (int64_t)row * L.ldc;
       const uint32_t tbase = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * BN);
@@ -272,6 +294,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     tmem_dealloc<Cfg::TMEM_COLS>(tmem_base);
   }
+  // Neither CTA of a pair leaves while the other may still multicast into its
+  // ring or commit to its barriers.
+  if (PAIR) cluster_sync();
 }
 
 }  // namespace tc

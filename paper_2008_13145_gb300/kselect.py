@@ -41,7 +41,8 @@ class Problem(ctypes.Structure):
 
 class Deployment(ctypes.Structure):
     _fields_ = [("precision", i32), ("n_configs", i32), ("config_ids", ctypes.POINTER(i32)),
-                ("n_nodes", i32), ("nodes", ctypes.POINTER(TreeNode)), ("mlp_params", ctypes.POINTER(f32))]
+                ("n_nodes", i32), ("nodes", ctypes.POINTER(TreeNode)), ("mlp_params", ctypes.POINTER(f32)),
+                ("n_known", i32), ("known_sizes", ctypes.POINTER(i64)), ("known_ids", ctypes.POINTER(i32))]
 
 
 def _sig(name, res, args):
@@ -84,6 +85,8 @@ _sig("gemm_benchmark_configs", i32, [i32, ctypes.POINTER(i32), ch, ch, i64, i64,
 _sig("kselect_normalise", i32, [i64, i32, vp, vp, i32, vp])
 _sig("kselect_kmeans", i32, [i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_uint32), i32, f32, vp, vp,
                              ctypes.POINTER(f64), ctypes.POINTER(i32), vp])
+_sig("kselect_pca", i32, [i32, i32, vp, i32, i32, vp, vp, vp, vp, ctypes.POINTER(f64), ctypes.POINTER(f64), vp])
+_sig("kselect_pca_backproject", i32, [i32, i32, i32, vp, vp, vp, vp, vp])
 _sig("kselect_score", i32, [i32, i32, vp, i32, ctypes.POINTER(i32), vp, f32, ctypes.POINTER(f64), vp])
 _sig("kselect_representatives", i32, [i32, i32, ctypes.POINTER(f32), i32, ctypes.POINTER(i32), i32,
                                       ctypes.POINTER(i32), ctypes.POINTER(i32)])
@@ -160,7 +163,8 @@ def config_params(cid: int) -> list[int]:
 class Handle:
     """An immutable library handle built from a deployment dict:
     {"precision": int, "config_ids": [...], "nodes": [{"feature", "threshold",
-    "left", "right", "label"}, ...], "mlp_params": [5192 floats] | None}."""
+    "left", "right", "label"}, ...], "mlp_params": [5192 floats] | None,
+    "known": [[M, N, K, batch, config id], ...] | None}."""
 
     def __init__(self, deployment: dict):
         ids = list(deployment["config_ids"])
@@ -171,8 +175,11 @@ class Handle:
             *[TreeNode(int(n["feature"]), int(n["left"]), int(n["right"]), int(n["label"]),
                        float(n["threshold"])) for n in nodes])
         self._mlp = (f32 * MLP_PARAMS)(*np.asarray(mlp, np.float32)) if mlp is not None else None
+        known = deployment.get("known") or []  # rows (M, N, K, batch, config id)
+        self._ksz = (i64 * max(4 * len(known), 1))(*[int(v) for r in known for v in r[:4]])
+        self._kid = (i32 * max(len(known), 1))(*[int(r[4]) for r in known])
         d = Deployment(int(deployment["precision"]), len(ids), self._ids, len(nodes), self._nodes,
-                       self._mlp if self._mlp is not None else None)
+                       self._mlp if self._mlp is not None else None, len(known), self._ksz, self._kid)
         h = vp()
         check(_lib.gemm_library_create(ctypes.byref(d), ctypes.byref(h)), "gemm_library_create")
         self.value = h.value
@@ -294,6 +301,23 @@ def kmeans(X, k: int, draws: np.ndarray, centres_out, labels_out, max_iter=300, 
     check(_lib.kselect_kmeans(n, d, k, dr.shape[0], ptr(X), pdr, max_iter, tol, ptr(centres_out), ptr(labels_out),
                               ctypes.byref(inertia), ctypes.byref(iters), stream_handle(stream)), "kselect_kmeans")
     return inertia.value, iters.value
+
+
+def pca(X, r: int, V0, mean_out, V_out, Y_out=None, iters: int = 60, stream=None):
+    """Returns (eigenvalues (r,), total variance); fills mean_out, V_out and optionally Y_out."""
+    n, d = X.shape
+    ev = np.zeros(r, np.float64)
+    tot = f64()
+    check(_lib.kselect_pca(n, d, ptr(X), r, iters, ptr(V0), ptr(mean_out), ptr(V_out), ptr(Y_out),
+                           ev.ctypes.data_as(ctypes.POINTER(f64)), ctypes.byref(tot), stream_handle(stream)),
+          "kselect_pca")
+    return ev, tot.value
+
+
+def pca_backproject(cent, V, mean, out, stream=None) -> None:
+    k, r = cent.shape
+    check(_lib.kselect_pca_backproject(k, V.shape[0], r, ptr(cent), ptr(V), ptr(mean), ptr(out), stream_handle(stream)),
+          "kselect_pca_backproject")
 
 
 def score(perf, deployed_cols=None, chosen=None, floor=1e-6, stream=None) -> dict:
@@ -421,6 +445,6 @@ def exported_symbols() -> list[str]:
             "gemm_config_params", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
             "gemm_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
             "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
-            "kselect_representatives", "kselect_top_n", "kselect_tree_train", "mlp_features", "mlp_forward", "mlp_loss_grad",
+            "kselect_representatives", "kselect_top_n", "kselect_tree_train", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
             "gemm_grouped_plan_destroy", "gemm_grouped"]

@@ -157,6 +157,34 @@ def prune(perf_train: np.ndarray, k: int, seed: int = 0, norm: str = "standard",
             "labels": lab.cpu().numpy().tolist()}
 
 
+def prune_pca(perf_train: np.ndarray, k: int, seed: int = 0, norm: str = "standard", n_init: int = 10,
+              var_frac: float = 0.95, r_max: int = 32) -> dict:
+    """PCA + k-means pruning (Section 4.1): k-means in the space of the leading
+    principal components that explain `var_frac` of the variance; each centre
+    is mapped back to a performance vector before taking its best configuration."""
+    import torch
+    ks = _ks()
+    P = torch.from_numpy(np.ascontiguousarray(perf_train, np.float32)).cuda()
+    X = torch.empty_like(P)
+    ks.normalise(P, X, norm)
+    n, d = X.shape
+    r_max = min(r_max, d, n - 1)
+    V0 = torch.from_numpy(wl.rng_for(seed, 51).standard_normal((d, r_max)).astype(np.float32)).cuda()
+    mean, V = torch.empty(d, device="cuda"), torch.empty((d, r_max), device="cuda")
+    ev, tot = ks.pca(X, r_max, V0, mean, V)
+    r = int(min(r_max, np.searchsorted(np.cumsum(ev) / tot, var_frac - 1e-12) + 1))
+    Vr, Y = torch.empty((d, r), device="cuda"), torch.empty((n, r), device="cuda")
+    ks.pca(X, r, V0[:, :r].contiguous(), mean, Vr, Y)
+    cen = torch.empty((k, r), device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    inertia, iters = ks.kmeans(Y, k, kmeans_draws(n_init, k, seed), cen, lab)
+    back = torch.empty((k, d), device="cuda")
+    ks.pca_backproject(cen, Vr, mean, back)
+    cols = ks.representatives(back.cpu().numpy(), lab.cpu().numpy(), dedupe=True)
+    return {"cols": [int(c) for c in cols], "inertia": inertia, "iters": iters, "components": r,
+            "explained": float(np.sum(ev[:r]) / tot), "labels": lab.cpu().numpy().tolist()}
+
+
 def features(shapes) -> np.ndarray:
     return np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
 
@@ -184,18 +212,22 @@ def evaluate(perf_test: np.ndarray, shapes_test, deployment: dict, all_ids: list
             "chosen_cols": chosen.tolist()}
 
 
-def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard", split_seed: int = 1) -> dict:
+def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard", split_seed: int = 1,
+           method: str = "kmeans") -> dict:
     shapes, perf, ids, precision = load_table(table_path)
     tr, te = wl.train_test_split(len(shapes), split_seed)
-    pr = prune(perf[tr], k, seed, norm)
+    pr = prune(perf[tr], k, seed, norm) if method == "kmeans" else prune_pca(perf[tr], k, seed, norm)
     nodes = train_tree(perf[tr], [shapes[i] for i in tr], pr["cols"], tree)
     dep = {"precision": precision, "config_ids": [ids[c] for c in pr["cols"]], "nodes": nodes}
     ev = evaluate(perf[te], [shapes[i] for i in te], dep, ids)
+    # Benchmarked (training) sizes keep their exhaustive-best kernel at run time.
+    dep["known"] = [[shapes[i].M, shapes[i].N, shapes[i].K, shapes[i].batch, ids[int(np.argmax(perf[i]))]]
+                    for i in tr]
     ks = _ks()
     topn = [int(c) for c in ks.top_n(perf[tr].astype(np.float32), len(pr["cols"]))]
     import torch
     ev["top_n"] = ks.score(torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda(), topn)
-    dep["meta"] = {"k": k, "tree": tree, "norm": norm, "kmeans_seed": seed, "split_seed": split_seed,
+    dep["meta"] = {"k": k, "tree": tree, "norm": norm, "method": method, "kmeans_seed": seed, "split_seed": split_seed,
                    "n_train": len(tr), "n_test": len(te), "inertia": pr["inertia"],
                    "scores": {key: v for key, v in ev.items() if key != "chosen_cols"}}
     return dep
@@ -291,6 +323,27 @@ def mlp_study(deploy_path: str, sweep_path: str, n: int = 2500, seed: int = 4, s
     return {"params": params.tolist(), "study": res}
 
 
+# ---------------------------------------------------------------- pruning study (Figures 5-6 analogue)
+def pruning_study(table_path: str, k_values=range(4, 16), seed: int = 0, split_seed: int = 1) -> dict:
+    """Held-out deployed-set maximum (geometric mean of the best deployed
+    kernel's fraction of the per-shape optimum) for k-means and PCA + k-means
+    pruning under each normalisation of Section 3.4 and for the Top-N
+    baseline, k = 4..15."""
+    import torch
+    ks = _ks()
+    shapes, perf, ids, _ = load_table(table_path)
+    tr, te = wl.train_test_split(len(shapes), split_seed)
+    P = torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda()
+    out = {"k": list(k_values), "kmeans": {}, "pca_kmeans": {}, "top_n": []}
+    for norm in ("standard", "raw_cutoff", "standard_cutoff", "sigmoid"):
+        out["kmeans"][norm] = [ks.score(P, prune(perf[tr], k, seed, norm)["cols"])["geomean"] for k in k_values]
+        out["pca_kmeans"][norm] = [ks.score(P, prune_pca(perf[tr], k, seed, norm)["cols"])["geomean"]
+                                   for k in k_values]
+    out["top_n"] = [ks.score(P, [int(c) for c in ks.top_n(perf[tr].astype(np.float32), k)])["geomean"]
+                    for k in k_values]
+    return out
+
+
 # ---------------------------------------------------------------- grouped launch (autotuned tile shape)
 def grouped_workload(family: int, n: int = 256, seed: int = 3, data_seed: int = 500):
     """Device buffers of the uneven group (M, N, K log-uniform in [32, 4096]), K-contiguous operands."""
@@ -359,21 +412,31 @@ def vgg_study(deploy_path: str, sweep_path: str, batches=(1, 16)) -> dict:
     perf = sweep(shapes, prec, sweep_path, seed=77, config_ids=ids)
     h = ks.Handle(dep)
     col = {c: j for j, c in enumerate(ids)}
+    mlp = mlp_choose(np.asarray(dep["mlp_params"], np.float32), shapes, dep["config_ids"]) \
+        if dep.get("mlp_params") else None
     rows, tot = [], {}
-    for (b, name, sh), p in zip(layers, perf):
+    for i, ((b, name, sh), p) in enumerate(zip(layers, perf)):
         sel = ks.select_kernel(h, sh.M, sh.N, sh.K, sh.batch)
         best = int(np.argmax(p))
-        rows.append({"batch": b, "layer": name, "M": sh.M, "N": sh.N, "K": sh.K, "selected": sel,
-                     "selected_tflops": p[col[sel]] / 1e3, "best": ids[best], "best_tflops": p[best] / 1e3,
-                     "ratio": p[col[sel]] / p[best] if p[best] > 0 else 0.0})
-        t = tot.setdefault(b, [0.0, 0.0, 0.0])
-        t[0] += sh.flops / (p[col[sel]] * 1e6)  # ms with the selected kernel
+        r = {"batch": b, "layer": name, "M": sh.M, "N": sh.N, "K": sh.K, "selected": sel,
+             "selected_tflops": p[col[sel]] / 1e3, "best": ids[best], "best_tflops": p[best] / 1e3,
+             "ratio": p[col[sel]] / p[best] if p[best] > 0 else 0.0}
+        t = tot.setdefault(b, [0.0, 0.0, 0.0, 0.0])
+        t[0] += sh.flops / (p[col[sel]] * 1e6)  # ms with the tree's kernel
         t[1] += sh.flops / (p[best] * 1e6)      # ms with the per-layer best
         t[2] += sh.flops
-    totals = {str(b): {"selected_ms": v[0], "exhaustive_ms": v[1], "ratio": v[1] / v[0],
-                       "selected_tflops": v[2] / (v[0] * 1e9), "distinct_selected": len({r["selected"] for r in rows
-                                                                                         if r["batch"] == b})}
-              for b, v in tot.items()}
+        if mlp is not None:
+            m = int(mlp[i])
+            r.update({"mlp_selected": m, "mlp_tflops": p[col[m]] / 1e3, "mlp_ratio": p[col[m]] / p[best]})
+            t[3] += sh.flops / (p[col[m]] * 1e6)
+        rows.append(r)
+    totals = {}
+    for b, v in tot.items():
+        totals[str(b)] = {"selected_ms": v[0], "exhaustive_ms": v[1], "ratio": v[1] / v[0],
+                          "selected_tflops": v[2] / (v[0] * 1e9),
+                          "distinct_selected": len({r["selected"] for r in rows if r["batch"] == b})}
+        if mlp is not None:
+            totals[str(b)].update({"mlp_ms": v[3], "mlp_ratio": v[1] / v[3]})
     return {"layers": rows, "totals": totals}
 
 
@@ -396,6 +459,9 @@ def main(argv=None):
     cb.add_argument("--tables", nargs="+", required=True)
     cb.add_argument("--precision", default="f32")
     cb.add_argument("--out", required=True)
+    st = sub.add_parser("study")
+    st.add_argument("--table", required=True)
+    st.add_argument("--out", required=True)
     gr = sub.add_parser("grouped")
     gr.add_argument("--out", required=True)
     vg = sub.add_parser("vgg")
@@ -408,11 +474,18 @@ def main(argv=None):
     d.add_argument("--tree", default="B")
     d.add_argument("--norm", default="standard")
     d.add_argument("--seed", type=int, default=0)
+    d.add_argument("--method", default="kmeans", choices=["kmeans", "pca"])
     d.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     ks = _ks()
     if a.cmd == "combine":
         combine_tables(a.tables, a.out, ks.PRECISIONS[a.precision])
+        return
+    if a.cmd == "study":
+        r = pruning_study(a.table)
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps(r))
         return
     if a.cmd == "grouped":
         r = grouped_tune()
@@ -442,7 +515,7 @@ def main(argv=None):
         if a.table:
             save_table(a.table, shapes, perf, ks.config_ids(prec), prec)
     else:
-        dep = deploy(a.table, a.k, a.tree, a.seed, a.norm)
+        dep = deploy(a.table, a.k, a.tree, a.seed, a.norm, method=a.method)
         with open(a.out, "w") as f:
             json.dump(dep, f, indent=1)
         print(json.dumps(dep["meta"]["scores"], indent=1))

@@ -63,7 +63,7 @@ def test_tc_config_space(ks):
         for c in ids:
             p = ks.config_params(c)
             assert p[0] == prec and p[1] == 128 and p[2] in (64, 128, 256) and p[4] in (2, 3, 4)
-            assert p[3] == (32 if prec == ks.PREC_TF32 else 64)
+            assert p[3] == (32 if prec == ks.PREC_TF32 else 64) and p[5] in (0, 1)
     with pytest.raises(ks.KSelectError):
         ks.config_params(999)
 
@@ -113,6 +113,12 @@ def test_deployment_validation(ks):
     assert ks.Handle({"precision": 0, "config_ids": [5, 1201], "nodes": []}).ids == [5, 1201]
     with pytest.raises(ks.KSelectError):
         ks.Handle({"precision": 3, "config_ids": [1101], "nodes": []})
+    # benchmarked sizes take their measured best kernel, the rest the tree's choice
+    hk = ks.Handle({**ok, "known": [[100, 5, 5, 1, 77], [7, 8, 9, 2, 1201], [100, 5, 5, 1, 3]]})
+    assert ks.select_kernel(hk, 100, 5, 5, 1) == 77 and ks.select_kernel(hk, 7, 8, 9, 2) == 1201
+    assert ks.select_kernel(hk, 100, 5, 5, 2) == 1 and ks.select_kernel(hk, 101, 5, 5, 1) == 2
+    with pytest.raises(ks.KSelectError):
+        ks.Handle({**ok, "known": [[1, 1, 1, 1, 1001]]})
     h0 = ks.Handle({"precision": 0, "config_ids": [42], "nodes": []})
     assert ks.select_kernel(h0, 1, 1, 1, 1) == 42
 
