@@ -9,7 +9,8 @@ input resident in HBM.  The step's inputs total ~7 GB, far above the 129 MB
 L2, so consecutive steps start from a cold L2.
 
 Also reported: the same metric end to end from pinned host buffers
-(gemm_host: H2D copies, GEMM, D2H copy inside the timed region); the share of
+(gemm_host: H2D copies, GEMM, D2H copy inside the timed region; consecutive
+shapes alternate between two streams so copies overlap GEMMs); the share of
 the per-shape exhaustive optimum (each held-out size re-run with the best of
 all 576 configs from the GB300 sweep table, untimed pass); the dominant
 kernel's roofline; the FP64 CPU oracle timed on a bounded sample on the host
@@ -261,14 +262,21 @@ def run_ours(args, ws, rank, local):
         hosts.append((hA, hB, hC))
         h2d += hA.numel() * hA.element_size() + hB.numel() * hB.element_size()
         d2h += hC.numel() * 4
+    # Consecutive shapes alternate between two streams (each shape has its own
+    # device staging buffers), so one shape's copies overlap another's GEMM.
+    streams = [stream, torch.cuda.Stream(dev)]
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     e0.record(stream)
+    streams[1].wait_event(e0)
     for _ in range(args.steps):
-        for sh, (A, B, C, lda, ldb, ldc), (hA, hB, hC) in zip(shapes, bufs, hosts):
+        for i, (sh, (A, B, C, lda, ldb, ldc), (hA, hB, hC)) in enumerate(zip(shapes, bufs, hosts)):
             ks.gemm_host(handle, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, hA, lda, hB, ldb, 0.0, hC, ldc,
-                         sh.batch, A, B, C, stream)
+                         sh.batch, A, B, C, streams[i & 1])
+    done1 = torch.cuda.Event()
+    done1.record(streams[1])
+    stream.wait_event(done1)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_e2e = max_over_ranks(e0.elapsed_time(e1))

@@ -92,6 +92,48 @@ __device__ __forceinline__ float sel4(const float (&v)[4], int i) {
   return i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
 }
 
+// The TM x TN accumulator tile.  With TM even it is held as row pairs, so one
+// packed FMA (__ffma2_rn: two FP32 FMAs, each rounded exactly like fmaf)
+// updates rows i and i+1 of a column: the pair (a_i, a_i+1) arrives in
+// consecutive registers from the vector shared-memory loads and b_j is
+// duplicated once per column.  This halves the FMA instructions of the
+// issue-bound inner loop without changing any result bit.
+template <int TM, int TN>
+struct AccTile {
+  static constexpr bool PAIRED = (TM % 2 == 0);
+  float2 v2[PAIRED ? TM / 2 : 1][TN];
+  float v1[PAIRED ? 1 : TM][TN];
+
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+#pragma unroll
+      for (int i = 0; i < (PAIRED ? TM / 2 : 1); ++i) v2[i][j] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < (PAIRED ? 1 : TM); ++i) v1[i][j] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void fma(const float (&a)[TM], const float (&b)[TN]) {
+    if constexpr (PAIRED) {
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const float2 bj = make_float2(b[j], b[j]);
+#pragma unroll
+        for (int i = 0; i < TM / 2; ++i) v2[i][j] = __ffma2_rn(make_float2(a[2 * i], a[2 * i + 1]), bj, v2[i][j]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) v1[i][j] = fmaf(a[i], b[j], v1[i][j]);
+    }
+  }
+  __device__ __forceinline__ float get(int i, int j) const {
+    if constexpr (PAIRED) return (i & 1) ? v2[i / 2][j].y : v2[i / 2][j].x;
+    else return v1[i][j];
+  }
+};
+
 template <class Cfg>
 __device__ __forceinline__ void store_out(const GemmArgs& p, float* Cb, int gm, int gn, float v) {
   if (gm < p.M && gn < p.N) {
@@ -300,11 +342,8 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
   const float* Bb = static_cast<const float*>(p.B) + (int64_t)b * p.strideB;
   float* Cb = p.C + (int64_t)b * p.strideC;
 
-  float acc[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  AccTile<TM, TN> acc;
+  acc.zero();
 
   const int nk = (p.K + BK - 1) / BK;
   if constexpr (Cfg::STAGED) {
@@ -345,10 +384,7 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
 #pragma unroll
         for (int jc = 0; jc < TN / CN; ++jc)
           load_vec_smem<CN>(bv + jc * CN, Bs + k * Cfg::LDS_B + Cfg::swz_b(jc * (Cfg::WX * CN) + tx * CN, k));
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], bv[j], acc[i][j]);
+        acc.fma(a, bv);
       }
       if (more) {
         float* An = smem + ((kt + 1) & 1) * Cfg::STAGE_FLOATS;
@@ -420,15 +456,21 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
           }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 4; ++k) {
+          float ak[TM];
 #pragma unroll
-          for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i][k], bv[k][j], acc[i][j]);
+          for (int i = 0; i < TM; ++i) ak[i] = a[i][k];
+          acc.fma(ak, bv[k]);
+        }
       }
     }
   }
-  epilogue<Cfg>(p, Cb, m0, n0, tx, ty, acc);
+  float out[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) out[i][j] = acc.get(i, j);
+  epilogue<Cfg>(p, Cb, m0, n0, tx, ty, out);
 }
 
 template <int ID>

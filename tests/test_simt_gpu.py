@@ -189,3 +189,24 @@ def test_error_check_kernel_semantics(lib, torch):
     e = ks.error_check(tC, torch.from_numpy(ref).cuda(), torch.from_numpy(den).cuda(), rows=20, cols=21, batch=3,
                        ldc=24, strideC=480)
     assert e == float("inf")
+
+
+def test_gemm_host_round_trip(lib, torch):
+    """gemm_host: pinned host inputs copied to device staging, selected kernel, C copied back."""
+    ks = lib
+    h = ks.Handle({"precision": 0, "config_ids": [531, 173], "nodes": [
+        {"feature": 0, "threshold": 100.5, "left": 1, "right": 2, "label": 0},
+        {"feature": -1, "threshold": 0, "left": -1, "right": -1, "label": 1},
+        {"feature": -1, "threshold": 0, "left": -1, "right": -1, "label": 0}]})
+    for shape, beta in ((wl.Shape(77, 130, 45, 3, "T", "N"), 0.5), (wl.Shape(300, 64, 200, 1, "N", "T"), 0.0)):
+        A, B, C0 = wl.gemm_inputs(shape, seed=21, beta_nonzero=beta != 0)
+        hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+        hC = torch.from_numpy(np.where(np.isnan(C0), 0, C0).astype(np.float32)).pin_memory()
+        dA, dB, dC = torch.empty_like(hA, device="cuda"), torch.empty_like(hB, device="cuda"), \
+            torch.empty_like(hC, device="cuda")
+        ks.gemm_host(h, shape.transA, shape.transB, shape.M, shape.N, shape.K, 1.0, hA, A.shape[2], hB, B.shape[2],
+                     beta, hC, C0.shape[2], shape.batch, dA, dB, dC)
+        torch.cuda.synchronize()
+        ref, den = og.gemm(shape.transA, shape.transB, shape.M, shape.N, shape.K, 1.0, A, B, beta,
+                           np.where(np.isnan(C0), 0, C0))
+        assert og.error_ratio(hC.numpy()[:, :, :shape.N], ref, den) <= TOL_F32

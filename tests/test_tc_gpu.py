@@ -142,3 +142,29 @@ def test_misaligned_direct_operand_is_rewritten(lib, torch):
     ks.gemm_with_config(tc_ids(ks, "tf32")[0], "N", "T", M, N, K, 1.0, fa.data_ptr() + 4, K, tB, K, 0.0, C, N, 1)
     ref, den = og.gemm("N", "T", M, N, K, 1.0, A[None], B[None])
     assert og.error_ratio(C.cpu().numpy()[None], ref, den) <= 5e-3
+
+
+def test_mixed_family_deployment_through_gemm(lib, torch):
+    """The FP32-input deployment mixing SIMT and split-BF16x3 kernels: sizes that
+    select either family give FP32-level results through gemm()."""
+    import json
+    import os
+    ks = lib
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2008_13145_gb300",
+                        "deploy", "f32mix.json")
+    dep = json.load(open(path))
+    h = ks.Handle(dep)
+    fams = set()
+    for i, sh in enumerate(wl.shape_grid(60, 99)[:60]):
+        if sh.flops > 4e9:
+            continue
+        fams.add(ks.family_of(ks.select_kernel(h, sh.M, sh.N, sh.K, sh.batch)))
+        A, B, C0 = wl.gemm_inputs(sh, seed=300 + i)
+        tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        out = Out(torch, C0, 0.0, sh.N)
+        ks.gemm(h, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, tA, A.shape[2], tB, B.shape[2], 0.0, out.ptr,
+                C0.shape[2], sh.batch)
+        torch.cuda.synchronize()
+        ref, den = og.gemm(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, B, nthreads=og.max_threads())
+        assert og.error_ratio(out.result(sh.N), ref, den) <= 1e-5, (sh, ks.select_kernel(h, sh.M, sh.N, sh.K, sh.batch))
+    assert fams == {0, 3}, fams
