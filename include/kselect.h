@@ -282,6 +282,15 @@ gemm_status_t kselect_representatives(int32_t k, int32_t d, const float* centres
  * often (lowest index on ties), filled up by highest mean normalised value. */
 gemm_status_t kselect_top_n(int32_t n_rows, int32_t n_cols, const float* perf, int32_t n, int32_t* out_cols);
 
+/* Section 5.1 comparison classifier: k nearest neighbours (k <= 16).  For each
+ * of n_query rows of query_dev (d features), the k training rows of train_dev
+ * nearest in squared Euclidean distance (ties to the lower index) vote with
+ * labels_dev; the majority label (ties to the nearest tied label) goes to
+ * out_dev.  All arrays device, row-major. */
+gemm_status_t kselect_knn(int32_t n_train, int32_t n_query, int32_t d, const float* train_dev,
+                          const int32_t* labels_dev, const float* query_dev, int32_t k, int32_t* out_dev,
+                          void* stream);
+
 /* Section 5.1 (host): CART classification tree on features (n x 4 doubles:
  * M, N, K, batch) and labels (n, in [0, n_classes)).  Gini impurity with the
  * class sum in class order; thresholds at midpoints of consecutive distinct
@@ -357,6 +366,25 @@ gemm_status_t mlp_train(int32_t n, float* params_dev, const float* X_dev, const 
  * copied to the device on the first call per device. */
 gemm_status_t select_kernels_batched(gemm_handle_t handle, int32_t n, const int64_t* shapes_dev, int32_t* ids_dev,
                                      float* pred_dev, void* stream);
+
+/* ---------------------------------------------------------------- convolutional network layers
+ * Section 6 runs VGG16 inference on the library's matrix multiply.  With NHWC
+ * activations a 3x3 convolution (padding 1) is an im2col matrix times the
+ * weights stored Cout x 9 Cin (op(B) = B^T), and the GEMM output rows are the
+ * next NHWC activation.  All pointers device. */
+
+/* out (N*H*W rows, leading dimension ld >= 9 C): row (n, h, w), column
+ * (kh * 3 + kw) * C + c = x[n, h + kh - 1, w + kw - 1, c], 0 outside the image. */
+gemm_status_t kselect_im2col3x3(const float* x_dev, int32_t N, int32_t H, int32_t W, int32_t C, float* out_dev,
+                                int64_t ld, void* stream);
+
+/* y[r, j] = y[r, j] + bias[j] (bias may be NULL), then max(., 0) if relu. */
+gemm_status_t kselect_bias_act(float* y_dev, int64_t rows, int32_t cols, int64_t ld, const float* bias_dev,
+                               int32_t relu, void* stream);
+
+/* 2 x 2, stride 2 max pooling of NHWC x (H, W even) into out (N, H/2, W/2, C). */
+gemm_status_t kselect_maxpool2x2(const float* x_dev, int32_t N, int32_t H, int32_t W, int32_t C, float* out_dev,
+                                 void* stream);
 
 /* ---------------------------------------------------------------- error check
  * The judge of every GEMM result: err = max over entries of

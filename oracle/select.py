@@ -353,6 +353,24 @@ def tree_predict(nodes: list[dict], F: np.ndarray) -> np.ndarray:
     return out
 
 
+def knn_predict(train: np.ndarray, labels: np.ndarray, query: np.ndarray, k: int) -> np.ndarray:
+    """k nearest neighbours by squared Euclidean distance (ties to the lower
+    training index); majority label, ties to the label met first in
+    nearest-first order."""
+    train = np.asarray(train, np.float64)
+    out = np.empty(len(query), np.int64)
+    for q, x in enumerate(np.asarray(query, np.float64)):
+        d = ((train - x) ** 2).sum(axis=1)
+        nn = sorted(range(len(train)), key=lambda i: (d[i], i))[:k]
+        best, count = None, 0
+        for i in nn:
+            c = sum(1 for j in nn if labels[j] == labels[i])
+            if c > count:
+                best, count = labels[i], c
+        out[q] = best
+    return out
+
+
 TREES = {"A": (None, 1), "B": (6, 3), "C": (3, 4)}  # (max_depth, min samples per leaf), Section 5.1
 
 

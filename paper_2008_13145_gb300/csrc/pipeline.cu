@@ -6,6 +6,7 @@
 // representatives, the Top-N baseline and CART training of the classifier
 // whose nodes the launcher walks.
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <algorithm>
 #include <cmath>
@@ -254,6 +255,56 @@ __global__ void __launch_bounds__(kScoreThreads) score_kernel(const ScoreArgs a)
   }
 }
 
+// ------------------------------------------------------------------ k-NN (Section 5.1 comparison)
+constexpr int kKnnMax = 16;
+
+// One thread per query: the k nearest training points (squared Euclidean
+// distance over d features; ties to the lower training index), then the
+// majority label (ties to the label of the nearest among the tied).
+__global__ void knn_kernel(int n_train, int n_query, int d, const float* train, const int* labels,
+                           const float* query, int k, int* out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_query) return;
+  float bd[kKnnMax];
+  int bi[kKnnMax];
+  for (int j = 0; j < k; ++j) {
+    bd[j] = CUDART_INF_F;
+    bi[j] = -1;
+  }
+  const float* x = query + (int64_t)q * d;
+  for (int i = 0; i < n_train; ++i) {
+    const float* t = train + (int64_t)i * d;
+    float dist = 0.f;
+    for (int f = 0; f < d; ++f) {
+      const float u = x[f] - t[f];
+      dist = fmaf(u, u, dist);
+    }
+    if (dist < bd[k - 1]) {  // insert, keeping (distance, index) order; equal distances keep the earlier point
+      int j = k - 1;
+      while (j > 0 && bd[j - 1] > dist) {
+        bd[j] = bd[j - 1];
+        bi[j] = bi[j - 1];
+        --j;
+      }
+      bd[j] = dist;
+      bi[j] = i;
+    }
+  }
+  int best = -1, best_count = 0;
+  for (int j = 0; j < k; ++j) {  // candidates in nearest-first order
+    if (bi[j] < 0) continue;
+    const int lab = labels[bi[j]];
+    int c = 0;
+    for (int m = 0; m < k; ++m)
+      if (bi[m] >= 0 && labels[bi[m]] == lab) ++c;
+    if (c > best_count) {
+      best = lab;
+      best_count = c;
+    }
+  }
+  out[q] = best;
+}
+
 static gemm_status_t cuda_fail(cudaError_t e) {
   set_last_cuda_error(e);
   return GEMM_ERR_CUDA;
@@ -429,6 +480,18 @@ gemm_status_t kselect_score(int32_t n_rows, int32_t n_cols, const float* perf, i
   if (e != cudaSuccess) return cuda_fail(e);
   out[0] = h[0]; out[1] = h[1]; out[2] = h[2];
   return GEMM_OK;
+}
+
+gemm_status_t kselect_knn(int32_t n_train, int32_t n_query, int32_t d, const float* train, const int32_t* labels,
+                          const float* query, int32_t k, int32_t* out, void* stream) {
+  if (n_train < 1 || n_query < 0 || d < 1 || k < 1 || k > kKnnMax || k > n_train || !train || !labels ||
+      (n_query > 0 && (!query || !out)))
+    return GEMM_ERR_INVALID_ARG;
+  if (n_query == 0) return GEMM_OK;
+  knn_kernel<<<(n_query + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(n_train, n_query, d, train, labels,
+                                                                                  query, k, out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GEMM_OK : cuda_fail(e);
 }
 
 // Section 4.2: the best configuration of each centre, clusters in descending

@@ -88,6 +88,10 @@ _sig("kselect_kmeans", i32, [i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_uin
 _sig("kselect_pca", i32, [i32, i32, vp, i32, i32, vp, vp, vp, vp, ctypes.POINTER(f64), ctypes.POINTER(f64), vp])
 _sig("kselect_pca_backproject", i32, [i32, i32, i32, vp, vp, vp, vp, vp])
 _sig("kselect_score", i32, [i32, i32, vp, i32, ctypes.POINTER(i32), vp, f32, ctypes.POINTER(f64), vp])
+_sig("kselect_im2col3x3", i32, [vp, i32, i32, i32, i32, vp, i64, vp])
+_sig("kselect_bias_act", i32, [vp, i64, i32, i64, vp, i32, vp])
+_sig("kselect_maxpool2x2", i32, [vp, i32, i32, i32, i32, vp, vp])
+_sig("kselect_knn", i32, [i32, i32, i32, vp, vp, vp, i32, vp, vp])
 _sig("kselect_representatives", i32, [i32, i32, ctypes.POINTER(f32), i32, ctypes.POINTER(i32), i32,
                                       ctypes.POINTER(i32), ctypes.POINTER(i32)])
 _sig("kselect_top_n", i32, [i32, i32, ctypes.POINTER(f32), i32, ctypes.POINTER(i32)])
@@ -330,6 +334,24 @@ def score(perf, deployed_cols=None, chosen=None, floor=1e-6, stream=None) -> dic
     return {"geomean": out[0], "mean": out[1], "clamped": int(out[2])}
 
 
+def im2col3x3(x, N, H, W, C, out, ld, stream=None) -> None:
+    check(_lib.kselect_im2col3x3(ptr(x), N, H, W, C, ptr(out), ld, stream_handle(stream)), "kselect_im2col3x3")
+
+
+def bias_act(y, rows, cols, ld, bias, relu=True, stream=None) -> None:
+    check(_lib.kselect_bias_act(ptr(y), rows, cols, ld, ptr(bias), int(relu), stream_handle(stream)), "kselect_bias_act")
+
+
+def maxpool2x2(x, N, H, W, C, out, stream=None) -> None:
+    check(_lib.kselect_maxpool2x2(ptr(x), N, H, W, C, ptr(out), stream_handle(stream)), "kselect_maxpool2x2")
+
+
+def knn(train, labels, query, k: int, out, stream=None) -> None:
+    """k-nearest-neighbour labels of the query rows (device tensors)."""
+    check(_lib.kselect_knn(train.shape[0], query.shape[0], train.shape[1], ptr(train), ptr(labels), ptr(query), k,
+                           ptr(out), stream_handle(stream)), "kselect_knn")
+
+
 def representatives(centres: np.ndarray, labels: np.ndarray, dedupe=True) -> np.ndarray:
     k, d = centres.shape
     c, pc = _arr(centres, np.float32, f32)
@@ -445,6 +467,6 @@ def exported_symbols() -> list[str]:
             "gemm_config_params", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
             "gemm_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
             "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
-            "kselect_representatives", "kselect_top_n", "kselect_tree_train", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
+            "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_train", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
             "gemm_grouped_plan_destroy", "gemm_grouped"]

@@ -344,6 +344,62 @@ def pruning_study(table_path: str, k_values=range(4, 16), seed: int = 0, split_s
     return out
 
 
+# ---------------------------------------------------------------- classifiers (Tables 1-2 analogue)
+def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, split_seed: int = 1,
+                     n_bag: int = 16, mlp_steps: int = 3000) -> dict:
+    """For each deployed-set size k (PCA + k-means selection, as in Section 5),
+    the held-out geometric-mean fraction of the per-shape optimum reached by:
+    decision trees A/B/C, 1/3/7 nearest neighbours on the performance model's
+    features, bagged trees (n_bag bootstrap trees of type A, majority vote, from
+    seeded draws) and, for k <= 8, the MLP performance model."""
+    import torch
+    ks = _ks()
+    shapes, perf, ids, prec = load_table(table_path)
+    tr, te = wl.train_test_split(len(shapes), split_seed)
+    s_tr, s_te = [shapes[i] for i in tr], [shapes[i] for i in te]
+    P = torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda()
+    X_tr, X_te = mlp_features(s_tr), mlp_features(s_te)
+    F_tr, F_te = features(s_tr), features(s_te)
+    rng = wl.rng_for(seed, 61)
+    boot = rng.integers(0, len(tr), (n_bag, len(tr)))
+    out = {"k": list(k_values), "deployed_max": [], "classifiers": {}}
+
+    def add(name, cols_chosen):
+        out["classifiers"].setdefault(name, []).append(
+            ks.score(P, chosen=torch.from_numpy(np.asarray(cols_chosen, np.int32)).cuda())["geomean"])
+
+    def tree_predict(nodes, F):
+        hh = ks.Handle({"precision": prec, "config_ids": cfg_ids, "nodes": nodes})
+        col = {c: j for j, c in enumerate(cfg_ids)}
+        return np.array([col[ks.select_kernel(hh, int(f[0]), int(f[1]), int(f[2]), int(f[3]))] for f in F])
+
+    for k in k_values:
+        cols = prune_pca(perf[tr], k, seed)["cols"]
+        cfg_ids = [ids[c] for c in cols]
+        y = np.argmax(perf[tr][:, cols], axis=1).astype(np.int32)
+        out["deployed_max"].append(ks.score(P, cols)["geomean"])
+        for name, (depth, leaf) in TREES.items():
+            add(f"DecisionTree{name}", [cols[j] for j in tree_predict(ks.tree_train(F_tr, y, k, depth, leaf), F_te)])
+        yd = torch.from_numpy(y).cuda()
+        for nn in (1, 3, 7):
+            pred = torch.empty(len(te), dtype=torch.int32, device="cuda")
+            ks.knn(X_tr, yd, X_te, nn, pred)
+            add(f"{nn}NearestNeighbor", [cols[j] for j in pred.cpu().numpy()])
+        votes = np.zeros((len(te), k), np.int64)
+        for b in range(n_bag):
+            nodes = ks.tree_train(F_tr[boot[b]], y[boot[b]], k, None, 1)
+            votes[np.arange(len(te)), tree_predict(nodes, F_te)] += 1
+        add("BaggedTrees", [cols[j] for j in np.argmax(votes, axis=1)])
+        if k <= 8:
+            T, M = mlp_targets(np.pad(perf[tr][:, cols], ((0, 0), (0, 8 - k))))
+            params, _ = mlp_train_params(X_tr, T, M, steps=mlp_steps, seed=seed)
+            col = {c: j for j, c in enumerate(cfg_ids)}
+            add("MLP", [cols[col[c]] for c in mlp_choose(params, s_te, cfg_ids)])
+        else:
+            out["classifiers"].setdefault("MLP", []).append(None)
+    return out
+
+
 # ---------------------------------------------------------------- grouped launch (autotuned tile shape)
 def grouped_workload(family: int, n: int = 256, seed: int = 3, data_seed: int = 500):
     """Device buffers of the uneven group (M, N, K log-uniform in [32, 4096]), K-contiguous operands."""
@@ -459,6 +515,9 @@ def main(argv=None):
     cb.add_argument("--tables", nargs="+", required=True)
     cb.add_argument("--precision", default="f32")
     cb.add_argument("--out", required=True)
+    cl = sub.add_parser("classifiers")
+    cl.add_argument("--table", required=True)
+    cl.add_argument("--out", required=True)
     st = sub.add_parser("study")
     st.add_argument("--table", required=True)
     st.add_argument("--out", required=True)
@@ -480,6 +539,12 @@ def main(argv=None):
     ks = _ks()
     if a.cmd == "combine":
         combine_tables(a.tables, a.out, ks.PRECISIONS[a.precision])
+        return
+    if a.cmd == "classifiers":
+        r = classifier_study(a.table)
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps(r))
         return
     if a.cmd == "study":
         r = pruning_study(a.table)

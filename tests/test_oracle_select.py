@@ -203,3 +203,13 @@ def test_pca_top_eigenpairs():
     assert np.allclose(cov @ v, v * w, atol=1e-10)
     assert np.allclose(v.T @ v, np.eye(3), atol=1e-12)
     assert tot == pytest.approx(np.trace(cov)) and np.all(np.diff(w) <= 0)
+
+
+def test_knn_by_hand():
+    train = np.array([[0.0], [1.0], [2.0], [10.0], [11.0]])
+    labels = np.array([0, 1, 1, 2, 2])
+    assert list(osel.knn_predict(train, labels, np.array([[0.2], [10.4], [1.6]]), 1)) == [0, 2, 1]
+    # 3-NN of 1.0: points 1.0, 0.0 and 2.0 (0.0 before 2.0 on the distance tie) -> labels {1, 0, 1} -> 1
+    assert list(osel.knn_predict(train, labels, np.array([[1.0]]), 3)) == [1]
+    # 2-NN of 0.5: labels 0 and 1 tie -> the nearer (index 0 first on the distance tie) wins
+    assert list(osel.knn_predict(train, labels, np.array([[0.5]]), 2)) == [0]

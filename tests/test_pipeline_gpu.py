@@ -86,3 +86,15 @@ def test_score(lib, torch, which):
     assert got["geomean"] == pytest.approx(want["geomean"], rel=1e-5)
     assert got["mean"] == pytest.approx(want["mean"], rel=1e-5)
     assert got["clamped"] == want["clamped"]
+
+
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_knn_matches_oracle(lib, torch, k):
+    rng = np.random.default_rng(k)
+    train = rng.random((400, 7)).astype(np.float32)
+    labels = rng.integers(0, 5, 400).astype(np.int32)
+    query = rng.random((300, 7)).astype(np.float32)
+    out = torch.empty(300, dtype=torch.int32, device="cuda")
+    lib.knn(torch.from_numpy(train).cuda(), torch.from_numpy(labels).cuda(), torch.from_numpy(query).cuda(), k, out)
+    want = osel.knn_predict(train.astype(np.float64), labels, query.astype(np.float64), k)
+    assert np.array_equal(out.cpu().numpy(), want)
