@@ -400,3 +400,111 @@ def pca_top(X: np.ndarray, r: int):
 
 def components_for(explained: np.ndarray, frac: float) -> int:
     return int(np.searchsorted(np.cumsum(explained), frac - 1e-12) + 1)
+
+
+# ----------------------------------------------------------------------------- Section 4.1, decision tree
+def leaf_sse(Y: np.ndarray) -> float:
+    """Sum over outputs of the squared deviations from the leaf mean."""
+    if len(Y) == 0:
+        return 0.0
+    return float(np.sum((Y - Y.mean(axis=0)) ** 2))
+
+
+def regression_split(F: np.ndarray, Y: np.ndarray, idx: np.ndarray):
+    """Best split of the samples `idx` for a multi-output regression tree: the
+    (feature, midpoint threshold) with the largest drop of summed squared error,
+    features in order and thresholds ascending, the first best kept.  Returns
+    (gain, feature, threshold) or None when no split separates the samples."""
+    parent = leaf_sse(Y[idx])
+    best = None
+    for f in range(F.shape[1]):
+        vals = np.unique(F[idx, f])
+        for a, b in zip(vals[:-1], vals[1:]):
+            thr = (a + b) / 2.0
+            left = idx[F[idx, f] <= thr]
+            right = idx[F[idx, f] > thr]
+            gain = parent - leaf_sse(Y[left]) - leaf_sse(Y[right])
+            if best is None or gain > best[0]:
+                best = (gain, f, thr)
+    return best
+
+
+def tree_regression_partition(F: np.ndarray, Y: np.ndarray, max_leaves: int):
+    """Section 4.1 "Decision tree": a regression tree from the sizes F (n x 4) to
+    the normalised performance vectors Y (n x d), limited to `max_leaves` leaves.
+
+    Grown best-first: while there are fewer than max_leaves leaves, split the
+    leaf whose best split removes the most squared error (lowest leaf index on
+    ties).  Growth stops when no split removes more than 1e-12 of the root's
+    squared error (rounding noise of leaves that are already constant).  A split
+    leaf keeps its index for the left part and the right part becomes a new last
+    leaf.  Returns (labels: leaf index per sample, centres: mean of Y per leaf)."""
+    n = len(F)
+    leaves = [np.arange(n)]
+    splits = [regression_split(F, Y, leaves[0])]
+    tol = 1e-12 * leaf_sse(Y)
+    while len(leaves) < max_leaves:
+        cand = [(s[0], i) for i, s in enumerate(splits) if s is not None and s[0] > tol]
+        if not cand:
+            break
+        gain, i = max(cand, key=lambda t: (t[0], -t[1]))
+        _, f, thr = splits[i]
+        idx = leaves[i]
+        left, right = idx[F[idx, f] <= thr], idx[F[idx, f] > thr]
+        leaves[i] = left
+        leaves.append(right)
+        splits[i] = regression_split(F, Y, left)
+        splits.append(regression_split(F, Y, right))
+    labels = np.empty(n, np.int64)
+    centres = np.empty((len(leaves), Y.shape[1]))
+    for j, idx in enumerate(leaves):
+        labels[idx] = j
+        centres[j] = Y[idx].mean(axis=0)
+    return labels, centres
+
+
+# ----------------------------------------------------------------------------- Section 4.1, spectral clustering
+def rbf_affinity(X: np.ndarray, gamma: float) -> np.ndarray:
+    """Similarity graph as an adjacency matrix: A_ij = exp(-gamma |x_i - x_j|^2), zero diagonal."""
+    n = len(X)
+    A = np.empty((n, n))
+    for i in range(n):
+        A[i] = np.exp(-gamma * np.sum((X - X[i]) ** 2, axis=1))
+    np.fill_diagonal(A, 0.0)
+    return A
+
+
+def spectral_embedding(A: np.ndarray, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """Coordinates from the Laplacian of the adjacency matrix: the k eigenvectors
+    of the normalised Laplacian L = I - D^-1/2 A D^-1/2 with the smallest
+    eigenvalues (equivalently the largest of S = D^-1/2 A D^-1/2), each row then
+    scaled to unit length.  Returns (rows n x k, eigenvalues of S, descending)."""
+    d = A.sum(axis=1)
+    s = 1.0 / np.sqrt(d)
+    S = A * s[:, None] * s[None, :]
+    w, V = np.linalg.eigh(S)
+    order = np.argsort(-w, kind="stable")[:k]
+    U = V[:, order]
+    U = U / np.linalg.norm(U, axis=1, keepdims=True)
+    return U, w[order]
+
+
+def spectral_partition(X: np.ndarray, k: int, gamma: float, uniforms: np.ndarray):
+    """Section 4.1 "Spectral clustering": k-means (same seeding draws as the
+    direct k-means) on the spectral coordinates of the RBF similarity graph.
+    Returns (labels, inertia in the embedding)."""
+    U, _ = spectral_embedding(rbf_affinity(X, gamma), k)
+    _, labels, inertia, _ = kmeans(U, k, uniforms)
+    return labels, inertia
+
+
+def cluster_geomean_centres(X: np.ndarray, labels: np.ndarray, k: int, floor: float = 1e-6) -> np.ndarray:
+    """Section 4.2 for label-only clusterings: each cluster's geometric-mean
+    performance vector (values clamped at ``floor``); an empty cluster gives zeros.
+    The deployed configurations are then `representatives` of these centres."""
+    out = np.zeros((k, X.shape[1]))
+    for c in range(k):
+        m = X[labels == c]
+        if len(m):
+            out[c] = np.exp(np.mean(np.log(np.maximum(m, floor)), axis=0))
+    return out

@@ -213,3 +213,105 @@ def test_knn_by_hand():
     assert list(osel.knn_predict(train, labels, np.array([[1.0]]), 3)) == [1]
     # 2-NN of 0.5: labels 0 and 1 tie -> the nearer (index 0 first on the distance tie) wins
     assert list(osel.knn_predict(train, labels, np.array([[0.5]]), 2)) == [0]
+
+
+# ---------------------------------------------------------------- regression-tree pruning (Section 4.1)
+def planted_regions(seed, n=60, d=7):
+    """Sizes whose performance vector depends only on which of three M ranges they fall in."""
+    rng = np.random.default_rng(seed)
+    F = np.column_stack([rng.permutation(n) * 10.0 + 16, rng.integers(16, 4096, n), rng.integers(16, 4096, n),
+                         rng.choice([1, 2, 4, 8, 16], n)]).astype(np.float64)
+    region = np.digitize(F[:, 0], [200.0, 450.0])
+    proto = rng.random((3, d))
+    return F, proto[region], region
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tree_regression_recovers_planted_regions(seed):
+    F, Y, region = planted_regions(seed)
+    labels, centres = osel.tree_regression_partition(F, Y, 3)
+    # same partition (leaf numbering is the tree's own)
+    pairs = set(zip(labels.tolist(), region.tolist()))
+    assert len(pairs) == 3 and len({a for a, _ in pairs}) == 3 and len({b for _, b in pairs}) == 3
+    for j in range(3):
+        assert np.allclose(centres[j], Y[labels == j].mean(axis=0), rtol=0, atol=1e-15)
+    # no gain left once the planted regions are separated: growth stops at 3 leaves
+    labels5, _ = osel.tree_regression_partition(F, Y, 5)
+    assert labels5.max() == 2
+
+
+def test_tree_regression_limits_and_monotone_error():
+    rng = np.random.default_rng(4)
+    F = rng.random((40, 4)) * 1000
+    Y = rng.random((40, 5))
+    l1, c1 = osel.tree_regression_partition(F, Y, 1)
+    assert np.all(l1 == 0) and np.allclose(c1[0], Y.mean(axis=0))
+    sse = []
+    for k in range(1, 12):
+        labels, centres = osel.tree_regression_partition(F, Y, k)
+        assert labels.max() == k - 1 and sorted(set(labels.tolist())) == list(range(k))
+        sse.append(sum(osel.leaf_sse(Y[labels == j]) for j in range(k)))
+    assert all(b <= a + 1e-12 for a, b in zip(sse, sse[1:]))
+    labels, _ = osel.tree_regression_partition(F, Y, 40)  # every sample alone
+    assert len(set(labels.tolist())) == 40
+
+
+@pytest.mark.parametrize("k", [2, 3, 5, 8])
+def test_tree_regression_matches_sklearn(k):
+    """scikit-learn's best-first regression tree (max_leaf_nodes) gives the same
+    partition on tie-free continuous data."""
+    tree = pytest.importorskip("sklearn.tree")
+    rng = np.random.default_rng(10 + k)
+    F = rng.random((80, 4)) * 4096
+    Y = rng.random((80, 6)) ** 3
+    labels, _ = osel.tree_regression_partition(F, Y, k)
+    sk = tree.DecisionTreeRegressor(max_leaf_nodes=k, random_state=0).fit(F, Y)
+    leaf = sk.apply(F)
+    assert len(set(leaf.tolist())) == k
+    assert len(set(zip(labels.tolist(), leaf.tolist()))) == k
+
+
+# ---------------------------------------------------------------- spectral clustering (Section 4.1)
+def test_spectral_embedding_matches_normalised_laplacian():
+    """The embedding's eigenvalues are 1 - (smallest eigenvalues of scipy's
+    normalised Laplacian); the top one is exactly 1 with eigenvector D^1/2 1."""
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    rng = np.random.default_rng(5)
+    X = rng.random((30, 6))
+    A = osel.rbf_affinity(X, 0.7)
+    assert np.all(np.diag(A) == 0) and np.allclose(A, A.T)
+    U, w = osel.spectral_embedding(A, 4)
+    L = csgraph.laplacian(A, normed=True)
+    lw = np.linalg.eigvalsh(L)
+    assert np.allclose(np.sort(1.0 - w), lw[:4], atol=1e-12)
+    assert w[0] == pytest.approx(1.0, abs=1e-12)
+    assert np.allclose(np.linalg.norm(U, axis=1), 1.0)
+    # the top eigenvector of S is D^1/2 1 (normalised): rows of U before scaling
+    d = A.sum(axis=1)
+    S = A / np.sqrt(d)[:, None] / np.sqrt(d)[None, :]
+    v = np.sqrt(d) / np.linalg.norm(np.sqrt(d))
+    assert np.allclose(S @ v, v, atol=1e-12)
+
+
+def test_spectral_partition_separates_distant_blobs():
+    """Three far-apart blobs: the graph has three (numerically) disconnected
+    components, eigenvalue 1 has multiplicity 3 and the partition is the blobs."""
+    rng = np.random.default_rng(6)
+    centres = np.array([[0.0] * 5, [10.0] * 5, [0.0, 10.0, 0.0, 10.0, 0.0]])
+    truth = np.repeat(np.arange(3), 12)
+    X = centres[truth] + 0.05 * rng.standard_normal((36, 5))
+    U, w = osel.spectral_embedding(osel.rbf_affinity(X, 1.0), 3)
+    assert np.allclose(w, 1.0, atol=1e-9)
+    u = rng.random((4, 3))
+    labels, inertia = osel.spectral_partition(X, 3, 1.0, u)
+    assert len(set(zip(labels.tolist(), truth.tolist()))) == 3
+    assert inertia < 1e-6
+
+
+def test_cluster_geomean_centres():
+    X = np.array([[1.0, 0.5], [0.25, 1.0], [0.5, 0.5], [1.0, 0.0]])
+    labels = np.array([0, 0, 1, 1])
+    C = osel.cluster_geomean_centres(X, labels, 3, floor=1e-6)
+    assert C[0] == pytest.approx([0.5, math.sqrt(0.5)], rel=1e-15)
+    assert C[1] == pytest.approx([math.sqrt(0.5), math.sqrt(0.5e-6)], rel=1e-15)
+    assert np.all(C[2] == 0)  # empty cluster
