@@ -74,13 +74,44 @@ int32_t gemm_last_cuda_error(void);
  * tile or a cluster of two CTAs on vertically adjacent tiles that share the B
  * slice by TMA multicast: 18 configs per family.
  *
+ * Split-K kind (Section 6 describes comparison libraries whose kernels for
+ * tall, skinny matrices compute partial results combined by a final
+ * reduction; Section 3.2 notes that such shapes behave differently): here it
+ * is one more kernel kind to select.  Id 2000 + b runs FP32 config b (staged, BK
+ * 16 or 32: 192 ids) with K divided among CTAs whenever its output tiles
+ * alone would leave the GPU's resident-CTA slots (SMs x CTAs per SM) largely
+ * idle.  Split s writes the partial product of K range [s * kchunk,
+ * (s + 1) * kchunk) to a stream-ordered workspace (at most 256 MB, taken from a
+ * per-device memory pool, or from the default pool while the stream is being
+ * captured), and a second kernel sums the partials in split order and applies
+ * alpha and beta: results are deterministic but rounded differently from the
+ * base config.  gemm_config_count(GEMM_PREC_F32) = 576 + 192; indexes 576.. map
+ * to the split-K ids in ascending base order.
+ *
  * gemm_config_params writes 8 integers:
- *   F32: {family=0, TM, TN, WX, WY, BK, staged, 0}
+ *   F32: {family=0, TM, TN, WX, WY, BK, staged, splitk (0 or 1)}
  *   TC : {family, BM=128, BN, BK (elements per 128-byte row), stages, pair (0 or 1), 0, 0}
  */
 int32_t gemm_config_count(int32_t precision);
 int32_t gemm_config_id(int32_t precision, int32_t index);
 gemm_status_t gemm_config_params(int32_t config_id, int32_t out_params[8]);
+
+/* Split decision of the split-K kind, as a pure host function: the split
+ * factor S >= 1 (a negative gemm_status_t on invalid arguments) for an
+ * M x N x K x batch product with BM x BN tiles and K-step BK when
+ * `resident_ctas_per_sm` CTAs fit on each of `sm_count` SMs; *kchunk receives
+ * the K range per split (a multiple of BK; K when S == 1).  The factor
+ * minimises (waves of tiles x S) x (K-steps per split + 2 for a CTA's start-up
+ * and epilogue) plus the reduction's traffic, splits only when that saves at least 10 %, gives each split a
+ * K range of at least 4 K-steps (the last one may be shorter), S <= 16,
+ * batch x S <= 65535 and the workspace <= 256 MB. */
+int32_t gemm_split_choose(int64_t M, int64_t N, int64_t K, int64_t batch, int32_t BM, int32_t BN, int32_t BK,
+                          int32_t resident_ctas_per_sm, int32_t sm_count, int32_t* kchunk);
+
+/* The split factor config `config_id` uses for these sizes on the current
+ * device (1 for every config outside the split-K kind; needs a GPU for the
+ * occupancy query); *kchunk as above.  Negative gemm_status_t on error. */
+int32_t gemm_split_factor(int32_t config_id, int64_t M, int64_t N, int64_t K, int64_t batch, int32_t* kchunk);
 
 /* ---------------------------------------------------------------- deployment
  * Section 5: the deployed set (<= 16 configs of one family) and a decision
@@ -148,6 +179,22 @@ gemm_status_t gemm_host(gemm_handle_t handle, char transA, char transB, int64_t 
                         float alpha, const void* A_host, int64_t lda, const void* B_host, int64_t ldb,
                         float beta, float* C_host, int64_t ldc, int64_t batch, void* A_dev, void* B_dev,
                         float* C_dev, void* stream);
+
+/* gemm() with explicit batch strides, in elements: batch entry b uses
+ * A + b * strideA, B + b * strideB, C + b * strideC.  strideA and strideB may be
+ * any value >= 0 (0 uses one matrix for every entry, e.g. shared weights);
+ * strideC must be >= ldc * M when batch > 1.  Tensor-core kernels read an
+ * operand in place only when it is batch-packed (stride = ld x stored rows),
+ * otherwise their pre-pass packs it first.  Errors as gemm(). */
+gemm_status_t gemm_strided_batched(gemm_handle_t handle, char transA, char transB, int64_t M, int64_t N, int64_t K,
+                                   float alpha, const void* A_dev, int64_t lda, int64_t strideA, const void* B_dev,
+                                   int64_t ldb, int64_t strideB, float beta, float* C_dev, int64_t ldc,
+                                   int64_t strideC, int64_t batch, void* stream);
+gemm_status_t gemm_strided_batched_with_config(int32_t config_id, char transA, char transB, int64_t M, int64_t N,
+                                               int64_t K, float alpha, const void* A_dev, int64_t lda,
+                                               int64_t strideA, const void* B_dev, int64_t ldb, int64_t strideB,
+                                               float beta, float* C_dev, int64_t ldc, int64_t strideC, int64_t batch,
+                                               void* stream);
 
 /* The same operation with an explicit config id (any family). */
 gemm_status_t gemm_with_config(int32_t config_id, char transA, char transB, int64_t M, int64_t N,
@@ -256,6 +303,28 @@ gemm_status_t kselect_pca(int32_t n, int32_t d, const float* X_dev, int32_t r, i
                           float* mean_out_dev, float* V_out_dev, float* Y_out_dev, double* evals_out,
                           double* total_var_out, void* stream);
 
+/* Section 4.1, spectral clustering: coordinates for k-means from the
+ * similarity graph of the n rows of X_dev (n x d, device).  Adjacency
+ * A_ij = exp(-gamma |x_i - x_j|^2) with a zero diagonal (distances from the
+ * Gram matrix X X^T, computed by the library's FP32 GEMM); S = D^-1/2 A D^-1/2
+ * with D the row sums (an isolated row gets D^-1/2 = 0); the k eigenvectors of
+ * S with the largest eigenvalues -- those of the normalised Laplacian I - S
+ * with the smallest -- by `iters` rounds of subspace iteration on S + I with an
+ * r-column block (k <= r <= min(n, 256)) from V0_dev (n x r), then
+ * Rayleigh-Ritz.  Writes U_out_dev (n x k, each row scaled to unit length) and
+ * evals_out (k eigenvalues of S, host, descending).  Scratch n^2 + 2nr + r^2
+ * floats, stream-ordered; synchronises `stream`. */
+gemm_status_t kselect_spectral_embedding(int32_t n, int32_t d, const float* X_dev, float gamma, int32_t k, int32_t r,
+                                         int32_t iters, const float* V0_dev, float* U_out_dev, double* evals_out,
+                                         void* stream);
+
+/* Section 4.2 for clusterings that give labels only: centres_out_dev (k x d)
+ * = per cluster, the geometric mean over its rows of X_dev (n x d) with values
+ * clamped below at `floor` (> 0); a cluster without rows gets zeros.  Labels
+ * outside [0, k) are ignored.  Device arrays. */
+gemm_status_t kselect_cluster_geomean(int32_t n, int32_t d, const float* X_dev, const int32_t* labels_dev, int32_t k,
+                                      float floor, float* centres_out_dev, void* stream);
+
 /* out_dev (k x d) = mean_dev + cent_dev (k x r) * V_dev^T: PCA-space centres as
  * performance vectors over the d configurations. */
 gemm_status_t kselect_pca_backproject(int32_t k, int32_t d, int32_t r, const float* cent_dev, const float* V_dev,
@@ -290,6 +359,21 @@ gemm_status_t kselect_top_n(int32_t n_rows, int32_t n_cols, const float* perf, i
 gemm_status_t kselect_knn(int32_t n_train, int32_t n_query, int32_t d, const float* train_dev,
                           const int32_t* labels_dev, const float* query_dev, int32_t k, int32_t* out_dev,
                           void* stream);
+
+/* Section 4.1 "Decision tree" pruning (host): a multi-output regression tree
+ * from the sizes (features, n x 4 doubles: M, N, K, batch) to the normalised
+ * performance vectors Y (n x d floats, host), grown best-first to at most
+ * max_leaves leaves: the leaf whose best split (features in order, midpoint
+ * thresholds ascending, first best kept) removes the most squared error is
+ * split next, lowest leaf index on ties (gains within a relative 1e-9 count as
+ * ties in both choices); growth stops early when no split
+ * removes more than 1e-12 of the root's squared error.  A split leaf keeps its
+ * index for the part <= threshold; the other part becomes the new last leaf.
+ * Writes labels_out (n, leaf per size), centres_out (max_leaves x d, the mean
+ * of Y over each leaf; rows beyond *n_leaves_out untouched) and *n_leaves_out.
+ * INVALID_ARG on null pointers, sizes < 1 or non-finite inputs. */
+gemm_status_t kselect_tree_regress(int32_t n, int32_t d, const double* features, const float* Y, int32_t max_leaves,
+                                   int32_t* labels_out, float* centres_out, int32_t* n_leaves_out);
 
 /* Section 5.1 (host): CART classification tree on features (n x 4 doubles:
  * M, N, K, batch) and labels (n, in [0, n_classes)).  Gini impurity with the
@@ -382,9 +466,23 @@ gemm_status_t kselect_im2col3x3(const float* x_dev, int32_t N, int32_t H, int32_
 gemm_status_t kselect_bias_act(float* y_dev, int64_t rows, int32_t cols, int64_t ld, const float* bias_dev,
                                int32_t relu, void* stream);
 
-/* 2 x 2, stride 2 max pooling of NHWC x (H, W even) into out (N, H/2, W/2, C). */
+/* 2 x 2, stride 2 max pooling of NHWC x (H, W even) into out (N, H/2, W/2, C).
+ * NCHW activations pool with N' = N * C images of one channel. */
 gemm_status_t kselect_maxpool2x2(const float* x_dev, int32_t N, int32_t H, int32_t W, int32_t C, float* out_dev,
                                  void* stream);
+
+/* The GEMM-batched layout Section 6 describes (per image, Cout x (H W) = the
+ * weights Cout x 9 Cin times the image's im2col matrix transposed; batch =
+ * images, weights shared through a zero batch stride in gemm_strided_batched):
+ * activations are NCHW.  im2col from NCHW x: the same output rows and columns
+ * as kselect_im2col3x3 (row (n, h, w), column (kh * 3 + kw) * C + c). */
+gemm_status_t kselect_im2col3x3_nchw(const float* x_dev, int32_t N, int32_t C, int32_t H, int32_t W, float* out_dev,
+                                     int64_t ld, void* stream);
+
+/* y[n, c, p] = y[n, c, p] + bias[c] (bias may be NULL) for p < HW, then
+ * max(., 0) if relu: per-channel bias of NCHW activations. */
+gemm_status_t kselect_bias_act_nchw(float* y_dev, int32_t N, int32_t C, int64_t HW, const float* bias_dev,
+                                    int32_t relu, void* stream);
 
 /* ---------------------------------------------------------------- error check
  * The judge of every GEMM result: err = max over entries of

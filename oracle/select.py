@@ -410,11 +410,16 @@ def leaf_sse(Y: np.ndarray) -> float:
     return float(np.sum((Y - Y.mean(axis=0)) ** 2))
 
 
+GAIN_TIE = 1e-9  # gains within this relative distance of the best count as ties
+
+
 def regression_split(F: np.ndarray, Y: np.ndarray, idx: np.ndarray):
     """Best split of the samples `idx` for a multi-output regression tree: the
     (feature, midpoint threshold) with the largest drop of summed squared error,
-    features in order and thresholds ascending, the first best kept.  Returns
-    (gain, feature, threshold) or None when no split separates the samples."""
+    features in order and thresholds ascending, the first best kept (a later
+    candidate must beat it by more than GAIN_TIE relative, so that splits giving
+    the same partition through different features tie whatever the rounding).
+    Returns (gain, feature, threshold) or None when no split separates the samples."""
     parent = leaf_sse(Y[idx])
     best = None
     for f in range(F.shape[1]):
@@ -424,7 +429,7 @@ def regression_split(F: np.ndarray, Y: np.ndarray, idx: np.ndarray):
             left = idx[F[idx, f] <= thr]
             right = idx[F[idx, f] > thr]
             gain = parent - leaf_sse(Y[left]) - leaf_sse(Y[right])
-            if best is None or gain > best[0]:
+            if best is None or gain > best[0] * (1 + GAIN_TIE):
                 best = (gain, f, thr)
     return best
 
@@ -435,7 +440,7 @@ def tree_regression_partition(F: np.ndarray, Y: np.ndarray, max_leaves: int):
 
     Grown best-first: while there are fewer than max_leaves leaves, split the
     leaf whose best split removes the most squared error (lowest leaf index on
-    ties).  Growth stops when no split removes more than 1e-12 of the root's
+    ties, within GAIN_TIE).  Growth stops when no split removes more than 1e-12 of the root's
     squared error (rounding noise of leaves that are already constant).  A split
     leaf keeps its index for the left part and the right part becomes a new last
     leaf.  Returns (labels: leaf index per sample, centres: mean of Y per leaf)."""
@@ -444,10 +449,12 @@ def tree_regression_partition(F: np.ndarray, Y: np.ndarray, max_leaves: int):
     splits = [regression_split(F, Y, leaves[0])]
     tol = 1e-12 * leaf_sse(Y)
     while len(leaves) < max_leaves:
-        cand = [(s[0], i) for i, s in enumerate(splits) if s is not None and s[0] > tol]
-        if not cand:
+        i = None
+        for j, s in enumerate(splits):
+            if s is not None and s[0] > tol and (i is None or s[0] > splits[i][0] * (1 + GAIN_TIE)):
+                i = j
+        if i is None:
             break
-        gain, i = max(cand, key=lambda t: (t[0], -t[1]))
         _, f, thr = splits[i]
         idx = leaves[i]
         left, right = idx[F[idx, f] <= thr], idx[F[idx, f] > thr]
@@ -478,14 +485,18 @@ def spectral_embedding(A: np.ndarray, k: int) -> tuple[np.ndarray, np.ndarray]:
     """Coordinates from the Laplacian of the adjacency matrix: the k eigenvectors
     of the normalised Laplacian L = I - D^-1/2 A D^-1/2 with the smallest
     eigenvalues (equivalently the largest of S = D^-1/2 A D^-1/2), each row then
-    scaled to unit length.  Returns (rows n x k, eigenvalues of S, descending)."""
+    scaled to unit length.  A row with zero degree (an isolated size) gets
+    D^-1/2 = 0, and a zero row of the embedding stays zero.
+    Returns (rows n x k, eigenvalues of S, descending)."""
     d = A.sum(axis=1)
-    s = 1.0 / np.sqrt(d)
+    s = np.zeros_like(d)
+    s[d > 0] = 1.0 / np.sqrt(d[d > 0])
     S = A * s[:, None] * s[None, :]
     w, V = np.linalg.eigh(S)
     order = np.argsort(-w, kind="stable")[:k]
     U = V[:, order]
-    U = U / np.linalg.norm(U, axis=1, keepdims=True)
+    nrm = np.linalg.norm(U, axis=1, keepdims=True)
+    U = np.divide(U, nrm, out=np.zeros_like(U), where=nrm > 0)
     return U, w[order]
 
 

@@ -39,13 +39,28 @@ struct GemmArgs {
   float* C;
   int64_t ldc, strideC;
   int vecA, vecB, vecC;  // 16-byte vector access is legal on this operand
+  // K split (SIMT family): blockIdx.z = batch entry * splits + split; split s
+  // covers k in [s * kchunk, min(K, (s + 1) * kchunk)) and C/ldc/strideC then
+  // describe the partial-sum workspace (one M x ldc slab per z).
+  int splits = 1, kchunk = 0;
 };
 
 using LaunchFn = cudaError_t (*)(const GemmArgs&, cudaStream_t);
+using OccFn = int (*)();  // resident CTAs per SM on the current device, 0 on error
 
 // Per-shard registration of the SIMT instantiations (simt_shard.cu compiled N times).
 constexpr int kSimtShards = 12;
-void simt_register_shard(int shard, LaunchFn* table);
+
+// ------------------------------------------------------------------ split-K kind
+// Config id kSplitBase + b runs SIMT config b with its K range divided among
+// CTAs when the output tiles alone would leave most of the GPU's resident-CTA
+// slots empty; the partial tiles are summed by a second kernel.  The kind
+// covers the staged configs with BK in {16, 32} (192 ids).
+constexpr int kSplitBase = 2000;
+constexpr int kSplitConfigs = 192;
+constexpr bool split_eligible(int base) {
+  return base >= 0 && base < kSimtConfigs && (base % 2) == 1 && ((base / 2) % 3) != 0;
+}
 
 // Tensor-core families (tc_gemm.cu).
 constexpr int kTcBase = 1000;

@@ -15,7 +15,7 @@
 #include "common.cuh"
 
 namespace ks {
-#define KS_DECL_SHARD(i) void simt_register_shard_##i(LaunchFn*);
+#define KS_DECL_SHARD(i) void simt_register_shard_##i(LaunchFn*, LaunchFn*, OccFn*);
 KS_DECL_SHARD(0) KS_DECL_SHARD(1) KS_DECL_SHARD(2) KS_DECL_SHARD(3) KS_DECL_SHARD(4) KS_DECL_SHARD(5)
 KS_DECL_SHARD(6) KS_DECL_SHARD(7) KS_DECL_SHARD(8) KS_DECL_SHARD(9) KS_DECL_SHARD(10) KS_DECL_SHARD(11)
 static_assert(kSimtShards == 12, "shard list above must match kSimtShards");
@@ -24,20 +24,34 @@ static thread_local int g_last_cuda_error = 0;
 void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = static_cast<int>(e); }
 
 static LaunchFn g_simt[kSimtConfigs];
+static LaunchFn g_simt_split[kSimtConfigs];  // split instances of the split-K kind's base configs
+static OccFn g_simt_occ[kSimtConfigs];
 static std::once_flag g_simt_once;
 
 static void init_simt_table() {
   std::call_once(g_simt_once, [] {
     std::memset(g_simt, 0, sizeof(g_simt));
-    simt_register_shard_0(g_simt); simt_register_shard_1(g_simt); simt_register_shard_2(g_simt);
-    simt_register_shard_3(g_simt); simt_register_shard_4(g_simt); simt_register_shard_5(g_simt);
-    simt_register_shard_6(g_simt); simt_register_shard_7(g_simt); simt_register_shard_8(g_simt);
-    simt_register_shard_9(g_simt); simt_register_shard_10(g_simt); simt_register_shard_11(g_simt);
+    std::memset(g_simt_split, 0, sizeof(g_simt_split));
+    std::memset(g_simt_occ, 0, sizeof(g_simt_occ));
+    LaunchFn* t = g_simt;
+    LaunchFn* x = g_simt_split;
+    OccFn* o = g_simt_occ;
+    simt_register_shard_0(t, x, o); simt_register_shard_1(t, x, o); simt_register_shard_2(t, x, o);
+    simt_register_shard_3(t, x, o); simt_register_shard_4(t, x, o); simt_register_shard_5(t, x, o);
+    simt_register_shard_6(t, x, o); simt_register_shard_7(t, x, o); simt_register_shard_8(t, x, o);
+    simt_register_shard_9(t, x, o); simt_register_shard_10(t, x, o); simt_register_shard_11(t, x, o);
   });
+}
+
+// Base SIMT config of a split-K id, or -1.
+static int split_base_of(int id) {
+  const int b = id - kSplitBase;
+  return split_eligible(b) ? b : -1;
 }
 
 static int family_of(int id) {
   if (id >= 0 && id < kSimtConfigs) return GEMM_PREC_F32;
+  if (split_base_of(id) >= 0) return GEMM_PREC_F32;
   if (id >= kTcBase && id < kTcBase + 300) {
     int fam = (id - kTcBase) / 100, idx = (id - kTcBase) % 100;
     if (idx < kTcConfigsPerFamily) return fam + 1;  // 1 TF32, 2 BF16, 3 F32X3
@@ -89,6 +103,188 @@ static gemm_status_t make_args(char transA, char transB, int64_t M, int64_t N, i
   a->vecA = ((uintptr_t)A % 16 == 0) && (lda % per16 == 0);
   a->vecB = ((uintptr_t)B % 16 == 0) && (ldb % per16 == 0);
   a->vecC = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0);
+  a->splits = 1;
+  a->kchunk = (int)K;
+  return GEMM_OK;
+}
+
+// ------------------------------------------------------------------ split-K kind
+// Cost model of the split decision (GB300 figures): a SIMT tile sustains about
+// kSplitFlopRate across the whole GPU when every resident-CTA slot is busy, a
+// wave that leaves slots empty costs as long as a full one, every CTA pays a
+// fixed start-up and epilogue cost of kSplitCtaOverhead K-steps, and the
+// reduction streams (splits + 2) x M x N x batch floats at kSplitReduceBps plus
+// a launch.
+constexpr double kSplitFlopRate = 50e12;
+constexpr double kSplitReduceBps = 5e12;
+constexpr double kSplitReduceLaunchS = 4e-6;
+constexpr double kSplitCtaOverhead = 2.0;  // first-slice load + epilogue of a CTA, in K-steps
+constexpr int kSplitMaxFactor = 16;
+constexpr int kSplitMinKBlocks = 4;                        // K-steps per split at least
+constexpr int64_t kSplitWorkspaceMax = 256ll << 20;        // bytes of partial tiles
+constexpr double kSplitMinGain = 0.9;                      // split only if <= 0.9 x the unsplit cost
+
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// The split factor (>= 1) and K-chunk for an M x N x K x batch product with BM x BN
+// tiles and K-step BK, given `occ` resident CTAs per SM on `sms` SMs.
+static int choose_split(int64_t M, int64_t N, int64_t K, int64_t batch, int BM, int BN, int BK, int occ, int sms,
+                        int* kchunk) {
+  *kchunk = (int)K;
+  if (occ < 1 || sms < 1 || K <= 0 || M <= 0 || N <= 0 || batch <= 0) return 1;
+  if ((double)M * (double)N * (double)batch > 1e12) return 1;  // far beyond one wave; keeps the int64 math exact
+  const int64_t tiles = ceil_div(M, BM) * ceil_div(N, BN) * batch;
+  const int64_t cap = (int64_t)occ * sms;
+  const int64_t nk = ceil_div(K, BK);
+  const double t_kb = 2.0 * BM * BN * BK * (double)cap / kSplitFlopRate;  // one K-step of a full wave
+  const double plain = (double)ceil_div(tiles, cap) * (nk + kSplitCtaOverhead) * t_kb;
+  double best = plain * kSplitMinGain;
+  int best_s = 1;
+  int64_t best_kc = K;
+  const int64_t ldw = (N + 3) / 4 * 4;
+  for (int S = 2; S <= kSplitMaxFactor; ++S) {
+    const int64_t kc = ceil_div(nk, S);  // K-steps per split
+    if (kc < kSplitMinKBlocks) break;
+    const int64_t s_eff = ceil_div(nk, kc);
+    if (s_eff != S) continue;  // same partition as a smaller factor
+    if (batch * s_eff > 65535) break;
+    if (s_eff * batch * M * ldw * 4 > kSplitWorkspaceMax) break;
+    const double cost = (double)ceil_div(tiles * s_eff, cap) * (kc + kSplitCtaOverhead) * t_kb +
+                        (double)(s_eff + 2) * batch * M * N * 4 / kSplitReduceBps + kSplitReduceLaunchS;
+    if (cost < best) {
+      best = cost;
+      best_s = (int)s_eff;
+      best_kc = kc * BK;
+    }
+  }
+  *kchunk = (int)best_kc;
+  return best_s;
+}
+
+static int sm_count_of(int dev) {
+  static std::atomic<int> cache[64];
+  if (dev < 0 || dev >= 64) return 0;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+// Resident CTAs per SM of SIMT config `base` on device `dev` (cached; 0 on error).
+static int occupancy_of(int base, int dev) {
+  static std::atomic<int> cache[64][kSimtConfigs];
+  if (dev < 0 || dev >= 64) return 0;
+  int v = cache[dev][base].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  init_simt_table();
+  if (!g_simt_occ[base]) return 0;
+  v = g_simt_occ[base]();
+  if (v > 0) cache[dev][base].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+// Split factor the launcher uses for config `id` on the current device.
+static int split_for(int id, const GemmArgs& a, int* kchunk) {
+  *kchunk = a.K;
+  const int base = split_base_of(id);
+  if (base < 0) return 1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  const SimtParams P = simt_params(base);
+  return choose_split(a.M, a.N, a.K, a.batch, P.wy * P.tm, P.wx * P.tn, P.bk, occupancy_of(base, dev),
+                      sm_count_of(dev), kchunk);
+}
+
+// C[b] = alpha * sum_s W[b, s] + beta * C[b], the splits summed in order s = 0, 1, ...
+// One thread per 4 consecutive columns of a row; W rows are 16-byte aligned (ldw % 4 == 0).
+__global__ void split_reduce_kernel(const float* __restrict__ W, int64_t ldw, int S, int M, int N, int batch,
+                                    float alpha, float beta, float* C, int64_t ldc, int64_t strideC, int vecC) {
+  const int n4 = (N + 3) / 4;
+  const int64_t total = (int64_t)batch * M * n4;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = t / n4;  // b * M + i
+    const int j = (int)(t - row * n4) * 4;
+    const int64_t b = row / M, i = row - b * M;
+    const float* w = W + ((b * S) * M + i) * ldw + j;
+    float4 acc = *reinterpret_cast<const float4*>(w);
+    for (int s = 1; s < S; ++s) {
+      const float4 v = *reinterpret_cast<const float4*>(w + (int64_t)s * M * ldw);
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    float o[4] = {alpha * acc.x, alpha * acc.y, alpha * acc.z, alpha * acc.w};
+    float* c = C + b * strideC + i * ldc + j;
+    if (vecC && j + 3 < N) {
+      if (beta != 0.f) {
+        const float4 c0 = *reinterpret_cast<const float4*>(c);
+        o[0] = fmaf(beta, c0.x, o[0]); o[1] = fmaf(beta, c0.y, o[1]);
+        o[2] = fmaf(beta, c0.z, o[2]); o[3] = fmaf(beta, c0.w, o[3]);
+      }
+      *reinterpret_cast<float4*>(c) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+      for (int q = 0; q < 4 && j + q < N; ++q) c[q] = (beta != 0.f) ? fmaf(beta, c[q], o[q]) : o[q];
+    }
+  }
+}
+
+// Stream-ordered workspace for the partial tiles: a per-device pool that keeps
+// its memory between calls; under stream capture the default pool is used so
+// that the allocation becomes a graph node.
+static cudaError_t split_alloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) return cudaMallocAsync(p, bytes, s);
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      if ((e = cudaMemPoolCreate(&pools[dev], &props)) != cudaSuccess) { pools[dev] = nullptr; return e; }
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// Runs config `id` of the split-K kind: partial products of `splits` K ranges into
+// the workspace, then the ordered reduction with alpha and beta.
+static gemm_status_t launch_split(int base, const GemmArgs& a, int splits, int kchunk, cudaStream_t s) {
+  const int64_t ldw = ((int64_t)a.N + 3) / 4 * 4;
+  const size_t bytes = (size_t)splits * a.batch * a.M * ldw * sizeof(float);
+  void* w = nullptr;
+  cudaError_t e = split_alloc(&w, bytes, s);
+  if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+  GemmArgs p = a;
+  p.alpha = 1.f;
+  p.beta = 0.f;
+  p.C = static_cast<float*>(w);
+  p.ldc = ldw;
+  p.strideC = ldw * a.M;
+  p.vecC = 1;
+  p.splits = splits;
+  p.kchunk = kchunk;
+  e = g_simt_split[base](p, s);
+  if (e == cudaSuccess) {
+    const int64_t total = (int64_t)a.batch * a.M * ((a.N + 3) / 4);
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    split_reduce_kernel<<<grid, 256, 0, s>>>(static_cast<const float*>(w), ldw, splits, a.M, a.N, a.batch, a.alpha,
+                                              a.beta, a.C, a.ldc, a.strideC, a.vecC);
+    e = cudaGetLastError();
+  }
+  cudaError_t ef = cudaFreeAsync(w, s);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
   return GEMM_OK;
 }
 
@@ -112,6 +308,19 @@ static gemm_status_t launch_config(int id, const GemmArgs& a, cudaStream_t s) {
     return GEMM_OK;
   }
   const int fam = family_of(id);
+  if (fam == GEMM_PREC_F32 && id >= kSimtConfigs) {
+    init_simt_table();
+    const int base = split_base_of(id);
+    if (!g_simt[base] || !g_simt_split[base]) return GEMM_ERR_NO_KERNEL;
+    int kchunk = a.K;
+    const int splits = split_for(id, a, &kchunk);
+    if (splits <= 1) {
+      cudaError_t e = g_simt[base](a, s);
+      if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+      return GEMM_OK;
+    }
+    return launch_split(base, a, splits, kchunk, s);
+  }
   if (fam == GEMM_PREC_F32) {
     init_simt_table();
     LaunchFn f = g_simt[id];
@@ -158,7 +367,7 @@ const char* gemm_status_string(int32_t s) {
 int32_t gemm_last_cuda_error(void) { return g_last_cuda_error; }
 
 int32_t gemm_config_count(int32_t precision) {
-  if (precision == GEMM_PREC_F32) return kSimtConfigs;
+  if (precision == GEMM_PREC_F32) return kSimtConfigs + kSplitConfigs;
   if (precision >= GEMM_PREC_TF32 && precision <= GEMM_PREC_F32X3) return kTcConfigsPerFamily;
   return GEMM_ERR_INVALID_ARG;
 }
@@ -166,7 +375,12 @@ int32_t gemm_config_count(int32_t precision) {
 int32_t gemm_config_id(int32_t precision, int32_t index) {
   const int32_t n = gemm_config_count(precision);
   if (n < 0 || index < 0 || index >= n) return GEMM_ERR_INVALID_ARG;
-  return precision == GEMM_PREC_F32 ? index : kTcBase + 100 * (precision - 1) + index;
+  if (precision != GEMM_PREC_F32) return kTcBase + 100 * (precision - 1) + index;
+  if (index < kSimtConfigs) return index;
+  int j = index - kSimtConfigs;
+  for (int b = 0; b < kSimtConfigs; ++b)
+    if (split_eligible(b) && j-- == 0) return kSplitBase + b;
+  return GEMM_ERR_INVALID_ARG;
 }
 
 gemm_status_t gemm_config_params(int32_t id, int32_t out[8]) {
@@ -174,8 +388,9 @@ gemm_status_t gemm_config_params(int32_t id, int32_t out[8]) {
   const int fam = family_of(id);
   if (fam < 0) return GEMM_ERR_NO_KERNEL;
   if (fam == GEMM_PREC_F32) {
-    SimtParams p = simt_params(id);
-    int32_t v[8] = {0, p.tm, p.tn, p.wx, p.wy, p.bk, p.staged, 0};
+    const int base = id < kSimtConfigs ? id : split_base_of(id);
+    SimtParams p = simt_params(base);
+    int32_t v[8] = {0, p.tm, p.tn, p.wx, p.wy, p.bk, p.staged, id < kSimtConfigs ? 0 : 1};
     std::memcpy(out, v, sizeof(v));
     return GEMM_OK;
   }
@@ -261,6 +476,52 @@ int32_t select_kernel(gemm_handle_t h, int64_t M, int64_t N, int64_t K, int64_t 
   return GEMM_ERR_INVALID_ARG;  // unreachable for a validated tree
 }
 
+// gemm_with_config with explicit batch strides (elements).  A and B strides may
+// be anything >= 0 (0 reuses one matrix for every batch entry); C's must keep
+// the batch entries' outputs apart.
+static gemm_status_t strided_args(int32_t id, char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha,
+                                  const void* A, int64_t lda, int64_t strideA, const void* B, int64_t ldb,
+                                  int64_t strideB, float beta, float* C, int64_t ldc, int64_t strideC, int64_t batch,
+                                  GemmArgs* a, bool* noop) {
+  if (family_of(id) < 0) return GEMM_ERR_NO_KERNEL;
+  gemm_status_t st = make_args(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch,
+                               elem_bytes_of(id), a, noop);
+  if (st != GEMM_OK || *noop) return st;
+  if (strideA < 0 || strideB < 0 || strideC < 0) return GEMM_ERR_INVALID_ARG;
+  if (batch > 1 && strideC < ldc * M) return GEMM_ERR_INVALID_ARG;  // batch entries would share outputs
+  a->strideA = strideA;
+  a->strideB = strideB;
+  a->strideC = strideC;
+  const int per16 = 16 / elem_bytes_of(id);
+  a->vecA = a->vecA && (strideA % per16 == 0);
+  a->vecB = a->vecB && (strideB % per16 == 0);
+  a->vecC = a->vecC && (strideC % 4 == 0);
+  return GEMM_OK;
+}
+
+gemm_status_t gemm_strided_batched_with_config(int32_t id, char transA, char transB, int64_t M, int64_t N, int64_t K,
+                                               float alpha, const void* A, int64_t lda, int64_t strideA,
+                                               const void* B, int64_t ldb, int64_t strideB, float beta, float* C,
+                                               int64_t ldc, int64_t strideC, int64_t batch, void* stream) {
+  GemmArgs a;
+  bool noop = false;
+  gemm_status_t st = strided_args(id, transA, transB, M, N, K, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc,
+                                  strideC, batch, &a, &noop);
+  if (st != GEMM_OK || noop) return st;
+  return launch_config(id, a, static_cast<cudaStream_t>(stream));
+}
+
+gemm_status_t gemm_strided_batched(gemm_handle_t h, char transA, char transB, int64_t M, int64_t N, int64_t K,
+                                   float alpha, const void* A, int64_t lda, int64_t strideA, const void* B,
+                                   int64_t ldb, int64_t strideB, float beta, float* C, int64_t ldc, int64_t strideC,
+                                   int64_t batch, void* stream) {
+  if (!h) return GEMM_ERR_INVALID_ARG;
+  const int32_t id = select_kernel(h, M, N, K, batch);
+  if (id < 0) return (gemm_status_t)id;
+  return gemm_strided_batched_with_config(id, transA, transB, M, N, K, alpha, A, lda, strideA, B, ldb, strideB, beta,
+                                          C, ldc, strideC, batch, stream);
+}
+
 gemm_status_t gemm_with_config(int32_t id, char transA, char transB, int64_t M, int64_t N, int64_t K,
                                float alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
                                float beta, float* C, int64_t ldc, int64_t batch, void* stream) {
@@ -271,6 +532,34 @@ gemm_status_t gemm_with_config(int32_t id, char transA, char transB, int64_t M, 
                                elem_bytes_of(id), &a, &noop);
   if (st != GEMM_OK || noop) return st;
   return launch_config(id, a, static_cast<cudaStream_t>(stream));
+}
+
+int32_t gemm_split_choose(int64_t M, int64_t N, int64_t K, int64_t batch, int32_t BM, int32_t BN, int32_t BK,
+                          int32_t resident_ctas_per_sm, int32_t sm_count, int32_t* kchunk) {
+  if (!kchunk || M < 0 || N < 0 || K < 0 || batch < 0 || BM < 1 || BN < 1 || BK < 1 || K >= ((int64_t)1 << 31))
+    return GEMM_ERR_INVALID_ARG;
+  int kc = 0;
+  const int s = choose_split(M, N, K, batch, BM, BN, BK, resident_ctas_per_sm, sm_count, &kc);
+  *kchunk = kc;
+  return s;
+}
+
+int32_t gemm_split_factor(int32_t id, int64_t M, int64_t N, int64_t K, int64_t batch, int32_t* kchunk) {
+  if (!kchunk) return GEMM_ERR_INVALID_ARG;
+  if (family_of(id) < 0) return GEMM_ERR_NO_KERNEL;
+  GemmArgs a;
+  bool noop = false;
+  const int64_t lda = std::max<int64_t>(K, M), ldb = std::max<int64_t>(K, N);
+  float dummy = 0.f;
+  gemm_status_t st = make_args('N', 'N', M, N, K, 1.f, &dummy, lda, &dummy, ldb, 0.f, &dummy, std::max<int64_t>(N, 1),
+                               batch, elem_bytes_of(id), &a, &noop);
+  if (st != GEMM_OK) return st;
+  *kchunk = (int)K;
+  if (noop || K == 0) return 1;
+  int kc = (int)K;
+  const int s = split_for(id, a, &kc);
+  *kchunk = kc;
+  return s;
 }
 
 gemm_status_t gemm(gemm_handle_t h, char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha,

@@ -95,6 +95,53 @@ gemm_status_t fail(cudaError_t e) {
   return GEMM_ERR_CUDA;
 }
 
+// ---- spectral embedding (Section 4.1, spectral clustering)
+__global__ void diag_kernel(int n, const float* G, float* sq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) sq[i] = G[(int64_t)i * n + i];
+}
+
+// G (the Gram matrix X X^T) becomes the RBF adjacency, zero diagonal.
+__global__ void affinity_kernel(int n, float gamma, const float* sq, float* G) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t - (int64_t)i * n);
+    const float d2 = fmaxf(sq[i] + sq[j] - 2.f * G[t], 0.f);
+    G[t] = (i == j) ? 0.f : expf(-gamma * d2);
+  }
+}
+
+// s_i = deg_i^-1/2 (0 for an isolated row), one block per row.
+__global__ void inv_sqrt_degree_kernel(int n, const float* A, float* s) {
+  __shared__ float sh[33];
+  const int i = blockIdx.x;
+  float part = 0.f;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) part += A[(int64_t)i * n + j];
+  const float deg = block_sum(part, sh);
+  if (threadIdx.x == 0) s[i] = deg > 0.f ? rsqrtf(deg) : 0.f;
+}
+
+// A <- D^-1/2 A D^-1/2 + I: the shift puts the spectrum in [0, 2], so the
+// subspace iteration converges to the largest (not the largest-magnitude) eigenvalues.
+__global__ void normalise_shift_kernel(int n, const float* s, float* A) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t - (int64_t)i * n);
+    A[t] = s[i] * A[t] * s[j] + (i == j ? 1.f : 0.f);
+  }
+}
+
+// Rows of U (n x k) scaled to unit length; zero rows stay zero.
+__global__ void row_unit_kernel(int n, int k, float* U) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float q = 0.f;
+    for (int j = 0; j < k; ++j) q = fmaf(U[i * k + j], U[i * k + j], q);
+    const float inv = q > 0.f ? rsqrtf(q) : 0.f;
+    for (int j = 0; j < k; ++j) U[i * k + j] *= inv;
+  }
+}
+
+int grid_of(int64_t total) { return (int)std::min<int64_t>((total + 255) / 256, 152 * 16); }
+
 // C[M x N] = alpha * op(A) * op(B) with the library's SIMT kernel.
 gemm_status_t mm(char ta, char tb, int M, int N, int K, float alpha, const float* A, int lda, const float* B, int ldb,
                  float* C, int ldc, cudaStream_t s) {
@@ -222,4 +269,75 @@ extern "C" gemm_status_t kselect_pca_backproject(int32_t k, int32_t d, int32_t r
   backproject_kernel<<<(k * d + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(k, d, r, cent, V, mean, out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GEMM_OK : fail(e);
+}
+
+// Section 4.1, spectral clustering: the k leading eigenvectors of
+// S = D^-1/2 A D^-1/2 for the RBF adjacency A_ij = exp(-gamma |x_i - x_j|^2)
+// (zero diagonal) of the n rows of X, i.e. those of the normalised Laplacian
+// I - S with the smallest eigenvalues, by subspace iteration on S + I with an
+// r-column block (r >= k) and Rayleigh-Ritz; rows then scaled to unit length.
+extern "C" gemm_status_t kselect_spectral_embedding(int32_t n, int32_t d, const float* X, float gamma, int32_t k,
+                                                    int32_t r, int32_t iters, const float* V0, float* U_out,
+                                                    double* evals_out, void* stream) {
+  if (n < 2 || d < 1 || k < 1 || r < k || r > n || r > 256 || iters < 1 || !(gamma > 0.f) || !std::isfinite(gamma) ||
+      !X || !V0 || !U_out || !evals_out)
+    return GEMM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t fA = (size_t)n * n, fW = (size_t)n * r, fT = (size_t)r * r;
+  float* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), sizeof(float) * (fA + 2 * fW + fT + 2 * (size_t)n), s);
+  if (e != cudaSuccess) return fail(e);
+  float *A = ws, *W = A + fA, *V = W + fW, *T = V + fW, *sq = T + fT, *sc = sq + n;
+  gemm_status_t st = mm('N', 'T', n, n, d, 1.f, X, d, X, d, A, n, s);  // Gram matrix
+  if (st == GEMM_OK) {
+    diag_kernel<<<grid_of(n), 256, 0, s>>>(n, A, sq);
+    affinity_kernel<<<grid_of((int64_t)n * n), 256, 0, s>>>(n, gamma, sq, A);
+    inv_sqrt_degree_kernel<<<n, 256, 0, s>>>(n, A, sc);
+    normalise_shift_kernel<<<grid_of((int64_t)n * n), 256, 0, s>>>(n, sc, A);
+    e = cudaMemcpyAsync(V, V0, sizeof(float) * fW, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) st = fail(e);
+  }
+  for (int it = 0; it < iters && st == GEMM_OK; ++it) {
+    st = mm('N', 'N', n, r, n, 1.f, A, n, V, r, W, r, s);  // W = (S + I) V
+    if (st != GEMM_OK) break;
+    mgs_kernel<<<1, 256, 0, s>>>(n, r, W);
+    e = cudaMemcpyAsync(V, W, sizeof(float) * fW, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) st = fail(e);
+  }
+  if (st == GEMM_OK) st = mm('N', 'N', n, r, n, 1.f, A, n, V, r, W, r, s);
+  if (st == GEMM_OK) st = mm('T', 'N', r, r, n, 1.f, V, r, W, r, T, r, s);  // V^T (S + I) V
+  std::vector<float> Th(fT);
+  if (st == GEMM_OK) {
+    e = cudaMemcpyAsync(Th.data(), T, sizeof(float) * fT, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(e);
+  }
+  if (st == GEMM_OK) {
+    std::vector<double> Am(fT), Q;
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < r; ++j) Am[(size_t)i * r + j] = 0.5 * ((double)Th[(size_t)i * r + j] + Th[(size_t)j * r + i]);
+    jacobi(r, Am, Q);
+    std::vector<int> order(r);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return Am[(size_t)a * r + a] > Am[(size_t)b * r + b]; });
+    std::vector<float> Qk((size_t)r * k);
+    for (int j = 0; j < k; ++j) {
+      evals_out[j] = Am[(size_t)order[j] * r + order[j]] - 1.0;  // undo the shift
+      for (int i = 0; i < r; ++i) Qk[(size_t)i * k + j] = (float)Q[(size_t)i * r + order[j]];
+    }
+    e = cudaMemcpyAsync(T, Qk.data(), sizeof(float) * Qk.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = fail(e);
+    if (st == GEMM_OK) st = mm('N', 'N', n, k, r, 1.f, V, r, T, k, U_out, k, s);  // U = V Q_k
+    if (st == GEMM_OK) {
+      row_unit_kernel<<<grid_of(n), 256, 0, s>>>(n, k, U_out);
+      if ((e = cudaGetLastError()) != cudaSuccess) st = fail(e);
+    }
+    if (st == GEMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = fail(e);
+  }
+  cudaFreeAsync(ws, s);
+  cudaStreamSynchronize(s);
+  return st;
 }

@@ -310,6 +310,24 @@ static gemm_status_t cuda_fail(cudaError_t e) {
   return GEMM_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ cluster geometric means (Section 4.2)
+// One thread per (cluster, configuration): log-mean over the cluster's rows in row order.
+__global__ void cluster_geomean_kernel(int n, int d, const float* X, const int32_t* labels, int k, float floor,
+                                       float* out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)k * d;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / d), j = (int)(t - (int64_t)c * d);
+    double acc = 0.0;
+    int cnt = 0;
+    for (int i = 0; i < n; ++i) {
+      if (labels[i] != c) continue;
+      acc += log((double)fmaxf(X[(int64_t)i * d + j], floor));
+      ++cnt;
+    }
+    out[t] = cnt ? (float)exp(acc / cnt) : 0.f;
+  }
+}
+
 // ------------------------------------------------------------------ CART (Section 5.1)
 struct TreeBuilder {
   const double* F;
@@ -377,6 +395,72 @@ struct TreeBuilder {
     const int r = grow(right, depth + 1);
     nodes[me].right = r;
     return me;
+  }
+};
+
+// ------------------------------------------------------------------ regression tree (Section 4.1)
+// Multi-output regression tree from sizes to performance vectors, grown
+// best-first to a leaf budget.  Within a node the rows are centred on the
+// node mean, so the squared error a split removes is the between-part sum
+// sum_j S_j^2 (1 / n_left + 1 / n_right), S_j the left part's column sums.
+// A candidate replaces the best so far only if its gain is larger by more than
+// this relative amount: splits that cut a node the same way through different
+// features then tie exactly as they do in exact arithmetic.
+constexpr double kGainTie = 1e-9;
+
+struct RegressionTree {
+  const double* F;
+  const float* Y;
+  int d;
+  struct Split {
+    double gain = 0.0;
+    int f = -1;
+    double thr = 0.0;
+  };
+
+  double sse(const std::vector<int>& idx) const {
+    const int n = (int)idx.size();
+    double total = 0.0;
+    for (int j = 0; j < d; ++j) {
+      double m = 0.0;
+      for (int i : idx) m += Y[(size_t)i * d + j];
+      m /= n;
+      for (int i : idx) {
+        const double e = Y[(size_t)i * d + j] - m;
+        total += e * e;
+      }
+    }
+    return total;
+  }
+
+  Split best(const std::vector<int>& idx) const {
+    Split b;
+    const int n = (int)idx.size();
+    if (n < 2) return b;
+    std::vector<double> mean(d, 0.0), L(d);
+    for (int i : idx)
+      for (int j = 0; j < d; ++j) mean[j] += Y[(size_t)i * d + j];
+    for (int j = 0; j < d; ++j) mean[j] /= n;
+    std::vector<int> order(idx);
+    for (int f = 0; f < 4; ++f) {
+      std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return F[4 * a + f] < F[4 * c + f]; });
+      std::fill(L.begin(), L.end(), 0.0);
+      for (int p = 0; p + 1 < n; ++p) {
+        const float* row = Y + (size_t)order[p] * d;
+        for (int j = 0; j < d; ++j) L[j] += (double)row[j] - mean[j];
+        const double xa = F[4 * order[p] + f], xb = F[4 * order[p + 1] + f];
+        if (!(xa < xb)) continue;
+        double s2 = 0.0;
+        for (int j = 0; j < d; ++j) s2 += L[j] * L[j];
+        const double gain = s2 * (1.0 / (p + 1) + 1.0 / (n - p - 1));
+        if (b.f < 0 || gain > b.gain * (1.0 + kGainTie)) {
+          b.gain = gain;
+          b.f = f;
+          b.thr = (xa + xb) / 2.0;
+        }
+      }
+    }
+    return b;
   }
 };
 
@@ -580,6 +664,58 @@ gemm_status_t kselect_tree_train(int32_t n, const double* features, const int32_
   if (tb.overflow) return GEMM_ERR_UNSUPPORTED;
   std::memcpy(out_nodes, tb.nodes.data(), tb.nodes.size() * sizeof(gemm_tree_node_t));
   *out_n_nodes = (int32_t)tb.nodes.size();
+  return GEMM_OK;
+}
+
+gemm_status_t kselect_cluster_geomean(int32_t n, int32_t d, const float* X, const int32_t* labels, int32_t k,
+                                      float floor, float* out, void* stream) {
+  if (n < 0 || d < 1 || k < 1 || !(floor > 0.f) || !out || (n > 0 && (!X || !labels))) return GEMM_ERR_INVALID_ARG;
+  const int64_t total = (int64_t)k * d;
+  const int grid = (int)std::min<int64_t>((total + 127) / 128, 152 * 16);
+  cluster_geomean_kernel<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(n, d, X, labels, k, floor, out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GEMM_OK : cuda_fail(e);
+}
+
+// Section 4.1 "Decision tree" pruning: partition of the training sizes by a
+// regression tree with at most max_leaves leaves.
+gemm_status_t kselect_tree_regress(int32_t n, int32_t d, const double* features, const float* Y, int32_t max_leaves,
+                                   int32_t* labels_out, float* centres_out, int32_t* n_leaves_out) {
+  if (n < 1 || d < 1 || !features || !Y || max_leaves < 1 || !labels_out || !centres_out || !n_leaves_out)
+    return GEMM_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < (int64_t)n * 4; ++i)
+    if (!std::isfinite(features[i])) return GEMM_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < (int64_t)n * d; ++i)
+    if (!std::isfinite(Y[i])) return GEMM_ERR_INVALID_ARG;
+  RegressionTree rt{features, Y, d};
+  std::vector<std::vector<int>> leaves(1, std::vector<int>(n));
+  std::iota(leaves[0].begin(), leaves[0].end(), 0);
+  std::vector<RegressionTree::Split> splits{rt.best(leaves[0])};
+  const double tol = 1e-12 * rt.sse(leaves[0]);
+  while ((int)leaves.size() < max_leaves) {
+    int pick = -1;
+    for (int i = 0; i < (int)leaves.size(); ++i)
+      if (splits[i].f >= 0 && splits[i].gain > tol &&
+          (pick < 0 || splits[i].gain > splits[pick].gain * (1.0 + kGainTie)))
+        pick = i;
+    if (pick < 0) break;
+    const RegressionTree::Split sp = splits[pick];
+    std::vector<int> left, right;
+    for (int i : leaves[pick]) (features[4 * i + sp.f] <= sp.thr ? left : right).push_back(i);
+    leaves[pick] = std::move(left);
+    leaves.push_back(std::move(right));
+    splits[pick] = rt.best(leaves[pick]);
+    splits.push_back(rt.best(leaves.back()));
+  }
+  for (int c = 0; c < (int)leaves.size(); ++c) {
+    for (int j = 0; j < d; ++j) {
+      double m = 0.0;
+      for (int i : leaves[c]) m += Y[(size_t)i * d + j];
+      centres_out[(size_t)c * d + j] = (float)(m / leaves[c].size());
+    }
+    for (int i : leaves[c]) labels_out[i] = c;
+  }
+  *n_leaves_out = (int32_t)leaves.size();
   return GEMM_OK;
 }
 

@@ -226,7 +226,7 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, float* Cb, int m0, i
 // FAST: the whole slice is inside op(A) and 16-byte loads are legal (interior tile).
 template <class Cfg, bool FAST>
 __device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArgs& p, const float* Ab,
-                                             int m0, int k0, int tid) {
+                                             int m0, int k0, int K, int tid) {
   constexpr int BK = Cfg::BK, BM = Cfg::BM;
 #pragma unroll
   for (int u = 0; u < Cfg::RA; ++u) {
@@ -240,7 +240,7 @@ __device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArg
           r[u] = __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gm * p.lda + gk));
           continue;
         }
-        if (gm < p.M) load_vec_global<4>(v, Ab + (int64_t)gm * p.lda + gk, p.K - gk, p.vecA);
+        if (gm < p.M) load_vec_global<4>(v, Ab + (int64_t)gm * p.lda + gk, K - gk, p.vecA);
       } else {  // stored K x M: chunk of 4 along m
         const int k = c / (BM / 4), mq = (c % (BM / 4)) * 4;
         const int gk = k0 + k, gm = m0 + mq;
@@ -248,7 +248,7 @@ __device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArg
           r[u] = __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gk * p.lda + gm));
           continue;
         }
-        if (gk < p.K) load_vec_global<4>(v, Ab + (int64_t)gk * p.lda + gm, p.M - gm, p.vecA);
+        if (gk < K) load_vec_global<4>(v, Ab + (int64_t)gk * p.lda + gm, p.M - gm, p.vecA);
       }
     }
     r[u] = make_float4(v[0], v[1], v[2], v[3]);
@@ -279,7 +279,7 @@ __device__ __forceinline__ void store_slice_a(const float4 (&r)[Cfg::RA], const 
 
 template <class Cfg, bool FAST>
 __device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArgs& p, const float* Bb,
-                                             int n0, int k0, int tid) {
+                                             int n0, int k0, int K, int tid) {
   constexpr int BK = Cfg::BK, BN = Cfg::BN;
 #pragma unroll
   for (int u = 0; u < Cfg::RB; ++u) {
@@ -293,7 +293,7 @@ __device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArg
           r[u] = __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gk * p.ldb + gn));
           continue;
         }
-        if (gk < p.K) load_vec_global<4>(v, Bb + (int64_t)gk * p.ldb + gn, p.N - gn, p.vecB);
+        if (gk < K) load_vec_global<4>(v, Bb + (int64_t)gk * p.ldb + gn, p.N - gn, p.vecB);
       } else {  // stored N x K: chunk along k
         const int n = c / (BK / 4), kq = (c % (BK / 4)) * 4;
         const int gn = n0 + n, gk = k0 + kq;
@@ -301,7 +301,7 @@ __device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArg
           r[u] = __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gn * p.ldb + gk));
           continue;
         }
-        if (gn < p.N) load_vec_global<4>(v, Bb + (int64_t)gn * p.ldb + gk, p.K - gk, p.vecB);
+        if (gn < p.N) load_vec_global<4>(v, Bb + (int64_t)gn * p.ldb + gk, K - gk, p.vecB);
       }
     }
     r[u] = make_float4(v[0], v[1], v[2], v[3]);
@@ -331,32 +331,45 @@ __device__ __forceinline__ void store_slice_b(const float4 (&r)[Cfg::RB], const 
 }
 
 // ---------------------------------------------------------------- kernel
-template <class Cfg>
+template <class Cfg, bool SPLIT>
 __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
   constexpr int TM = Cfg::TM, TN = Cfg::TN, BK = Cfg::BK, CM = Cfg::CM, CN = Cfg::CN;
   const int tid = threadIdx.x;
   const int tx = tid % Cfg::WX, ty = tid / Cfg::WX;
   const int m0 = blockIdx.x * Cfg::BM, n0 = blockIdx.y * Cfg::BN;
-  const int b = blockIdx.z;
-  const float* Ab = static_cast<const float*>(p.A) + (int64_t)b * p.strideA;
-  const float* Bb = static_cast<const float*>(p.B) + (int64_t)b * p.strideB;
-  float* Cb = p.C + (int64_t)b * p.strideC;
+  // SPLIT instances: blockIdx.z enumerates (batch entry, K split) pairs, split
+  // s covers k in [s * kchunk, min(K, (s + 1) * kchunk)) and writes its own
+  // partial tile (C then points at the split workspace, one M x ldc slab per z).
+  // Otherwise blockIdx.z is the batch entry and the CTA covers all of K.
+  const int z = blockIdx.z;
+  int b = z, K = p.K;
+  int64_t offA = 0, offB = 0;
+  if constexpr (SPLIT) {
+    b = z / p.splits;
+    const int kbeg = (z - b * p.splits) * p.kchunk;
+    K = min(p.K - kbeg, p.kchunk);
+    offA = p.transA ? (int64_t)kbeg * p.lda : kbeg;
+    offB = p.transB ? kbeg : (int64_t)kbeg * p.ldb;
+  }
+  const float* Ab = static_cast<const float*>(p.A) + (int64_t)b * p.strideA + offA;
+  const float* Bb = static_cast<const float*>(p.B) + (int64_t)b * p.strideB + offB;
+  float* Cb = p.C + (int64_t)z * p.strideC;
 
   AccTile<TM, TN> acc;
   acc.zero();
 
-  const int nk = (p.K + BK - 1) / BK;
+  const int nk = (K + BK - 1) / BK;
   if constexpr (Cfg::STAGED) {
     extern __shared__ __align__(16) float smem[];
     float4 ra[Cfg::RA], rb[Cfg::RB];
     // Interior tiles with 16-byte-loadable operands skip every bounds check.
     const bool fast_mn = (m0 + Cfg::BM <= p.M) && (n0 + Cfg::BN <= p.N) && p.vecA && p.vecB;
-    if (fast_mn && BK <= p.K) {
-      load_slice_a<Cfg, true>(ra, p, Ab, m0, 0, tid);
-      load_slice_b<Cfg, true>(rb, p, Bb, n0, 0, tid);
+    if (fast_mn && BK <= K) {
+      load_slice_a<Cfg, true>(ra, p, Ab, m0, 0, K, tid);
+      load_slice_b<Cfg, true>(rb, p, Bb, n0, 0, K, tid);
     } else {
-      load_slice_a<Cfg, false>(ra, p, Ab, m0, 0, tid);
-      load_slice_b<Cfg, false>(rb, p, Bb, n0, 0, tid);
+      load_slice_a<Cfg, false>(ra, p, Ab, m0, 0, K, tid);
+      load_slice_b<Cfg, false>(rb, p, Bb, n0, 0, K, tid);
     }
     store_slice_a<Cfg>(ra, p, smem, tid);
     store_slice_b<Cfg>(rb, p, smem + BK * Cfg::LDS_A, tid);
@@ -367,12 +380,12 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
       const bool more = kt + 1 < nk;
       if (more) {
         const int kn = (kt + 1) * BK;
-        if (fast_mn && kn + BK <= p.K) {
-          load_slice_a<Cfg, true>(ra, p, Ab, m0, kn, tid);
-          load_slice_b<Cfg, true>(rb, p, Bb, n0, kn, tid);
+        if (fast_mn && kn + BK <= K) {
+          load_slice_a<Cfg, true>(ra, p, Ab, m0, kn, K, tid);
+          load_slice_b<Cfg, true>(rb, p, Bb, n0, kn, K, tid);
         } else {
-          load_slice_a<Cfg, false>(ra, p, Ab, m0, kn, tid);
-          load_slice_b<Cfg, false>(rb, p, Bb, n0, kn, tid);
+          load_slice_a<Cfg, false>(ra, p, Ab, m0, kn, K, tid);
+          load_slice_b<Cfg, false>(rb, p, Bb, n0, kn, K, tid);
         }
       }
 #pragma unroll
@@ -399,8 +412,8 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
 #pragma unroll
       for (int kq = 0; kq < BK; kq += 4) {
         const int gk = kt * BK + kq;
-        if (gk >= p.K) break;
-        const int klim = p.K - gk;
+        if (gk >= K) break;
+        const int klim = K - gk;
         float a[TM][4], bv[4][TN];
         if (!p.transA) {
 #pragma unroll
@@ -473,11 +486,11 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
   epilogue<Cfg>(p, Cb, m0, n0, tx, ty, out);
 }
 
-template <int ID>
+template <int ID, bool SPLIT = false>
 cudaError_t launch_simt(const GemmArgs& a, cudaStream_t s) {
   constexpr SimtParams P = simt_params(ID);
   using Cfg = SimtCfg<P.tm, P.tn, P.wx, P.wy, P.bk, P.staged != 0>;
-  auto kern = simt_gemm_kernel<Cfg>;
+  auto kern = simt_gemm_kernel<Cfg, SPLIT>;
   if constexpr (Cfg::SMEM_BYTES > 48 * 1024) {
     static unsigned long long done_mask = 0;  // devices whose attribute is set
     int dev = 0;
@@ -489,9 +502,24 @@ cudaError_t launch_simt(const GemmArgs& a, cudaStream_t s) {
       __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);
     }
   }
-  dim3 grid((a.M + Cfg::BM - 1) / Cfg::BM, (a.N + Cfg::BN - 1) / Cfg::BN, a.batch);
+  dim3 grid((a.M + Cfg::BM - 1) / Cfg::BM, (a.N + Cfg::BN - 1) / Cfg::BN, SPLIT ? a.batch * a.splits : a.batch);
   kern<<<grid, Cfg::T, Cfg::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the split instance of config ID on the current device (0 on error).
+template <int ID>
+int occupancy_simt() {
+  constexpr SimtParams P = simt_params(ID);
+  using Cfg = SimtCfg<P.tm, P.tn, P.wx, P.wy, P.bk, P.staged != 0>;
+  auto kern = simt_gemm_kernel<Cfg, true>;
+  if constexpr (Cfg::SMEM_BYTES > 48 * 1024) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES) != cudaSuccess)
+      return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Cfg::T, Cfg::SMEM_BYTES) != cudaSuccess) return 0;
+  return n;
 }
 
 }  // namespace ks

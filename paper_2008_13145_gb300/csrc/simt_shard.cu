@@ -1,6 +1,7 @@
 // One shard of the FP32 SIMT instantiations.  This file is compiled
 // kSimtShards times with -DKS_SHARD=<i>; shard i instantiates the config ids
-// with id % kSimtShards == i, so the 576 kernels build in parallel.
+// with id % kSimtShards == i, so the 576 kernels (and the 192 split-K
+// instances) build in parallel.
 #include <utility>
 
 #include "simt_gemm.cuh"
@@ -12,18 +13,24 @@
 namespace ks {
 namespace {
 template <int ID>
-void reg_one(LaunchFn* table) {
-  if constexpr (ID % kSimtShards == KS_SHARD) table[ID] = &launch_simt<ID>;
+void reg_one(LaunchFn* table, LaunchFn* split, OccFn* occ) {
+  if constexpr (ID % kSimtShards == KS_SHARD) {
+    table[ID] = &launch_simt<ID, false>;
+    if constexpr (split_eligible(ID)) {
+      split[ID] = &launch_simt<ID, true>;
+      occ[ID] = &occupancy_simt<ID>;
+    }
+  }
 }
 template <int... I>
-void reg_all(std::integer_sequence<int, I...>, LaunchFn* table) {
-  (reg_one<I>(table), ...);
+void reg_all(std::integer_sequence<int, I...>, LaunchFn* table, LaunchFn* split, OccFn* occ) {
+  (reg_one<I>(table, split, occ), ...);
 }
 }  // namespace
 
 #define KS_CAT2(a, b) a##b
 #define KS_CAT(a, b) KS_CAT2(a, b)
-void KS_CAT(simt_register_shard_, KS_SHARD)(LaunchFn* table) {
-  reg_all(std::make_integer_sequence<int, kSimtConfigs>{}, table);
+void KS_CAT(simt_register_shard_, KS_SHARD)(LaunchFn* table, LaunchFn* split, OccFn* occ) {
+  reg_all(std::make_integer_sequence<int, kSimtConfigs>{}, table, split, occ);
 }
 }  // namespace ks

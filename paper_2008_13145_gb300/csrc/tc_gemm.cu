@@ -283,7 +283,10 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   const int64_t in_elem = c.family == GEMM_PREC_BF16 ? 2 : 4;
   const int64_t op_elem = c.family == GEMM_PREC_TF32 ? 4 : 2;
   OperandPlan o;
-  o.direct = !x3 && kcontig && ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0);
+  // Read in place only when K-contiguous, 16-byte aligned and batch-packed (the
+  // tensor map's third dimension steps R x ld); otherwise the pre-pass packs it.
+  o.direct = !x3 && kcontig && ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0) &&
+             (batch == 1 || stride == (int64_t)R * ld);
   const int nseg = x3 ? 3 : 1;
   const int64_t Kp = x3 ? round_up(K, 64) : round_up(K, 16 / op_elem);
   o.ld = o.direct ? ld : nseg * Kp;

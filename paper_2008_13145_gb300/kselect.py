@@ -57,12 +57,17 @@ _sig("gemm_last_cuda_error", i32, [])
 _sig("gemm_config_count", i32, [i32])
 _sig("gemm_config_id", i32, [i32, i32])
 _sig("gemm_config_params", i32, [i32, ctypes.POINTER(i32)])
+_sig("gemm_split_choose", i32, [i64, i64, i64, i64, i32, i32, i32, i32, i32, ctypes.POINTER(i32)])
+_sig("gemm_split_factor", i32, [i32, i64, i64, i64, i64, ctypes.POINTER(i32)])
 _sig("gemm_library_create", i32, [ctypes.POINTER(Deployment), ctypes.POINTER(vp)])
 _sig("gemm_library_destroy", None, [vp])
 _sig("select_kernel", i32, [vp, i64, i64, i64, i64])
 _GEMM_ARGS = [ch, ch, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i64, vp]
 _sig("gemm", i32, [vp] + _GEMM_ARGS)
 _sig("gemm_with_config", i32, [i32] + _GEMM_ARGS)
+_STRIDED_ARGS = [ch, ch, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32, vp, i64, i64, i64, vp]
+_sig("gemm_strided_batched", i32, [vp] + _STRIDED_ARGS)
+_sig("gemm_strided_batched_with_config", i32, [i32] + _STRIDED_ARGS)
 _sig("gemm_host", i32, [vp, ch, ch, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i64, vp, vp, vp, vp])
 _sig("gemm_benchmark", i32, [i32, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64, i64, i32, i32, i32, f64,
                              ctypes.POINTER(f64), vp])
@@ -91,10 +96,16 @@ _sig("kselect_score", i32, [i32, i32, vp, i32, ctypes.POINTER(i32), vp, f32, cty
 _sig("kselect_im2col3x3", i32, [vp, i32, i32, i32, i32, vp, i64, vp])
 _sig("kselect_bias_act", i32, [vp, i64, i32, i64, vp, i32, vp])
 _sig("kselect_maxpool2x2", i32, [vp, i32, i32, i32, i32, vp, vp])
+_sig("kselect_im2col3x3_nchw", i32, [vp, i32, i32, i32, i32, vp, i64, vp])
+_sig("kselect_bias_act_nchw", i32, [vp, i32, i32, i64, vp, i32, vp])
 _sig("kselect_knn", i32, [i32, i32, i32, vp, vp, vp, i32, vp, vp])
 _sig("kselect_representatives", i32, [i32, i32, ctypes.POINTER(f32), i32, ctypes.POINTER(i32), i32,
                                       ctypes.POINTER(i32), ctypes.POINTER(i32)])
 _sig("kselect_top_n", i32, [i32, i32, ctypes.POINTER(f32), i32, ctypes.POINTER(i32)])
+_sig("kselect_spectral_embedding", i32, [i32, i32, vp, f32, i32, i32, i32, vp, vp, ctypes.POINTER(f64), vp])
+_sig("kselect_cluster_geomean", i32, [i32, i32, vp, vp, i32, f32, vp, vp])
+_sig("kselect_tree_regress", i32, [i32, i32, ctypes.POINTER(f64), ctypes.POINTER(f32), i32, ctypes.POINTER(i32),
+                                   ctypes.POINTER(f32), ctypes.POINTER(i32)])
 _sig("kselect_tree_train", i32, [i32, ctypes.POINTER(f64), ctypes.POINTER(i32), i32, i32, i32,
                                  ctypes.POINTER(TreeNode), i32, ctypes.POINTER(i32)])
 
@@ -163,6 +174,24 @@ def config_params(cid: int) -> list[int]:
     return list(out)
 
 
+def split_choose(M, N, K, batch, BM, BN, BK, resident_ctas_per_sm, sm_count) -> tuple[int, int]:
+    """(split factor, K per split) of the split-K kind's host cost model."""
+    kc = i32()
+    r = _lib.gemm_split_choose(M, N, K, batch, BM, BN, BK, resident_ctas_per_sm, sm_count, ctypes.byref(kc))
+    if r < 0:
+        raise KSelectError(r, "gemm_split_choose")
+    return r, kc.value
+
+
+def split_factor(cid: int, M, N, K, batch) -> tuple[int, int]:
+    """(split factor, K per split) config `cid` uses for these sizes on the current device."""
+    kc = i32()
+    r = _lib.gemm_split_factor(cid, M, N, K, batch, ctypes.byref(kc))
+    if r < 0:
+        raise KSelectError(r, "gemm_split_factor")
+    return r, kc.value
+
+
 # ---------------------------------------------------------------- handle
 class Handle:
     """An immutable library handle built from a deployment dict:
@@ -228,6 +257,20 @@ def gemm_with_config(cid: int, transA: str, transB: str, M, N, K, alpha, A, lda,
                      stream=None) -> None:
     check(_lib.gemm_with_config(cid, _c(transA), _c(transB), M, N, K, alpha, ptr(A), lda, ptr(B), ldb, beta,
                                 ptr(C), ldc, batch, stream_handle(stream)), "gemm_with_config")
+
+
+def gemm_strided_batched(h, transA: str, transB: str, M, N, K, alpha, A, lda, strideA, B, ldb, strideB, beta, C,
+                         ldc, strideC, batch=1, stream=None) -> None:
+    check(_lib.gemm_strided_batched(h.value, _c(transA), _c(transB), M, N, K, alpha,
+                                    ptr(A), lda, strideA, ptr(B), ldb, strideB, beta, ptr(C), ldc, strideC, batch,
+                                    stream_handle(stream)), "gemm_strided_batched")
+
+
+def gemm_strided_batched_with_config(cid: int, transA: str, transB: str, M, N, K, alpha, A, lda, strideA, B, ldb,
+                                     strideB, beta, C, ldc, strideC, batch=1, stream=None) -> None:
+    check(_lib.gemm_strided_batched_with_config(cid, _c(transA), _c(transB), M, N, K, alpha, ptr(A), lda, strideA,
+                                                ptr(B), ldb, strideB, beta, ptr(C), ldc, strideC, batch,
+                                                stream_handle(stream)), "gemm_strided_batched_with_config")
 
 
 def gemm_status(cid: int, transA: str, transB: str, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, batch=1,
@@ -346,10 +389,50 @@ def maxpool2x2(x, N, H, W, C, out, stream=None) -> None:
     check(_lib.kselect_maxpool2x2(ptr(x), N, H, W, C, ptr(out), stream_handle(stream)), "kselect_maxpool2x2")
 
 
+def im2col3x3_nchw(x, N, C, H, W, out, ld, stream=None) -> None:
+    check(_lib.kselect_im2col3x3_nchw(ptr(x), N, C, H, W, ptr(out), ld, stream_handle(stream)),
+          "kselect_im2col3x3_nchw")
+
+
+def bias_act_nchw(y, N, C, HW, bias, relu=True, stream=None) -> None:
+    check(_lib.kselect_bias_act_nchw(ptr(y), N, C, HW, ptr(bias), int(relu), stream_handle(stream)),
+          "kselect_bias_act_nchw")
+
+
 def knn(train, labels, query, k: int, out, stream=None) -> None:
     """k-nearest-neighbour labels of the query rows (device tensors)."""
     check(_lib.kselect_knn(train.shape[0], query.shape[0], train.shape[1], ptr(train), ptr(labels), ptr(query), k,
                            ptr(out), stream_handle(stream)), "kselect_knn")
+
+
+def spectral_embedding(X, gamma: float, k: int, V0, U_out, iters: int = 200, stream=None) -> np.ndarray:
+    """Unit-length spectral coordinates (U_out, n x k) of the rows of X; V0 (n x r) the
+    starting block.  Returns the k leading eigenvalues of D^-1/2 A D^-1/2."""
+    n, d = X.shape
+    r = V0.shape[1]
+    ev = (f64 * k)()
+    check(_lib.kselect_spectral_embedding(n, d, ptr(X), gamma, k, r, iters, ptr(V0), ptr(U_out), ev,
+                                          stream_handle(stream)), "kselect_spectral_embedding")
+    return np.array(ev[:])
+
+
+def cluster_geomean(X, labels, k: int, out, floor: float = 1e-6, stream=None) -> None:
+    check(_lib.kselect_cluster_geomean(X.shape[0], X.shape[1], ptr(X), ptr(labels), k, floor, ptr(out),
+                                       stream_handle(stream)), "kselect_cluster_geomean")
+
+
+def tree_regress(features: np.ndarray, Y: np.ndarray, max_leaves: int) -> tuple[np.ndarray, np.ndarray]:
+    """Regression-tree partition of the sizes (host): (labels, leaf-mean centres)."""
+    n, d = Y.shape
+    F, pf = _arr(features, np.float64, f64)
+    Yc, py = _arr(Y, np.float32, f32)
+    labels = np.zeros(n, np.int32)
+    centres = np.zeros((max_leaves, d), np.float32)
+    nl = i32()
+    check(_lib.kselect_tree_regress(n, d, pf, py, max_leaves, labels.ctypes.data_as(ctypes.POINTER(i32)),
+                                    centres.ctypes.data_as(ctypes.POINTER(f32)), ctypes.byref(nl)),
+          "kselect_tree_regress")
+    return labels, centres[:nl.value].copy()
 
 
 def representatives(centres: np.ndarray, labels: np.ndarray, dedupe=True) -> np.ndarray:
@@ -464,9 +547,9 @@ def select_kernels_batched(handle: Handle, shapes, ids_out, pred=None, stream=No
 def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points this binding expects."""
     return ["gemm_status_string", "gemm_last_cuda_error", "gemm_config_count", "gemm_config_id",
-            "gemm_config_params", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
-            "gemm_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
+            "gemm_config_params", "gemm_split_choose", "gemm_split_factor", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
+            "gemm_with_config", "gemm_strided_batched", "gemm_strided_batched_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
             "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
-            "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_train", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
+            "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_im2col3x3_nchw", "kselect_bias_act_nchw", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_regress", "kselect_tree_train", "kselect_spectral_embedding", "kselect_cluster_geomean", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
             "gemm_grouped_plan_destroy", "gemm_grouped"]

@@ -53,6 +53,9 @@ def alloc_inputs(shape: wl.Shape, precision: int, seed: int, device="cuda"):
     return A, B, C, lda, ldb, ldc
 
 
+SPLIT_BASE = 2000  # ids of the FP32 split-K kind: SPLIT_BASE + base config
+
+
 # ---------------------------------------------------------------- Section 3.1
 def sweep(shapes: list[wl.Shape], precision: int, out_path: str, seed: int = 0, refine_ratio: float = 2.0,
           min_total_ms: float = 2.0, config_ids: list[int] | None = None, log=sys.stderr) -> np.ndarray:
@@ -185,6 +188,63 @@ def prune_pca(perf_train: np.ndarray, k: int, seed: int = 0, norm: str = "standa
             "explained": float(np.sum(ev[:r]) / tot), "labels": lab.cpu().numpy().tolist()}
 
 
+def prune_spectral(perf_train: np.ndarray, k: int, seed: int = 0, norm: str = "standard", n_init: int = 10,
+                   iters: int = 300, oversample: int = 10) -> dict:
+    """Spectral clustering pruning (Section 4.1): k-means on the spectral
+    coordinates of the RBF similarity graph of the normalised performance
+    vectors, gamma = 1 / (2 x total per-configuration variance) (one over the
+    mean squared distance between two sizes); clusters give labels only, so each
+    deployed configuration is the best of its cluster's geometric-mean vector
+    (Section 4.2)."""
+    import torch
+    ks = _ks()
+    P = torch.from_numpy(np.ascontiguousarray(perf_train, np.float32)).cuda()
+    X = torch.empty_like(P)
+    ks.normalise(P, X, norm)
+    n, d = X.shape
+    var = X.double().var(dim=0, unbiased=False).sum().item()
+    gamma = 1.0 / (2.0 * var) if var > 0 else 1.0
+    r = min(n, k + oversample)
+    V0 = torch.from_numpy(wl.rng_for(seed, 71).standard_normal((n, r)).astype(np.float32)).cuda()
+    U = torch.empty((n, k), device="cuda")
+    ev = ks.spectral_embedding(X, gamma, k, V0, U, iters)
+    cen = torch.empty((k, k), device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    inertia, it = ks.kmeans(U, k, kmeans_draws(n_init, k, seed), cen, lab)
+    gm = torch.empty((k, d), device="cuda")
+    ks.cluster_geomean(X, lab, k, gm)
+    cols = ks.representatives(gm.cpu().numpy(), lab.cpu().numpy(), dedupe=True)
+    return {"cols": [int(c) for c in cols], "inertia": inertia, "iters": it, "gamma": gamma,
+            "eigenvalues": [float(v) for v in ev], "labels": lab.cpu().numpy().tolist()}
+
+
+def prune_tree(perf_train: np.ndarray, shapes_train, k: int, norm: str = "standard") -> dict:
+    """Decision-tree pruning (Section 4.1): a regression tree from the sizes to
+    the normalised performance vectors with at most k leaves; each leaf's mean
+    vector stands for its sizes and gives one deployed configuration."""
+    import torch
+    ks = _ks()
+    P = torch.from_numpy(np.ascontiguousarray(perf_train, np.float32)).cuda()
+    X = torch.empty_like(P)
+    ks.normalise(P, X, norm)
+    labels, centres = ks.tree_regress(features(shapes_train), X.cpu().numpy(), k)
+    cols = ks.representatives(centres, labels, dedupe=True)
+    return {"cols": [int(c) for c in cols], "inertia": None, "leaves": int(centres.shape[0]),
+            "labels": labels.tolist()}
+
+
+def prune_by(method: str, perf_train: np.ndarray, shapes_train, k: int, seed: int = 0, norm: str = "standard"):
+    if method == "kmeans":
+        return prune(perf_train, k, seed, norm)
+    if method == "pca":
+        return prune_pca(perf_train, k, seed, norm)
+    if method == "spectral":
+        return prune_spectral(perf_train, k, seed, norm)
+    if method == "tree":
+        return prune_tree(perf_train, shapes_train, k, norm)
+    raise ValueError(method)
+
+
 def features(shapes) -> np.ndarray:
     return np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
 
@@ -216,7 +276,7 @@ def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard"
            method: str = "kmeans") -> dict:
     shapes, perf, ids, precision = load_table(table_path)
     tr, te = wl.train_test_split(len(shapes), split_seed)
-    pr = prune(perf[tr], k, seed, norm) if method == "kmeans" else prune_pca(perf[tr], k, seed, norm)
+    pr = prune_by(method, perf[tr], [shapes[i] for i in tr], k, seed, norm)
     nodes = train_tree(perf[tr], [shapes[i] for i in tr], pr["cols"], tree)
     dep = {"precision": precision, "config_ids": [ids[c] for c in pr["cols"]], "nodes": nodes}
     ev = evaluate(perf[te], [shapes[i] for i in te], dep, ids)
@@ -326,19 +386,23 @@ def mlp_study(deploy_path: str, sweep_path: str, n: int = 2500, seed: int = 4, s
 # ---------------------------------------------------------------- pruning study (Figures 5-6 analogue)
 def pruning_study(table_path: str, k_values=range(4, 16), seed: int = 0, split_seed: int = 1) -> dict:
     """Held-out deployed-set maximum (geometric mean of the best deployed
-    kernel's fraction of the per-shape optimum) for k-means and PCA + k-means
-    pruning under each normalisation of Section 3.4 and for the Top-N
-    baseline, k = 4..15."""
+    kernel's fraction of the per-shape optimum) for k-means, PCA + k-means,
+    spectral clustering and decision-tree pruning under each normalisation of
+    Section 3.4 and for the Top-N baseline, k = 4..15."""
     import torch
     ks = _ks()
     shapes, perf, ids, _ = load_table(table_path)
     tr, te = wl.train_test_split(len(shapes), split_seed)
+    s_tr = [shapes[i] for i in tr]
     P = torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda()
-    out = {"k": list(k_values), "kmeans": {}, "pca_kmeans": {}, "top_n": []}
+    methods = {"kmeans": "kmeans", "pca_kmeans": "pca", "spectral": "spectral", "tree": "tree"}
+    out = {"k": list(k_values), "top_n": []}
+    for key in methods:
+        out[key] = {}
     for norm in ("standard", "raw_cutoff", "standard_cutoff", "sigmoid"):
-        out["kmeans"][norm] = [ks.score(P, prune(perf[tr], k, seed, norm)["cols"])["geomean"] for k in k_values]
-        out["pca_kmeans"][norm] = [ks.score(P, prune_pca(perf[tr], k, seed, norm)["cols"])["geomean"]
-                                   for k in k_values]
+        for key, method in methods.items():
+            out[key][norm] = [ks.score(P, prune_by(method, perf[tr], s_tr, k, seed, norm)["cols"])["geomean"]
+                              for k in k_values]
     out["top_n"] = [ks.score(P, [int(c) for c in ks.top_n(perf[tr].astype(np.float32), k)])["geomean"]
                     for k in k_values]
     return out
@@ -455,17 +519,30 @@ def grouped_tune(families=("tf32", "bf16", "f32x3")) -> dict:
 
 
 # ---------------------------------------------------------------- VGG16 layers (Section 6)
-def vgg_study(deploy_path: str, sweep_path: str, batches=(1, 16)) -> dict:
+def vgg_study(deploy_path: str, sweep_path: str, batches=(1, 16), layout: str = "nhwc") -> dict:
     """Per VGG16 GEMM (im2col convolutions and FC layers): the throughput of the
     kernel the deployed tree selects against the layer's exhaustive best over
     the whole family, and the layer-time-weighted totals."""
+    return network_study("vgg16", deploy_path, sweep_path, batches, layout)
+
+
+def network_study(net: str, deploy_path: str, sweep_path: str, batches=(1, 16), layout: str = "nhwc") -> dict:
+    """vgg_study for any network of workloads.NETWORKS: each distinct GEMM of the
+    forward pass is benchmarked over every config once; layers that repeat a GEMM
+    count once per occurrence in the totals."""
     ks = _ks()
     dep = json.load(open(deploy_path))
     prec = dep["precision"]
     ids = ks.config_ids(prec)
-    layers = [(b, name, sh) for b in batches for name, sh in wl.vgg16_layers(b)]
+    make = wl.NETWORKS[net]
+    layers = [(b, name, sh) for b in batches
+              for name, sh in (make(b, layout) if net == "vgg16" else make(b))]
+    uniq = {}
+    for _, _, sh in layers:
+        uniq.setdefault(sh, len(uniq))
+    perf_u = sweep(list(uniq), prec, sweep_path, seed=77, config_ids=ids)
     shapes = [sh for _, _, sh in layers]
-    perf = sweep(shapes, prec, sweep_path, seed=77, config_ids=ids)
+    perf = perf_u[[uniq[sh] for sh in shapes]]
     h = ks.Handle(dep)
     col = {c: j for j, c in enumerate(ids)}
     mlp = mlp_choose(np.asarray(dep["mlp_params"], np.float32), shapes, dep["config_ids"]) \
@@ -505,6 +582,8 @@ def main(argv=None):
     s.add_argument("--seed", type=int, default=1)
     s.add_argument("--out", required=True)
     s.add_argument("--table", default=None)
+    s.add_argument("--kind", default="all", choices=["all", "base", "split"],
+                   help="FP32 only: every config, the 576 base configs, or the split-K kind")
     ml = sub.add_parser("mlp")
     ml.add_argument("--deploy", required=True)
     ml.add_argument("--sweep", required=True)
@@ -527,13 +606,19 @@ def main(argv=None):
     vg.add_argument("--deploy", required=True)
     vg.add_argument("--sweep", required=True)
     vg.add_argument("--out", required=True)
+    vg.add_argument("--layout", default="nhwc", choices=["nhwc", "batched"])
+    nw = sub.add_parser("network")
+    nw.add_argument("--net", required=True, choices=sorted(wl.NETWORKS))
+    nw.add_argument("--deploy", required=True)
+    nw.add_argument("--sweep", required=True)
+    nw.add_argument("--out", required=True)
     d = sub.add_parser("deploy")
     d.add_argument("--table", required=True)
     d.add_argument("--k", type=int, default=8)
     d.add_argument("--tree", default="B")
     d.add_argument("--norm", default="standard")
     d.add_argument("--seed", type=int, default=0)
-    d.add_argument("--method", default="kmeans", choices=["kmeans", "pca"])
+    d.add_argument("--method", default="kmeans", choices=["kmeans", "pca", "spectral", "tree"])
     d.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     ks = _ks()
@@ -558,8 +643,14 @@ def main(argv=None):
             json.dump(r, f, indent=1)
         print(json.dumps({k: {"config": v["config"], "tflops": v["tflops"]} for k, v in r.items()}, indent=1))
         return
+    if a.cmd == "network":
+        r = network_study(a.net, a.deploy, a.sweep)
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps(r["totals"], indent=1))
+        return
     if a.cmd == "vgg":
-        r = vgg_study(a.deploy, a.sweep)
+        r = vgg_study(a.deploy, a.sweep, layout=a.layout)
         with open(a.out, "w") as f:
             json.dump(r, f, indent=1)
         print(json.dumps(r["totals"], indent=1))
@@ -576,9 +667,12 @@ def main(argv=None):
     if a.cmd == "sweep":
         prec = ks.PRECISIONS[a.precision]
         shapes = wl.shape_grid(a.n, a.seed)
-        perf = sweep(shapes, prec, a.out)
+        ids = ks.config_ids(prec)
+        if a.kind != "all":
+            ids = [c for c in ids if (c >= SPLIT_BASE) == (a.kind == "split")]
+        perf = sweep(shapes, prec, a.out, config_ids=ids)
         if a.table:
-            save_table(a.table, shapes, perf, ks.config_ids(prec), prec)
+            save_table(a.table, shapes, perf, ids, prec)
     else:
         dep = deploy(a.table, a.k, a.tree, a.seed, a.norm, method=a.method)
         with open(a.out, "w") as f:

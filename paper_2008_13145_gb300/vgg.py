@@ -65,15 +65,35 @@ def flops(plan, batch: int) -> int:
     return f
 
 
-class VGG16:
-    """Device weights plus activation buffers for one batch size."""
+def nchw_fc1(W1: np.ndarray, hw: int, c: int) -> np.ndarray:
+    """The first FC layer's weights for an NCHW flatten (c, h, w): the same layer
+    as W1 on the NHWC flatten (h, w, c), so both layouts compute the same logits."""
+    nout = W1.shape[0]
+    return np.ascontiguousarray(W1.reshape(nout, hw, hw, c).transpose(0, 3, 1, 2).reshape(nout, -1))
 
-    def __init__(self, handle, batch: int, width_div: int = 1, hw: int = 224, classes: int = 1000, seed: int = 7):
+
+class VGG16:
+    """Device weights plus activation buffers for one batch size.
+
+    layout "nhwc": one GEMM per convolution with M = batch x H x W, N = Cout
+    (the im2col rows of all images at once).  layout "batched": the paper's
+    GEMM-batched form, per image M = Cout, N = H x W, batch = images, the
+    weights shared by a zero batch stride; activations NCHW."""
+
+    def __init__(self, handle, batch: int, width_div: int = 1, hw: int = 224, classes: int = 1000, seed: int = 7,
+                 layout: str = "nhwc"):
         import torch
+        assert layout in ("nhwc", "batched")
         self.plan = layer_plan(width_div, hw, classes)
-        self.handle, self.batch = handle, batch
+        self.handle, self.batch, self.layout = handle, batch, layout
+        host = make_weights(self.plan, seed)
+        if layout == "batched":
+            fc1 = next(i for i, layer in enumerate(self.plan) if layer[0] == "fc")
+            last = [layer for layer in self.plan[:fc1] if layer[0] == "pool"][-1]
+            side, chans = last[1] // 2, last[2]
+            host[fc1] = (nchw_fc1(host[fc1][0], side, chans), host[fc1][1])
         self.weights = [None if w is None else (torch.from_numpy(w[0]).cuda(), torch.from_numpy(w[1]).cuda())
-                        for w in make_weights(self.plan, seed)]
+                        for w in host]
         biggest_act, biggest_col = 0, 0
         for layer in self.plan:
             if layer[0] == "conv":
@@ -87,13 +107,27 @@ class VGG16:
         self.flops = flops(self.plan, batch)
 
     def forward(self, x, stream=None):
-        """x: device (batch, hw, hw, 3) float32; returns the logits tensor (batch, classes)."""
+        """x: device (batch, hw, hw, 3) NHWC float32 (the "batched" layout takes
+        (batch, 3, hw, hw) NCHW); returns the logits tensor (batch, classes)."""
         from . import kselect as ks
         n = self.batch
         cur = x.reshape(-1)
         nxt = 0
         for layer, w in zip(self.plan, self.weights):
             out = self.act[nxt]
+            if self.layout == "batched" and layer[0] != "fc":
+                if layer[0] == "conv":
+                    _, h, ci, co = layer
+                    K, ldk = 9 * ci, wl.round_up(9 * ci, 4)
+                    ks.im2col3x3_nchw(cur, n, ci, h, h, self.col, ldk, stream)
+                    ks.gemm_strided_batched(self.handle, "N", "T", co, h * h, K, 1.0, w[0], K, 0, self.col, ldk,
+                                            h * h * ldk, 0.0, out, h * h, co * h * h, n, stream)
+                    ks.bias_act_nchw(out, n, co, h * h, w[1], True, stream)
+                else:
+                    _, h, c = layer
+                    ks.maxpool2x2(cur, n * c, h, h, 1, out, stream)
+                cur, nxt = out, 1 - nxt
+                continue
             if layer[0] == "conv":
                 _, h, ci, co = layer
                 M, K = n * h * h, 9 * ci

@@ -83,19 +83,66 @@ def train_test_split(n: int, seed: int, train_frac: float = 0.8) -> tuple[np.nda
     return np.sort(perm[:n_train]), np.sort(perm[n_train:])
 
 
-def vgg16_layers(batch: int) -> list[tuple[str, Shape]]:
-    """VGG16 GEMMs.  Activations (im2col rows) are A (M x K, 'N'); weights are
-    stored output-channel-major (N x K), so op(B) = B^T ('T')."""
+def vgg16_layers(batch: int, layout: str = "nhwc") -> list[tuple[str, Shape]]:
+    """VGG16 GEMMs.  layout "nhwc": activations (im2col rows of all images) are
+    A (M = batch x H x W by K, 'N'); weights are stored output-channel-major
+    (N x K), so op(B) = B^T ('T').  layout "batched" (the GEMM-batched form of
+    Section 6): per image, weights A (Cout x K, 'N') times the image's im2col
+    rows B (H W x K, 'T'), batch = images.  FC layers are the same in both."""
     convs = [("conv1_1", 224, 3, 64), ("conv1_2", 224, 64, 64),
              ("conv2_1", 112, 64, 128), ("conv2_2", 112, 128, 128),
              ("conv3_1", 56, 128, 256), ("conv3_2", 56, 256, 256), ("conv3_3", 56, 256, 256),
              ("conv4_1", 28, 256, 512), ("conv4_2", 28, 512, 512), ("conv4_3", 28, 512, 512),
              ("conv5_1", 14, 512, 512), ("conv5_2", 14, 512, 512), ("conv5_3", 14, 512, 512)]
-    out = [(name, Shape(hw * hw * batch, cout, 9 * cin, 1, "N", "T")) for name, hw, cin, cout in convs]
+    if layout == "batched":
+        out = [(name, Shape(cout, hw * hw, 9 * cin, batch, "N", "T")) for name, hw, cin, cout in convs]
+    else:
+        out = [(name, Shape(hw * hw * batch, cout, 9 * cin, 1, "N", "T")) for name, hw, cin, cout in convs]
     out += [("fc6", Shape(batch, 4096, 25088, 1, "N", "T")),
             ("fc7", Shape(batch, 4096, 4096, 1, "N", "T")),
             ("fc8", Shape(batch, 1000, 4096, 1, "N", "T"))]
     return out
+
+
+def _lowered(name: str, out_hw: int, k: int, cin: int, cout: int, batch: int) -> tuple[str, Shape]:
+    """A k x k convolution as an im2col GEMM: M = output pixels x images, N = Cout, K = k^2 Cin."""
+    return name, Shape(out_hw * out_hw * batch, cout, k * k * cin, 1, "N", "T")
+
+
+def resnet50_layers(batch: int) -> list[tuple[str, Shape]]:
+    """ResNet-50 (v1.5: stride 2 on the 3x3 convolution of each downsampling block),
+    224 x 224 input, every convolution lowered by im2col plus the FC layer.  Repeated
+    blocks repeat their GEMMs (the per-layer list, as a forward pass runs it)."""
+    out = [_lowered("conv1", 112, 7, 3, 64, batch)]
+    cin = 64
+    for stage, (width, blocks, hw) in enumerate([(64, 3, 56), (128, 4, 28), (256, 6, 14), (512, 3, 7)], start=2):
+        for b in range(blocks):
+            in_hw = hw * 2 if (b == 0 and stage > 2) else hw
+            tag = f"conv{stage}_{b + 1}"
+            out.append(_lowered(tag + "a", in_hw, 1, cin, width, batch))
+            out.append(_lowered(tag + "b", hw, 3, width, width, batch))
+            out.append(_lowered(tag + "c", hw, 1, width, 4 * width, batch))
+            if b == 0:
+                out.append(_lowered(tag + "_down", hw, 1, cin, 4 * width, batch))
+            cin = 4 * width
+    out.append(("fc", Shape(batch, 1000, 2048, 1, "N", "T")))
+    return out
+
+
+def mobilenet_v1_layers(batch: int) -> list[tuple[str, Shape]]:
+    """MobileNet v1 (width 1.0, 224 x 224): the first 3x3 convolution and the 13
+    pointwise (1x1) convolutions as im2col GEMMs, plus the FC layer.  The 3x3
+    depthwise convolutions are not matrix multiplies (one 9-tap filter per channel)
+    and are left out."""
+    pw = [(112, 32, 64), (56, 64, 128), (56, 128, 128), (28, 128, 256), (28, 256, 256), (14, 256, 512)] + \
+         [(14, 512, 512)] * 5 + [(7, 512, 1024), (7, 1024, 1024)]
+    out = [_lowered("conv1", 112, 3, 3, 32, batch)]
+    out += [_lowered(f"pw{i + 1}", hw, 1, cin, cout, batch) for i, (hw, cin, cout) in enumerate(pw)]
+    out.append(("fc", Shape(batch, 1000, 1024, 1, "N", "T")))
+    return out
+
+
+NETWORKS = {"vgg16": vgg16_layers, "resnet50": resnet50_layers, "mobilenet_v1": mobilenet_v1_layers}
 
 
 def grouped_problems(n: int = 256, seed: int = 3, lo: int = 32, hi: int = 4096) -> list[Shape]:

@@ -44,14 +44,62 @@ def test_every_declared_symbol_is_exported(ks):
 
 
 def test_simt_config_space(ks):
-    assert ks.config_count(ks.PREC_F32) == 576
-    seen = set()
-    for cid in ks.config_ids(ks.PREC_F32):
-        fam, tm, tn, wx, wy, bk, staged, _ = ks.config_params(cid)
+    assert ks.config_count(ks.PREC_F32) == 576 + 192
+    ids = ks.config_ids(ks.PREC_F32)
+    assert ids[:576] == list(range(576))
+    seen, split = set(), []
+    for cid in ids:
+        fam, tm, tn, wx, wy, bk, staged, splitk = ks.config_params(cid)
         assert fam == 0 and tm in (1, 2, 4, 8) and tn in (1, 2, 4, 8) and bk in (8, 16, 32) and staged in (0, 1)
         assert (wx, wy) in [(8, 8), (16, 16), (32, 8), (8, 32), (16, 8), (8, 16)]
-        seen.add((tm, tn, wx, wy, bk, staged))
+        assert splitk == (cid >= 2000)
+        if splitk:
+            split.append((tm, tn, wx, wy, bk, staged))
+            assert ks.config_params(cid - 2000)[:7] == [fam, tm, tn, wx, wy, bk, staged]
+        else:
+            seen.add((tm, tn, wx, wy, bk, staged))
     assert len(seen) == 576
+    # the split-K kind: every staged config with BK 16 or 32, once, ids ascending
+    assert sorted(set(split)) == sorted(c for c in seen if c[5] == 1 and c[4] in (16, 32))
+    assert len(split) == 192 and ids[576:] == sorted(ids[576:])
+    for bad in (2000, 2001, 2002, 2000 + 576, 576, 1999):  # unstaged or BK 8 bases, out of range
+        with pytest.raises(ks.KSelectError):
+            ks.config_params(bad)
+
+
+def test_split_choice_invariants(ks):
+    """The split-K kind's host cost model on GB300-like figures (152 SMs)."""
+    # a full-GPU product never splits
+    assert ks.split_choose(4096, 4096, 4096, 1, 64, 64, 32, 4, 152) == (1, 4096)
+    # K too short for a first split of 4 K-steps and a second one
+    assert ks.split_choose(64, 64, 192, 1, 64, 64, 32, 4, 152) == (1, 192)
+    assert ks.split_choose(64, 64, 193, 1, 64, 64, 32, 4, 152) == (2, 128)
+    for (M, N, K, b, BM, BN, BK) in [(64, 64, 8192, 1, 64, 64, 32), (37, 45, 2000, 2, 32, 32, 16),
+                                    (300, 200, 3945, 8, 64, 32, 32), (323, 312, 3945, 8, 64, 64, 32),
+                                    (100, 100, 100000, 1, 128, 64, 16)]:
+        S, kc = ks.split_choose(M, N, K, b, BM, BN, BK, 4, 152)
+        assert 2 <= S <= 16, (M, N, K, S)
+        nk = -(-K // BK)
+        assert kc % BK == 0 and kc // BK >= 4
+        assert S == -(-nk // (kc // BK))  # every split non-empty
+        assert (S - 1) * kc < K <= S * kc
+        assert b * S <= 65535 and S * b * M * (-(-N // 4) * 4) * 4 <= 256 << 20
+    # batch x S stays within the grid's z limit
+    S, _ = ks.split_choose(8, 8, 4096, 65535, 64, 64, 32, 4, 152)
+    assert S == 1
+    S, _ = ks.split_choose(8, 8, 4096, 60000, 64, 64, 32, 4, 152)
+    assert S == 1
+    # the partial-tile workspace stays within 256 MB
+    S, _ = ks.split_choose(4000, 4000, 1 << 20, 1, 4096, 4096, 32, 1, 1)
+    assert S == 1 or S * 4000 * 4000 * 4 <= 256 << 20
+    # no occupancy information, or degenerate sizes: no split
+    assert ks.split_choose(64, 64, 8192, 1, 64, 64, 32, 0, 152)[0] == 1
+    assert ks.split_choose(0, 64, 8192, 1, 64, 64, 32, 4, 152)[0] == 1
+    assert ks.split_choose(64, 64, 0, 1, 64, 64, 32, 4, 152) == (1, 0)
+    for bad in [(-1, 64, 64, 1, 64, 64, 32, 4, 152), (64, 64, 64, 1, 0, 64, 32, 4, 152),
+                (64, 64, 1 << 31, 1, 64, 64, 32, 4, 152)]:
+        with pytest.raises(ks.KSelectError):
+            ks.split_choose(*bad)
 
 
 def test_tc_config_space(ks):
@@ -144,3 +192,12 @@ def test_argument_validation_needs_no_device(ks):
     assert st(M=0, A=0, B=0, C=0) == 0  # empty: no-op
     assert st(batch=0) == 0
     assert ks.gemm_status(5000, "N", "N", 4, 4, 4, 1.0, fake, 4, fake, 4, 0.0, fake, 4, 1, stream=0) == -6
+
+    def strided(sa, sb, sc, batch=3, cid=0):
+        return ks._lib.gemm_strided_batched_with_config(cid, b"N", b"N", 4, 4, 4, 1.0, fake, 4, sa, fake, 4, sb, 0.0,
+                                                       fake, 4, sc, batch, None)
+    assert strided(-1, 16, 16) == -1
+    assert strided(16, -4, 16) == -1
+    assert strided(16, 16, 15) == -1  # batch entries would overlap in C
+    assert strided(0, 0, 0, batch=1, cid=5000) == -6
+    assert strided(0, 16, 16, batch=0) == 0  # empty: no-op

@@ -98,3 +98,60 @@ def test_knn_matches_oracle(lib, torch, k):
     lib.knn(torch.from_numpy(train).cuda(), torch.from_numpy(labels).cuda(), torch.from_numpy(query).cuda(), k, out)
     want = osel.knn_predict(train.astype(np.float64), labels, query.astype(np.float64), k)
     assert np.array_equal(out.cpu().numpy(), want)
+
+
+# ---------------------------------------------------------------- spectral clustering (Section 4.1)
+def blobs(seed, n_per=40, k=4, d=12, spread=0.15):
+    rng = np.random.default_rng(seed)
+    centres = rng.random((k, d)) * 3
+    truth = np.repeat(np.arange(k), n_per)
+    X = centres[truth] + spread * rng.standard_normal((k * n_per, d))
+    return X.astype(np.float32), truth
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_spectral_embedding_matches_oracle(lib, torch, seed):
+    """Eigenvalues to 2e-4; the embedding through the rotation-invariant Gram
+    matrix U U^T (eigenvectors are fixed only up to sign and, within a
+    multiple eigenvalue, rotation) to 2e-3."""
+    X, _ = blobs(seed)
+    n, k, r = X.shape[0], 4, 12
+    gamma = 1.0 / (2.0 * X.astype(np.float64).var(axis=0).sum())
+    V0 = np.random.default_rng(50 + seed).standard_normal((n, r)).astype(np.float32)
+    U = torch.empty((n, k), device="cuda")
+    ev = lib.spectral_embedding(torch.from_numpy(X).cuda(), gamma, k, torch.from_numpy(V0).cuda(), U, iters=300)
+    Uo, wo = osel.spectral_embedding(osel.rbf_affinity(X.astype(np.float64), gamma), k)
+    assert np.allclose(ev, wo, atol=2e-4), (ev, wo)
+    Ug = U.cpu().numpy().astype(np.float64)
+    assert np.allclose(np.linalg.norm(Ug, axis=1), 1.0, atol=1e-5)
+    assert np.allclose(Ug @ Ug.T, Uo @ Uo.T, atol=2e-3)
+
+
+def test_spectral_partition_recovers_blobs(lib, torch):
+    X, truth = blobs(3)
+    n, k = X.shape[0], 4
+    gamma = 1.0 / (2.0 * X.astype(np.float64).var(axis=0).sum())
+    V0 = np.random.default_rng(9).standard_normal((n, 14)).astype(np.float32)
+    U = torch.empty((n, k), device="cuda")
+    lib.spectral_embedding(torch.from_numpy(X).cuda(), gamma, k, torch.from_numpy(V0).cuda(), U, iters=300)
+    cen = torch.empty((k, k), device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    draws = np.random.default_rng(4).integers(0, 2 ** 32, (10, k), dtype=np.uint64).astype(np.uint32)
+    lib.kmeans(U, k, draws, cen, lab)
+    got = lab.cpu().numpy()
+    assert len(set(zip(got.tolist(), truth.tolist()))) == k
+    ref, _ = osel.spectral_partition(X.astype(np.float64), k, gamma, draws / 2.0 ** 32)
+    assert len(set(zip(got.tolist(), ref.tolist()))) == k
+
+
+def test_cluster_geomean_matches_oracle(lib, torch):
+    rng = np.random.default_rng(8)
+    X = (rng.random((300, 50)) ** 2).astype(np.float32)
+    X[:20, :5] = 0.0  # clamped at the floor
+    labels = rng.integers(0, 6, 300).astype(np.int32)
+    labels[labels == 4] = 3  # cluster 4 empty
+    out = torch.full((6, 50), 7.0, device="cuda")
+    lib.cluster_geomean(torch.from_numpy(X).cuda(), torch.from_numpy(labels).cuda(), 6, out, floor=1e-6)
+    want = osel.cluster_geomean_centres(X.astype(np.float64), labels, 6, floor=1e-6)
+    assert np.allclose(out.cpu().numpy(), want, rtol=2e-6, atol=0)
+    assert np.all(out.cpu().numpy()[4] == 0)

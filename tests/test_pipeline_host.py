@@ -85,3 +85,48 @@ def test_top_n_matches_oracle(ks, seed):
     perf[:, 7] *= 3.0
     for n in (1, 4, 8, 15, 30):
         assert list(ks.top_n(perf, n)) == list(osel.top_n(perf.astype(np.float64), n))
+
+
+# ---------------------------------------------------------------- regression-tree pruning (Section 4.1)
+def same_partition(a, b):
+    return len(set(zip(a.tolist(), b.tolist()))) == len(set(a.tolist())) == len(set(b.tolist()))
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("k", [1, 2, 4, 8, 15])
+def test_tree_regress_matches_oracle(ks, seed, k):
+    """Tie-free sizes, float32 performance vectors: the same leaves in the same
+    order (exact labels) and leaf means within float rounding."""
+    rng = np.random.default_rng(100 + seed)
+    F = rng.permutation(4096)[:4 * 90].reshape(90, 4).astype(np.float64) + 16
+    Y = (rng.random((90, 12)) ** 3).astype(np.float32)
+    labels, centres = ks.tree_regress(F, Y, k)
+    ref_labels, ref_centres = osel.tree_regression_partition(F, Y.astype(np.float64), k)
+    assert np.array_equal(labels, ref_labels)
+    assert np.allclose(centres, ref_centres, rtol=0, atol=1e-6)
+
+
+def test_tree_regress_on_grid_sizes_with_ties(ks):
+    """Grid-like sizes (repeated values, batch in 5 levels) and normalised rows:
+    same partition as the oracle."""
+    from paper_2008_13145_gb300 import workloads as wl
+    shapes = wl.shape_grid(300, 9)
+    F = np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
+    rng = np.random.default_rng(9)
+    perf = rng.random((300, 20)) * np.log(F[:, :1]) * np.sqrt(F[:, 3:4])
+    Y = osel.normalise(perf, "standard").astype(np.float32)
+    for k in (4, 8, 15):
+        labels, _ = ks.tree_regress(F, Y, k)
+        ref, _ = osel.tree_regression_partition(F, Y.astype(np.float64), k)
+        assert same_partition(labels, ref), k
+
+
+def test_tree_regress_constant_leaves_stop(ks):
+    F = np.array([[16, 16, 16, 1], [32, 16, 16, 1], [64, 16, 16, 1], [128, 16, 16, 1]], np.float64)
+    Y = np.array([[1, 0], [1, 0], [0, 1], [0, 1]], np.float32)
+    labels, centres = ks.tree_regress(F, Y, 4)
+    assert labels.tolist() == [0, 0, 1, 1] and np.array_equal(centres, [[1, 0], [0, 1]])
+    with pytest.raises(ks.KSelectError):
+        ks.tree_regress(F, np.full((4, 2), np.nan, np.float32), 2)
+    with pytest.raises(ks.KSelectError):
+        ks.tree_regress(F, Y, 0)

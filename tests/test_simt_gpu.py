@@ -210,3 +210,89 @@ def test_gemm_host_round_trip(lib, torch):
         ref, den = og.gemm(shape.transA, shape.transB, shape.M, shape.N, shape.K, 1.0, A, B, beta,
                            np.where(np.isnan(C0), 0, C0))
         assert og.error_ratio(hC.numpy()[:, :, :shape.N], ref, den) <= TOL_F32
+
+
+# ---------------------------------------------------------------- split-K kind
+def split_ids(ks):
+    return [c for c in ks.config_ids(ks.PREC_F32) if c >= 2000]
+
+
+@pytest.mark.parametrize("ta,tb", TRANS)
+def test_split_kind_every_config(lib, torch, ta, tb):
+    """Every split-K config on a shape it does split (two batch entries of a single
+    tile, K = 1999 so the last split is ragged), alpha -0.5, beta 0.25, NaN padding
+    in A and B, and an odd ldc so the reduction takes its scalar stores."""
+    ks = lib
+    shape = wl.Shape(37, 45, 1999, 2, ta, tb)
+    A, B, C0 = wl.gemm_inputs(shape, seed=21, beta_nonzero=True, ld_multiple=8)
+    C0 = pad_c(C0, ldc_extra=3)[:, :, :51]  # ldc 51
+    ref, den = og.gemm(ta, tb, shape.M, shape.N, shape.K, -0.5, A, B, 0.25, C0[:, :, :shape.N])
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    bad = []
+    for cid in split_ids(ks):
+        S, kc = ks.split_factor(cid, shape.M, shape.N, shape.K, shape.batch)
+        assert S > 1 and (S - 1) * kc < shape.K <= S * kc, (cid, S, kc)
+        out = Out(torch, C0, 0.25, shape.N)
+        ks.gemm_with_config(cid, ta, tb, shape.M, shape.N, shape.K, -0.5, tA, A.shape[2], tB, B.shape[2], 0.25,
+                            out.ptr, C0.shape[2], shape.batch)
+        err = og.error_ratio(out.result(shape.N), ref, den)
+        if not err <= TOL_F32:
+            bad.append((cid, ks.config_params(cid), S, err))
+    assert not bad, bad[:10]
+
+
+def test_split_kind_integer_exact(lib, torch):
+    """Small integers: every partial sum and the split reduction are exact."""
+    ks = lib
+    shape = wl.Shape(70, 66, 1500, 3, "T", "N")
+    A, B, C0 = wl.gemm_inputs(shape, seed=22, kind="integer", bound=8, beta_nonzero=True)
+    ref, _ = og.gemm("T", "N", shape.M, shape.N, shape.K, 1.0, A, B, 1.0, C0)
+    for cid in split_ids(ks)[::7]:
+        assert ks.split_factor(cid, shape.M, shape.N, shape.K, shape.batch)[0] > 1
+        C = run_case(ks, torch, cid, shape, 1.0, 1.0, A, B, C0)
+        assert np.array_equal(C.astype(np.float64), ref), cid
+
+
+def test_split_kind_deterministic_and_graph_capturable(lib, torch):
+    """Two eager calls and a CUDA-graph replay give identical bits (the partials are
+    summed in split order); beta = 0 over NaN-filled C."""
+    ks = lib
+    cid = 2000 + find_cfg(ks, 8, 4, 16, 8, 32, 1)
+    shape = wl.Shape(300, 200, 3945, 8, "N", "T")
+    S, _ = ks.split_factor(cid, shape.M, shape.N, shape.K, shape.batch)
+    assert S > 1
+    A, B, C0 = wl.gemm_inputs(shape, seed=23)
+    ref, den = og.gemm("N", "T", shape.M, shape.N, shape.K, 1.5, A, B)
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    outs = []
+    for _ in range(2):
+        out = Out(torch, C0, 0.0, shape.N)
+        ks.gemm_with_config(cid, "N", "T", shape.M, shape.N, shape.K, 1.5, tA, A.shape[2], tB, B.shape[2], 0.0,
+                            out.ptr, C0.shape[2], shape.batch)
+        outs.append(out.result(shape.N))
+    assert og.error_ratio(outs[0], ref, den) <= TOL_F32
+    assert np.array_equal(outs[0], outs[1])
+    out = Out(torch, C0, 0.0, shape.N)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            ks.gemm_with_config(cid, "N", "T", shape.M, shape.N, shape.K, 1.5, tA, A.shape[2], tB, B.shape[2],
+                                0.0, out.ptr, C0.shape[2], shape.batch, side)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(out.result(shape.N), outs[0])
+
+
+def test_split_kind_unsplit_equals_base(lib, torch):
+    """Where the cost model keeps S = 1 the split-K id runs its base kernel unchanged."""
+    ks = lib
+    base = find_cfg(ks, 8, 4, 16, 8, 32, 1)
+    shape = wl.Shape(2048, 2048, 256, 1, "N", "N")
+    assert ks.split_factor(2000 + base, shape.M, shape.N, shape.K, shape.batch)[0] == 1
+    A, B, C0 = wl.gemm_inputs(shape, seed=24, beta_nonzero=True)
+    a = run_case(ks, torch, base, shape, 0.75, -0.5, A, B, C0)
+    b = run_case(ks, torch, 2000 + base, shape, 0.75, -0.5, A, B, C0)
+    assert np.array_equal(a, b)
+    assert ks.split_factor(base, 37, 45, 1999, 2) == (1, 1999)  # not of the split kind
