@@ -277,14 +277,15 @@ def gini_ordered(counts: np.ndarray, n) -> np.ndarray:
     return 1.0 - s
 
 
-def best_split(F: np.ndarray, y: np.ndarray, n_classes: int, min_leaf: int):
+def best_split(F: np.ndarray, y: np.ndarray, n_classes: int, min_leaf: int, features=None):
     """Lowest weighted child Gini, (n_L G_L + n_R G_R) / n, over every
     (feature, midpoint threshold) whose two sides each hold >= min_leaf
-    samples.  Features in column order, thresholds ascending; the first best
-    is kept.  Returns (feature, threshold, weighted impurity) or None."""
+    samples.  Features in column order (only those in ``features`` when given),
+    thresholds ascending; the first best is kept.  Returns (feature, threshold,
+    weighted impurity) or None."""
     n = len(y)
     best = None
-    for f in range(F.shape[1]):
+    for f in (range(F.shape[1]) if features is None else sorted(features)):
         order = np.argsort(F[:, f], kind="stable")
         xs = F[order, f]
         onehot = np.zeros((n, n_classes))
@@ -306,18 +307,32 @@ def best_split(F: np.ndarray, y: np.ndarray, n_classes: int, min_leaf: int):
     return best
 
 
+def feature_subset(draw_row: np.ndarray, n_features: int, m: int) -> list[int]:
+    """The m features a random-forest node may split on: the first m entries of a
+    partial Fisher-Yates shuffle of 0..n_features-1 in which step t swaps entry t
+    with entry t + draw_row[t] mod (n_features - t) (uint32 draws passed in)."""
+    order = list(range(n_features))
+    for t in range(m):
+        j = t + int(draw_row[t]) % (n_features - t)
+        order[t], order[j] = order[j], order[t]
+    return sorted(order[:m])
+
+
 def tree_train(F: np.ndarray, y: np.ndarray, n_classes: int, max_depth: int | None = None,
-               min_leaf: int = 1) -> list[dict]:
+               min_leaf: int = 1, max_features: int | None = None, draws: np.ndarray | None = None) -> list[dict]:
     """CART classification tree, nodes in depth-first preorder.
 
     A node is a leaf when it is pure, is at max_depth, or has no admissible
     split; otherwise it splits at ``best_split`` (x[feature] <= threshold goes
     left).  Leaf label: majority class, lowest class on ties.  Every node
-    records its majority label.
+    records its majority label.  With ``max_features`` < the feature count (a
+    random-forest tree), node j may only split on ``feature_subset(draws[j])``
+    and becomes a leaf when none of those features splits it.
     """
     F = np.asarray(F, np.float64)
     y = np.asarray(y, np.int64)
     nodes: list[dict] = []
+    subsample = max_features is not None and max_features < F.shape[1]
 
     def grow(idx, depth):
         counts = np.bincount(y[idx], minlength=n_classes)
@@ -327,7 +342,8 @@ def tree_train(F: np.ndarray, y: np.ndarray, n_classes: int, max_depth: int | No
         nodes.append(node)
         if counts.max() == len(idx) or (max_depth is not None and depth >= max_depth):
             return me
-        s = best_split(F[idx], y[idx], n_classes, min_leaf)
+        feats = feature_subset(draws[me], F.shape[1], max_features) if subsample else None
+        s = best_split(F[idx], y[idx], n_classes, min_leaf, feats)
         if s is None:
             return me
         f, t, _ = s

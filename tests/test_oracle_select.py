@@ -315,3 +315,31 @@ def test_cluster_geomean_centres():
     assert C[0] == pytest.approx([0.5, math.sqrt(0.5)], rel=1e-15)
     assert C[1] == pytest.approx([math.sqrt(0.5), math.sqrt(0.5e-6)], rel=1e-15)
     assert np.all(C[2] == 0)  # empty cluster
+
+
+# ---------------------------------------------------------------- random-forest trees (Section 5.1 classifiers)
+def test_feature_subset_by_hand():
+    # step 0 swaps entries 0 and 0 + 5 % 4 = 1 -> [1, 0, 2, 3]; step 1 swaps 1 and 1 + 7 % 3 = 2 -> [1, 2, 0, 3]
+    assert osel.feature_subset(np.array([5, 7, 0, 0]), 4, 2) == [1, 2]
+    assert osel.feature_subset(np.array([0, 0, 0, 0]), 4, 1) == [0]
+    assert osel.feature_subset(np.array([3, 9, 9, 9]), 4, 4) == [0, 1, 2, 3]
+
+
+def test_random_forest_tree_restricts_features():
+    rng = np.random.default_rng(12)
+    F = rng.permutation(4000)[:4 * 120].reshape(120, 4).astype(float)
+    y = (F[:, 0] > 2000).astype(int)  # only feature 0 separates the classes
+    full = osel.tree_train(F, y, 2)
+    assert full[0]["feature"] == 0 and len(full) == 3
+    # all features allowed: identical to the plain tree whatever the draws
+    draws = rng.integers(0, 2 ** 32, (4096, 4), dtype=np.uint64).astype(np.uint32)
+    assert osel.tree_train(F, y, 2, max_features=4, draws=draws) == full
+    # root limited to features {1, 2}: its split is the best one over those two alone
+    d = draws.copy()
+    d[0] = [5, 7, 0, 0]
+    nodes = osel.tree_train(F, y, 2, max_features=2, draws=d)
+    want = osel.best_split(F, y, 2, 1, features=[1, 2])
+    assert (nodes[0]["feature"], nodes[0]["threshold"]) == want[:2]
+    for j, nd in enumerate(nodes):
+        if nd["feature"] >= 0:
+            assert nd["feature"] in osel.feature_subset(d[j], 4, 2)
