@@ -196,6 +196,35 @@ gemm_status_t gemm_strided_batched_with_config(int32_t config_id, char transA, c
                                                float beta, float* C_dev, int64_t ldc, int64_t strideC, int64_t batch,
                                                void* stream);
 
+/* A sequence of gemm_host() problems as a three-stage pipeline: problem i's
+ * host-to-device copies run on a library-owned upload stream, its GEMM (the
+ * kernel select_kernel picks) on `stream` once they are done, and its C copy
+ * back on a library-owned download stream once the GEMM is done, so uploads,
+ * kernels and downloads of different problems overlap on the host link and
+ * the GPU.  The uploads start after the work already queued on `stream`, and
+ * `stream` ends waiting for the last download: synchronising `stream` covers
+ * the whole call.  Each problem's staging buffers (A_dev, B_dev, C_dev, sized
+ * as for gemm_host) must not overlap another problem's in the same call; host
+ * buffers should be pinned for the copies to be asynchronous.  Problems are
+ * validated before anything is enqueued (first error returned, nothing run). */
+typedef struct {
+  char transA, transB;
+  int64_t M, N, K, batch;
+  float alpha, beta;
+  const void* A_host;
+  int64_t lda;
+  const void* B_host;
+  int64_t ldb;
+  float* C_host;
+  int64_t ldc;
+  void* A_dev;
+  void* B_dev;
+  float* C_dev;
+} gemm_host_problem_t;
+
+gemm_status_t gemm_host_pipeline(gemm_handle_t handle, int32_t count, const gemm_host_problem_t* problems,
+                                 void* stream);
+
 /* The same operation with an explicit config id (any family). */
 gemm_status_t gemm_with_config(int32_t config_id, char transA, char transB, int64_t M, int64_t N,
                                int64_t K, float alpha, const void* A_dev, int64_t lda,
@@ -375,6 +404,17 @@ gemm_status_t kselect_knn(int32_t n_train, int32_t n_query, int32_t d, const flo
 gemm_status_t kselect_tree_regress(int32_t n, int32_t d, const double* features, const float* Y, int32_t max_leaves,
                                    int32_t* labels_out, float* centres_out, int32_t* n_leaves_out);
 
+/* Section 5.1 classifier comparison (host): one random-forest tree -- the CART
+ * of kselect_tree_train, except that node j (depth-first preorder) may split
+ * only on max_features of the 4 features: the first max_features entries of
+ * the permutation (0, 1, 2, 3) after partial Fisher-Yates steps t = 0, 1, ...
+ * that swap entry t with entry t + draws[4 j + t] mod (4 - t); it becomes a
+ * leaf when none of them splits it.  draws: 4 x max_nodes uint32 (host),
+ * ignored when max_features == 4. */
+gemm_status_t kselect_tree_train_rf(int32_t n, const double* features, const int32_t* labels, int32_t n_classes,
+                                    int32_t max_depth, int32_t min_leaf, int32_t max_features, const uint32_t* draws,
+                                    gemm_tree_node_t* out_nodes, int32_t max_nodes, int32_t* out_n_nodes);
+
 /* Section 5.1 (host): CART classification tree on features (n x 4 doubles:
  * M, N, K, batch) and labels (n, in [0, n_classes)).  Gini impurity with the
  * class sum in class order; thresholds at midpoints of consecutive distinct
@@ -509,6 +549,7 @@ gemm_status_t gemm_error_check(int64_t rows, int64_t cols, int64_t batch, const 
  * that device wind down early -- until read with clear != 0.  Synchronises
  * the device.  Returns GEMM_ERR_TIMEOUT when the word is nonzero. */
 gemm_status_t gemm_device_status(int32_t* out_status, int32_t clear);
+
 
 /* Fills a (batch, rows, ld) float array with uniform[lo, hi) values from a
  * counter-based hash of (seed, element index); padding columns get `pad`.

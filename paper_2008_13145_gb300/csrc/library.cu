@@ -601,6 +601,90 @@ gemm_status_t gemm_host(gemm_handle_t h, char transA, char transB, int64_t M, in
   return GEMM_OK;
 }
 
+// Library-owned copy streams per device for gemm_host_pipeline.
+static gemm_status_t copy_streams(cudaStream_t* up, cudaStream_t* down) {
+  static std::mutex mu;
+  static cudaStream_t ups[64] = {}, downs[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    set_last_cuda_error(e);
+    return GEMM_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ups[dev]) {
+    if ((e = cudaStreamCreateWithFlags(&ups[dev], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&downs[dev], cudaStreamNonBlocking)) != cudaSuccess) {
+      set_last_cuda_error(e);
+      return GEMM_ERR_CUDA;
+    }
+  }
+  *up = ups[dev];
+  *down = downs[dev];
+  return GEMM_OK;
+}
+
+gemm_status_t gemm_host_pipeline(gemm_handle_t h, int32_t count, const gemm_host_problem_t* probs, void* stream) {
+  if (!h || count < 0 || (count > 0 && !probs)) return GEMM_ERR_INVALID_ARG;
+  std::vector<GemmArgs> args(count);
+  std::vector<int32_t> ids(count);
+  std::vector<char> noop(count);
+  for (int i = 0; i < count; ++i) {
+    const gemm_host_problem_t& p = probs[i];
+    ids[i] = select_kernel(h, p.M, p.N, p.K, p.batch);
+    if (ids[i] < 0) return (gemm_status_t)ids[i];
+    bool nop = false;
+    gemm_status_t st = make_args(p.transA, p.transB, p.M, p.N, p.K, p.alpha, p.A_dev, p.lda, p.B_dev, p.ldb, p.beta,
+                                 p.C_dev, p.ldc, p.batch, elem_bytes_of(ids[i]), &args[i], &nop);
+    if (st != GEMM_OK) return st;
+    noop[i] = nop;
+    if (!nop && ((p.K > 0 && (!p.A_host || !p.B_host)) || !p.C_host)) return GEMM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream), up = nullptr, down = nullptr;
+  gemm_status_t st = copy_streams(&up, &down);
+  if (st != GEMM_OK) return st;
+  // Two events per problem (uploads done, GEMM done) plus the start and end markers.
+  std::vector<cudaEvent_t> ev(2 * (size_t)count + 2, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);  // uploads follow the work already on `stream`
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(up, ev[0], 0);
+  for (int i = 0; i < count && e == cudaSuccess && st == GEMM_OK; ++i) {
+    if (noop[i]) continue;
+    const gemm_host_problem_t& p = probs[i];
+    const GemmArgs& a = args[i];
+    const size_t elem = (size_t)elem_bytes_of(ids[i]);
+    if (p.K > 0) {
+      e = cudaMemcpyAsync(p.A_dev, p.A_host, (size_t)a.strideA * p.batch * elem, cudaMemcpyHostToDevice, up);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p.B_dev, p.B_host, (size_t)a.strideB * p.batch * elem, cudaMemcpyHostToDevice, up);
+    }
+    const size_t bytesC = (size_t)a.strideC * p.batch * sizeof(float);
+    if (e == cudaSuccess && p.beta != 0.f) e = cudaMemcpyAsync(p.C_dev, p.C_host, bytesC, cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * i], up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + 2 * i], 0);
+    if (e != cudaSuccess) break;
+    st = launch_config(ids[i], a, s);
+    if (st != GEMM_OK) break;
+    e = cudaEventRecord(ev[2 + 2 * i], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(down, ev[2 + 2 * i], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.C_host, p.C_dev, bytesC, cudaMemcpyDeviceToHost, down);
+  }
+  // `stream` ends after the last download (also on an error, so nothing is left pending).
+  cudaError_t e2 = cudaEventRecord(ev.back(), down);
+  if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev.back(), 0);
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  if (e == cudaSuccess) e = e2;
+  if (st != GEMM_OK) return st;
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e);
+    return GEMM_ERR_CUDA;
+  }
+  return GEMM_OK;
+}
+
 gemm_status_t gemm_benchmark(int32_t id, char transA, char transB, int64_t M, int64_t N, int64_t K,
                              const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                              int64_t batch, int32_t warmup, int32_t min_reps, int32_t max_reps,

@@ -335,6 +335,8 @@ struct TreeBuilder {
   int n_classes, max_depth, min_leaf, max_nodes;
   std::vector<gemm_tree_node_t> nodes;
   bool overflow = false;
+  int max_features = 4;             // < 4: random-forest node feature subsets
+  const uint32_t* draws = nullptr;  // 4 per node, in node (preorder) order
 
   // 1 - sum_c (cnt_c / n)^2, summed in class order.
   double gini(const std::vector<double>& cnt, double n) const {
@@ -360,12 +362,25 @@ struct TreeBuilder {
     nodes.push_back(gemm_tree_node_t{-1, -1, -1, label, 0.0});
     const int n = (int)idx.size();
     if (counts[label] == n || (max_depth >= 0 && depth >= max_depth)) return me;
+    // Features this node may split on: all, or the first max_features entries of a
+    // partial Fisher-Yates shuffle driven by the node's draws, taken in order.
+    bool allowed[4] = {true, true, true, true};
+    if (max_features < 4) {
+      int perm[4] = {0, 1, 2, 3};
+      for (int t = 0; t < max_features; ++t) {
+        const int j = t + (int)(draws[4 * (size_t)me + t] % (uint32_t)(4 - t));
+        std::swap(perm[t], perm[j]);
+      }
+      for (int f = 0; f < 4; ++f) allowed[f] = false;
+      for (int t = 0; t < max_features; ++t) allowed[perm[t]] = true;
+    }
     // Best split: features in order, thresholds ascending, first best kept.
     int bf = -1;
     double bt = 0.0, bw = 0.0;
     std::vector<int> order(idx);
     std::vector<double> cl(n_classes), cr(n_classes);
     for (int f = 0; f < 4; ++f) {
+      if (!allowed[f]) continue;
       std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return F[4 * a + f] < F[4 * b + f]; });
       std::fill(cl.begin(), cl.end(), 0.0);
       for (int c = 0; c < n_classes; ++c) cr[c] = counts[c];
@@ -642,6 +657,29 @@ gemm_status_t kselect_top_n(int32_t n_rows, int32_t n_cols, const float* perf, i
     if (cnt == n) break;
     if (!used[c]) out_cols[cnt++] = c;
   }
+  return GEMM_OK;
+}
+
+// Section 5.1 classifier comparison: one random-forest tree (CART restricted to
+// per-node feature subsets drawn from `draws`, 4 uint32 per node).
+gemm_status_t kselect_tree_train_rf(int32_t n, const double* features, const int32_t* labels, int32_t n_classes,
+                                    int32_t max_depth, int32_t min_leaf, int32_t max_features, const uint32_t* draws,
+                                    gemm_tree_node_t* out_nodes, int32_t max_nodes, int32_t* out_n_nodes) {
+  if (n < 1 || !features || !labels || n_classes < 1 || min_leaf < 1 || !out_nodes || max_nodes < 1 ||
+      !out_n_nodes || max_features < 1 || max_features > 4 || (max_features < 4 && !draws))
+    return GEMM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (labels[i] < 0 || labels[i] >= n_classes) return GEMM_ERR_INVALID_ARG;
+    for (int f = 0; f < 4; ++f)
+      if (!std::isfinite(features[4 * i + f])) return GEMM_ERR_INVALID_ARG;
+  }
+  TreeBuilder tb{features, labels, n_classes, max_depth, min_leaf, max_nodes, {}, false, max_features, draws};
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  tb.grow(idx, 0);
+  if (tb.overflow) return GEMM_ERR_UNSUPPORTED;
+  std::memcpy(out_nodes, tb.nodes.data(), tb.nodes.size() * sizeof(gemm_tree_node_t));
+  *out_n_nodes = (int32_t)tb.nodes.size();
   return GEMM_OK;
 }
 

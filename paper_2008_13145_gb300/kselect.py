@@ -39,6 +39,12 @@ class Problem(ctypes.Structure):
                 ("A", vp), ("lda", i64), ("B", vp), ("ldb", i64), ("C", vp), ("ldc", i64)]
 
 
+class HostProblem(ctypes.Structure):
+    _fields_ = [("transA", ctypes.c_char), ("transB", ctypes.c_char), ("M", i64), ("N", i64), ("K", i64),
+                ("batch", i64), ("alpha", f32), ("beta", f32), ("A_host", vp), ("lda", i64), ("B_host", vp),
+                ("ldb", i64), ("C_host", vp), ("ldc", i64), ("A_dev", vp), ("B_dev", vp), ("C_dev", vp)]
+
+
 class Deployment(ctypes.Structure):
     _fields_ = [("precision", i32), ("n_configs", i32), ("config_ids", ctypes.POINTER(i32)),
                 ("n_nodes", i32), ("nodes", ctypes.POINTER(TreeNode)), ("mlp_params", ctypes.POINTER(f32)),
@@ -69,6 +75,7 @@ _STRIDED_ARGS = [ch, ch, i64, i64, i64, f32, vp, i64, i64, vp, i64, i64, f32, vp
 _sig("gemm_strided_batched", i32, [vp] + _STRIDED_ARGS)
 _sig("gemm_strided_batched_with_config", i32, [i32] + _STRIDED_ARGS)
 _sig("gemm_host", i32, [vp, ch, ch, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i64, vp, vp, vp, vp])
+_sig("gemm_host_pipeline", i32, [vp, i32, ctypes.POINTER(HostProblem), vp])
 _sig("gemm_benchmark", i32, [i32, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64, i64, i32, i32, i32, f64,
                              ctypes.POINTER(f64), vp])
 _sig("gemm_error_check", i32, [i64, i64, i64, vp, i64, i64, i64, vp, vp, vp, ctypes.POINTER(f64), vp])
@@ -106,6 +113,8 @@ _sig("kselect_spectral_embedding", i32, [i32, i32, vp, f32, i32, i32, i32, vp, v
 _sig("kselect_cluster_geomean", i32, [i32, i32, vp, vp, i32, f32, vp, vp])
 _sig("kselect_tree_regress", i32, [i32, i32, ctypes.POINTER(f64), ctypes.POINTER(f32), i32, ctypes.POINTER(i32),
                                    ctypes.POINTER(f32), ctypes.POINTER(i32)])
+_sig("kselect_tree_train_rf", i32, [i32, ctypes.POINTER(f64), ctypes.POINTER(i32), i32, i32, i32, i32,
+                                    ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(TreeNode), i32, ctypes.POINTER(i32)])
 _sig("kselect_tree_train", i32, [i32, ctypes.POINTER(f64), ctypes.POINTER(i32), i32, i32, i32,
                                  ctypes.POINTER(TreeNode), i32, ctypes.POINTER(i32)])
 
@@ -257,6 +266,27 @@ def gemm_with_config(cid: int, transA: str, transB: str, M, N, K, alpha, A, lda,
                      stream=None) -> None:
     check(_lib.gemm_with_config(cid, _c(transA), _c(transB), M, N, K, alpha, ptr(A), lda, ptr(B), ldb, beta,
                                 ptr(C), ldc, batch, stream_handle(stream)), "gemm_with_config")
+
+
+def host_problems(problems: list[dict]):
+    """ctypes array of gemm_host_problem_t from dicts with the gemm_host arguments
+    (transA, transB, M, N, K, batch, alpha, beta, A_host, lda, B_host, ldb, C_host,
+    ldc, A_dev, B_dev, C_dev); keep the result alive while the call is queued."""
+    arr = (HostProblem * len(problems))()
+    for q, p in zip(arr, problems):
+        q.transA, q.transB = _c(p["transA"]), _c(p["transB"])
+        q.M, q.N, q.K, q.batch = p["M"], p["N"], p["K"], p.get("batch", 1)
+        q.alpha, q.beta = p.get("alpha", 1.0), p.get("beta", 0.0)
+        q.A_host, q.lda, q.B_host, q.ldb = ptr(p["A_host"]), p["lda"], ptr(p["B_host"]), p["ldb"]
+        q.C_host, q.ldc = ptr(p["C_host"]), p["ldc"]
+        q.A_dev, q.B_dev, q.C_dev = ptr(p["A_dev"]), ptr(p["B_dev"]), ptr(p["C_dev"])
+    return arr
+
+
+def gemm_host_pipeline(handle: Handle, problems, stream=None) -> None:
+    """problems: a list of dicts (see host_problems) or its ctypes array."""
+    arr = problems if isinstance(problems, ctypes.Array) else host_problems(problems)
+    check(_lib.gemm_host_pipeline(handle.value, len(arr), arr, stream_handle(stream)), "gemm_host_pipeline")
 
 
 def gemm_strided_batched(h, transA: str, transB: str, M, N, K, alpha, A, lda, strideA, B, ldb, strideB, beta, C,
@@ -466,6 +496,23 @@ def tree_train(features: np.ndarray, labels: np.ndarray, n_classes: int, max_dep
              "right": nodes[j].right, "label": nodes[j].label} for j in range(cnt.value)]
 
 
+def tree_train_rf(features: np.ndarray, labels: np.ndarray, n_classes: int, max_features: int, draws: np.ndarray,
+                  max_depth=None, min_leaf=1, max_nodes=8192) -> list[dict]:
+    """One random-forest tree; draws: (>= max_nodes, 4) uint32, row j for node j."""
+    F, pF = _arr(features, np.float64, f64)
+    assert F.ndim == 2 and F.shape[1] == 4
+    y, py = _arr(labels, np.int32, i32)
+    d = np.ascontiguousarray(draws, np.uint32)
+    assert d.ndim == 2 and d.shape[1] == 4 and d.shape[0] >= max_nodes
+    nodes = (TreeNode * max_nodes)()
+    cnt = i32()
+    check(_lib.kselect_tree_train_rf(F.shape[0], pF, py, n_classes, -1 if max_depth is None else max_depth, min_leaf,
+                                     max_features, d.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), nodes,
+                                     max_nodes, ctypes.byref(cnt)), "kselect_tree_train_rf")
+    return [{"feature": nodes[j].feature, "threshold": nodes[j].threshold, "left": nodes[j].left,
+             "right": nodes[j].right, "label": nodes[j].label} for j in range(cnt.value)]
+
+
 # ---------------------------------------------------------------- grouped GEMM
 def _problems(problems):
     """problems: iterable of dicts with M, N, K, transA, transB, alpha, beta, A, lda, B, ldb, C, ldc."""
@@ -548,8 +595,8 @@ def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points this binding expects."""
     return ["gemm_status_string", "gemm_last_cuda_error", "gemm_config_count", "gemm_config_id",
             "gemm_config_params", "gemm_split_choose", "gemm_split_factor", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
-            "gemm_with_config", "gemm_strided_batched", "gemm_strided_batched_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
+            "gemm_with_config", "gemm_host_pipeline", "gemm_strided_batched", "gemm_strided_batched_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
             "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
-            "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_im2col3x3_nchw", "kselect_bias_act_nchw", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_regress", "kselect_tree_train", "kselect_spectral_embedding", "kselect_cluster_geomean", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
+            "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_im2col3x3_nchw", "kselect_bias_act_nchw", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_regress", "kselect_tree_train", "kselect_tree_train_rf", "kselect_spectral_embedding", "kselect_cluster_geomean", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
             "gemm_grouped_plan_destroy", "gemm_grouped"]

@@ -415,7 +415,8 @@ def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, spl
     the held-out geometric-mean fraction of the per-shape optimum reached by:
     decision trees A/B/C, 1/3/7 nearest neighbours on the performance model's
     features, bagged trees (n_bag bootstrap trees of type A, majority vote, from
-    seeded draws) and, for k <= 8, the MLP performance model."""
+    seeded draws), a random forest (the same bootstraps, each node limited to 2
+    of the 4 features) and, for k <= 8, the MLP performance model."""
     import torch
     ks = _ks()
     shapes, perf, ids, prec = load_table(table_path)
@@ -426,6 +427,7 @@ def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, spl
     F_tr, F_te = features(s_tr), features(s_te)
     rng = wl.rng_for(seed, 61)
     boot = rng.integers(0, len(tr), (n_bag, len(tr)))
+    rf_draws = wl.rng_for(seed, 81).integers(0, 2 ** 32, (n_bag, 8192, 4), dtype=np.uint64).astype(np.uint32)
     out = {"k": list(k_values), "deployed_max": [], "classifiers": {}}
 
     def add(name, cols_chosen):
@@ -450,10 +452,14 @@ def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, spl
             ks.knn(X_tr, yd, X_te, nn, pred)
             add(f"{nn}NearestNeighbor", [cols[j] for j in pred.cpu().numpy()])
         votes = np.zeros((len(te), k), np.int64)
+        rf_votes = np.zeros((len(te), k), np.int64)
         for b in range(n_bag):
             nodes = ks.tree_train(F_tr[boot[b]], y[boot[b]], k, None, 1)
             votes[np.arange(len(te)), tree_predict(nodes, F_te)] += 1
+            rf = ks.tree_train_rf(F_tr[boot[b]], y[boot[b]], k, 2, rf_draws[b], None, 1)
+            rf_votes[np.arange(len(te)), tree_predict(rf, F_te)] += 1
         add("BaggedTrees", [cols[j] for j in np.argmax(votes, axis=1)])
+        add("RandomForest", [cols[j] for j in np.argmax(rf_votes, axis=1)])
         if k <= 8:
             T, M = mlp_targets(np.pad(perf[tr][:, cols], ((0, 0), (0, 8 - k))))
             params, _ = mlp_train_params(X_tr, T, M, steps=mlp_steps, seed=seed)

@@ -201,3 +201,13 @@ def test_argument_validation_needs_no_device(ks):
     assert strided(16, 16, 15) == -1  # batch entries would overlap in C
     assert strided(0, 0, 0, batch=1, cid=5000) == -6
     assert strided(0, 16, 16, batch=0) == 0  # empty: no-op
+
+    # the host pipeline validates every problem before it enqueues anything
+    h = ks.Handle({"precision": 0, "config_ids": [369], "nodes": []})
+    good = dict(transA="N", transB="N", M=4, N=4, K=4, lda=4, ldb=4, ldc=4, A_host=fake, B_host=fake, C_host=fake,
+                A_dev=fake, B_dev=fake, C_dev=fake)
+    for bad in (dict(lda=3), dict(transA="Q"), dict(C_host=0), dict(M=-1), dict(C_dev=0)):
+        arr = ks.host_problems([good, {**good, **bad}])
+        assert ks._lib.gemm_host_pipeline(h.value, 2, arr, None) == -1, bad
+    assert ks._lib.gemm_host_pipeline(h.value, -1, None, None) == -1
+    assert ks._lib.gemm_host_pipeline(None, 0, None, None) == -1

@@ -130,3 +130,23 @@ def test_tree_regress_constant_leaves_stop(ks):
         ks.tree_regress(F, np.full((4, 2), np.nan, np.float32), 2)
     with pytest.raises(ks.KSelectError):
         ks.tree_regress(F, Y, 0)
+
+
+# ---------------------------------------------------------------- random-forest trees (Section 5.1 classifiers)
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("m", [1, 2, 3, 4])
+def test_random_forest_tree_matches_oracle(ks, seed, m):
+    """Node for node, with bootstrap-like repeated rows and the same per-node draws."""
+    from paper_2008_13145_gb300 import workloads as wl
+    rng = np.random.default_rng(200 + seed)
+    shapes = wl.shape_grid(400, 10 + seed)
+    F = np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
+    y = (np.log(F[:, 0]) + np.log(F[:, 1]) > 12).astype(np.int32) + (F[:, 3] > 4).astype(np.int32)
+    boot = rng.integers(0, 400, 400)
+    draws = rng.integers(0, 2 ** 32, (8192, 4), dtype=np.uint64).astype(np.uint32)
+    for depth, leaf in ((None, 1), (6, 3)):
+        got = ks.tree_train_rf(F[boot], y[boot], 3, m, draws, depth, leaf)
+        want = osel.tree_train(F[boot], y[boot], 3, depth, leaf, max_features=m, draws=draws)
+        same_tree(got, want)
+        if m == 4:
+            same_tree(got, ks.tree_train(F[boot], y[boot], 3, depth, leaf))

@@ -296,3 +296,45 @@ def test_split_kind_unsplit_equals_base(lib, torch):
     b = run_case(ks, torch, 2000 + base, shape, 0.75, -0.5, A, B, C0)
     assert np.array_equal(a, b)
     assert ks.split_factor(base, 37, 45, 1999, 2) == (1, 1999)  # not of the split kind
+
+
+def test_host_pipeline(lib, torch):
+    """gemm_host_pipeline: uploads, selected GEMMs and downloads of 14 problems on
+    three streams; every C lands in pinned host memory as the oracle has it
+    (beta != 0 problems upload C first; K = 0 scales C; an empty problem is skipped)."""
+    import json
+    import os
+    ks = lib
+    dep = json.load(open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                      "paper_2008_13145_gb300", "deploy", "f32.json")))
+    h = ks.Handle(dep)
+    rng = np.random.default_rng(31)
+    cases, keep = [], []
+    for n in range(14):
+        M, N, K = (int(x) for x in rng.integers(1, 700, 3))
+        if n == 5:
+            K = 0
+        if n == 9:
+            M = 0
+        sh = wl.Shape(M, N, K, int(rng.choice([1, 2, 4])), "NT"[n % 2], "NT"[(n // 2) % 2])
+        beta = 0.0 if n % 3 == 0 else 0.5
+        A, B, C0 = wl.gemm_inputs(sh, seed=300 + n, beta_nonzero=beta != 0)
+        hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+        hC = torch.from_numpy(C0.copy() if beta != 0 else np.zeros_like(C0)).pin_memory()
+        dA, dB = torch.empty(max(A.size, 1), device="cuda"), torch.empty(max(B.size, 1), device="cuda")
+        dC = torch.empty(max(C0.size, 1), device="cuda")
+        keep.append((hA, hB, hC, dA, dB, dC))
+        cases.append((sh, beta, A, B, C0, hC, dict(transA=sh.transA, transB=sh.transB, M=sh.M, N=sh.N, K=sh.K,
+                                                   batch=sh.batch, alpha=1.25, beta=beta, A_host=hA.data_ptr(),
+                                                   lda=A.shape[2], B_host=hB.data_ptr(), ldb=B.shape[2],
+                                                   C_host=hC.data_ptr(), ldc=C0.shape[2], A_dev=dA, B_dev=dB,
+                                                   C_dev=dC)))
+    s = torch.cuda.Stream()
+    ks.gemm_host_pipeline(h, [c[-1] for c in cases], s)
+    s.synchronize()
+    for sh, beta, A, B, C0, hC, _ in cases:
+        got = hC.numpy()[:, :, :sh.N]
+        if sh.M == 0:
+            continue
+        ref, den = og.gemm(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.25, A, B, beta, C0 if beta != 0 else None)
+        assert og.error_ratio(got, ref, den) <= TOL_F32, sh
