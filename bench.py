@@ -265,6 +265,32 @@ def run_ours(args, ws, rank, local):
     dom_flops = by_cfg[dom][1] / by_cfg[dom][2]
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
 
+    # The same deployed kernels chosen by the other selectors (untimed choice,
+    # timed steps): the random forest of deploy/f32_forest.json and the MLP
+    # performance model served by the batched selection kernel.
+    selectors = {"decision_tree_b": {"value": value, "live_geomean": live["geomean"]}}
+    alt = {}
+    forest_path = os.path.join(DEPLOY, "f32_forest.json")
+    if os.path.exists(forest_path):
+        fdep = json.load(open(forest_path))
+        if fdep["config_ids"] == dep["config_ids"]:
+            hf = ks.Handle(fdep)
+            alt["random_forest"] = [ks.select_kernel(hf, sh.M, sh.N, sh.K, sh.batch) for sh in shapes]
+    if dep.get("mlp_params"):
+        alt["mlp"] = [int(c) for c in tune.mlp_choose(np.asarray(dep["mlp_params"], np.float32), shapes,
+                                                      dep["config_ids"])]
+    for name, cfgs in alt.items():
+        per_launch_ms(cfgs)
+        r = np.minimum(exh_ms / per_launch_ms(cfgs), 1.0)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(10):
+            step(None, cfgs)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        selectors[name] = {"value": job_throughput(ws, flops, 10, max_over_ranks(e0.elapsed_time(e1))),
+                           "live_geomean": float(np.exp(np.mean(np.log(r))))}
+
     # End to end from pinned host buffers through gemm_host_pipeline.
     hosts = []
     h2d = d2h = 0
@@ -323,6 +349,7 @@ def run_ours(args, ws, rank, local):
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel_config": dom,
                      "kernel_params": ks.config_params(dom), "share_of_step": dom_share},
         "e2e": {"value": e2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "selectors": selectors,
         "tc": tc,
         "grouped": grouped,
         "vgg16": vgg16,

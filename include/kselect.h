@@ -122,7 +122,8 @@ int32_t gemm_split_factor(int32_t config_id, int64_t M, int64_t N, int64_t K, in
  * Optional MLP parameters (GEMM_MLP_PARAMS floats, layout W1 7x64, b1, W2
  * 64x64, b2, W3 64x8, b3) let select_kernels_batched rank the deployed set. */
 #define GEMM_MAX_DEPLOYED 16
-#define GEMM_MAX_TREE_NODES 8192
+#define GEMM_MAX_TREE_NODES 65536
+#define GEMM_MAX_TREES 256
 #define GEMM_MLP_PARAMS 5192
 
 typedef struct {
@@ -145,6 +146,12 @@ typedef struct {
   int32_t n_known;              /* benchmarked sizes with their measured best kernel, or 0 */
   const int64_t* known_sizes;   /* host, n_known rows of (M, N, K, batch) */
   const int32_t* known_ids;     /* host, n_known config ids (any config of an allowed family) */
+  int32_t n_trees;              /* 0 or 1: one tree rooted at node 0; 2..GEMM_MAX_TREES: a forest */
+  const int32_t* tree_roots;    /* host, n_trees root indices into `nodes` (forest only); the
+                                   trees share the node array but no node; every tree votes
+                                   for one deployed config and the most-voted wins, the
+                                   lowest label on ties (the random-forest classifier of
+                                   Tables 1-2 as a runtime selector) */
 } gemm_deployment_t;
 
 /* Copies the deployment into a new immutable handle (host only; device
@@ -550,6 +557,13 @@ gemm_status_t gemm_error_check(int64_t rows, int64_t cols, int64_t batch, const 
  * the device.  Returns GEMM_ERR_TIMEOUT when the word is nonzero. */
 gemm_status_t gemm_device_status(int32_t* out_status, int32_t clear);
 
+/* Test hook for the failure path above (no paper counterpart): one warp runs the
+ * tensor-core kernels' bounded mbarrier wait, with a limit of limit_ns
+ * (1 .. 2e9), on a barrier that nothing arrives at.  The wait gives up, sets the
+ * status word to 1 as a stalled TMA slice would, and the kernel returns;
+ * *waited_out = 0 (1 would mean the barrier completed).  The context stays
+ * usable.  Synchronises `stream`. */
+gemm_status_t kselect_wait_selftest(int64_t limit_ns, int32_t* waited_out, void* stream);
 
 /* Fills a (batch, rows, ld) float array with uniform[lo, hi) values from a
  * counter-based hash of (seed, element index); padding columns get `pad`.

@@ -79,6 +79,7 @@ struct kselect_library {
   int precision;
   std::vector<int32_t> ids;
   std::vector<gemm_tree_node_t> nodes;
+  std::vector<int32_t> roots;  // forest: one root per tree; empty: one tree rooted at 0
   std::vector<float> mlp;  // empty when absent
   std::vector<std::array<int64_t, 4>> known;  // sorted benchmarked sizes
   std::vector<int32_t> known_ids;

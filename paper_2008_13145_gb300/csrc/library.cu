@@ -406,11 +406,17 @@ gemm_status_t gemm_library_create(const gemm_deployment_t* d, gemm_handle_t* out
   for (int i = 0; i < d->n_configs; ++i)
     if (family_of(d->config_ids[i]) < 0 || !family_allowed(d->precision, family_of(d->config_ids[i])))
       return GEMM_ERR_NO_KERNEL;
-  // Tree: children in range, every node reached at most once from the root
-  // (so no cycles and no sharing), leaf labels inside the deployed set.
+  // Trees: children in range, every node reached at most once from the roots
+  // (so no cycles and no sharing, also between the trees of a forest), leaf
+  // labels inside the deployed set.
+  const bool forest = d->n_trees > 1;
+  if (d->n_trees < 0 || d->n_trees > GEMM_MAX_TREES || (forest && (!d->tree_roots || d->n_nodes < 1)))
+    return GEMM_ERR_INVALID_ARG;
   if (d->n_nodes > 0) {
     std::vector<char> seen(d->n_nodes, 0);
-    std::vector<int> stack{0};
+    std::vector<int> stack;
+    if (forest) stack.assign(d->tree_roots, d->tree_roots + d->n_trees);
+    else stack.push_back(0);
     while (!stack.empty()) {
       int j = stack.back();
       stack.pop_back();
@@ -448,6 +454,7 @@ gemm_status_t gemm_library_create(const gemm_deployment_t* d, gemm_handle_t* out
   h->precision = d->precision;
   h->ids.assign(d->config_ids, d->config_ids + d->n_configs);
   if (d->n_nodes > 0) h->nodes.assign(d->nodes, d->nodes + d->n_nodes);
+  if (forest) h->roots.assign(d->tree_roots, d->tree_roots + d->n_trees);
   if (d->mlp_params) h->mlp.assign(d->mlp_params, d->mlp_params + GEMM_MLP_PARAMS);
   *out = h;
   return GEMM_OK;
@@ -467,13 +474,28 @@ int32_t select_kernel(gemm_handle_t h, int64_t M, int64_t N, int64_t K, int64_t 
   }
   if (h->nodes.empty()) return h->ids[0];
   const double f[4] = {(double)M, (double)N, (double)K, (double)batch};
-  int j = 0;
-  for (int steps = 0; steps <= (int)h->nodes.size(); ++steps) {
-    const gemm_tree_node_t& nd = h->nodes[j];
-    if (nd.feature < 0) return h->ids[nd.label];
-    j = (f[nd.feature] <= nd.threshold) ? nd.left : nd.right;
+  auto walk = [&](int j) -> int {  // leaf label of the tree rooted at j
+    for (int steps = 0; steps <= (int)h->nodes.size(); ++steps) {
+      const gemm_tree_node_t& nd = h->nodes[j];
+      if (nd.feature < 0) return nd.label;
+      j = (f[nd.feature] <= nd.threshold) ? nd.left : nd.right;
+    }
+    return -1;  // unreachable for a validated tree
+  };
+  if (h->roots.empty()) {
+    const int label = walk(0);
+    return label < 0 ? GEMM_ERR_INVALID_ARG : h->ids[label];
   }
-  return GEMM_ERR_INVALID_ARG;  // unreachable for a validated tree
+  int votes[GEMM_MAX_DEPLOYED] = {0};
+  for (int32_t r : h->roots) {
+    const int label = walk(r);
+    if (label < 0) return GEMM_ERR_INVALID_ARG;
+    ++votes[label];
+  }
+  int best = 0;
+  for (int c = 1; c < (int)h->ids.size(); ++c)
+    if (votes[c] > votes[best]) best = c;
+  return h->ids[best];
 }
 
 // gemm_with_config with explicit batch strides (elements).  A and B strides may

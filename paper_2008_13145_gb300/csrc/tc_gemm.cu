@@ -368,6 +368,22 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
 
 }  // namespace ks
 
+namespace ks {
+// One warp waits, with the kernels' bounded wait and the given limit, on an
+// mbarrier that nothing ever arrives at: the wait gives up, records the
+// "slice never landed" code in the status word and the kernel returns.
+__global__ void wait_selftest_kernel(int* status, uint64_t limit_ns, int* waited) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  const bool ok = tc::mbar_wait_for(&bar, 0, status, tc::kStatusTimeoutFull, limit_ns);
+  if (threadIdx.x == 0) *waited = ok ? 1 : 0;
+}
+}  // namespace ks
+
 // ------------------------------------------------------------------ grouped plans
 struct kselect_grouped_plan {
   ks::TcConfig cfg;
@@ -525,6 +541,25 @@ gemm_status_t gemm_grouped(int32_t id, int32_t count, const gemm_problem_t* prob
   plan_free(p);
   if (st == GEMM_OK && e != cudaSuccess) st = fail(e);
   return st;
+}
+
+gemm_status_t kselect_wait_selftest(int64_t limit_ns, int32_t* waited_out, void* stream) {
+  if (!waited_out || limit_ns < 1 || limit_ns > (int64_t)ks::tc::kWaitLimitNs) return GEMM_ERR_INVALID_ARG;
+  int* w = status_word();
+  if (!w) return fail(cudaGetLastError());
+  int* flag = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&flag), sizeof(int), s);
+  if (e != cudaSuccess) return fail(e);
+  ks::wait_selftest_kernel<<<1, 32, 0, s>>>(w, (uint64_t)limit_ns, flag);
+  int v = -1;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(flag, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e);
+  *waited_out = v;
+  return GEMM_OK;
 }
 
 gemm_status_t gemm_device_status(int32_t* out_status, int32_t clear) {

@@ -68,19 +68,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity to complete.  On timeout
-// writes `code` to *status (first error wins) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int code) {
+// (limit_ns of polling) writes `code` to *status (first error wins) and
+// returns false; also returns false once another role has recorded an error.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, int* status, int code,
+                                              uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > kWaitLimitNs) {
+    if (globaltimer() - t0 > limit_ns) {
       if (status) atomicCAS(status, 0, code);
       return false;
     }
     if (status && *(volatile int*)status != 0) return false;  // another role gave up
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, int code) {
+  return mbar_wait_for(bar, parity, status, code, kWaitLimitNs);
 }
 
 // ------------------------------------------------------------------ TMA

@@ -48,7 +48,8 @@ class HostProblem(ctypes.Structure):
 class Deployment(ctypes.Structure):
     _fields_ = [("precision", i32), ("n_configs", i32), ("config_ids", ctypes.POINTER(i32)),
                 ("n_nodes", i32), ("nodes", ctypes.POINTER(TreeNode)), ("mlp_params", ctypes.POINTER(f32)),
-                ("n_known", i32), ("known_sizes", ctypes.POINTER(i64)), ("known_ids", ctypes.POINTER(i32))]
+                ("n_known", i32), ("known_sizes", ctypes.POINTER(i64)), ("known_ids", ctypes.POINTER(i32)),
+                ("n_trees", i32), ("tree_roots", ctypes.POINTER(i32))]
 
 
 def _sig(name, res, args):
@@ -81,6 +82,7 @@ _sig("gemm_benchmark", i32, [i32, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i
 _sig("gemm_error_check", i32, [i64, i64, i64, vp, i64, i64, i64, vp, vp, vp, ctypes.POINTER(f64), vp])
 _sig("kselect_fill_uniform", i32, [vp, i64, i64, i64, i64, u64, f32, f32, f32, vp])
 _sig("gemm_device_status", i32, [ctypes.POINTER(i32), i32])
+_sig("kselect_wait_selftest", i32, [i64, ctypes.POINTER(i32), vp])
 _sig("gemm_grouped_plan_create", i32, [i32, i32, ctypes.POINTER(Problem), vp, ctypes.POINTER(vp)])
 _sig("gemm_grouped_run", i32, [vp, vp])
 _sig("gemm_grouped_plan_destroy", None, [vp])
@@ -206,11 +208,23 @@ class Handle:
     """An immutable library handle built from a deployment dict:
     {"precision": int, "config_ids": [...], "nodes": [{"feature", "threshold",
     "left", "right", "label"}, ...], "mlp_params": [5192 floats] | None,
-    "known": [[M, N, K, batch, config id], ...] | None}."""
+    "known": [[M, N, K, batch, config id], ...] | None,
+    "forest": [[nodes of tree 0], [nodes of tree 1], ...] | None}.
+    With "forest", its trees (each with node indices local to itself) replace
+    "nodes" and vote."""
 
     def __init__(self, deployment: dict):
         ids = list(deployment["config_ids"])
         nodes = deployment.get("nodes") or []
+        roots = []
+        if deployment.get("forest"):
+            nodes = []
+            for tree in deployment["forest"]:
+                base = len(nodes)
+                roots.append(base)
+                nodes += [{**n, "left": n["left"] + base if n["feature"] >= 0 else -1,
+                           "right": n["right"] + base if n["feature"] >= 0 else -1} for n in tree]
+        self._roots = (i32 * max(len(roots), 1))(*roots)
         mlp = deployment.get("mlp_params")
         self._ids = (i32 * max(len(ids), 1))(*ids)
         self._nodes = (TreeNode * max(len(nodes), 1))(
@@ -221,7 +235,8 @@ class Handle:
         self._ksz = (i64 * max(4 * len(known), 1))(*[int(v) for r in known for v in r[:4]])
         self._kid = (i32 * max(len(known), 1))(*[int(r[4]) for r in known])
         d = Deployment(int(deployment["precision"]), len(ids), self._ids, len(nodes), self._nodes,
-                       self._mlp if self._mlp is not None else None, len(known), self._ksz, self._kid)
+                       self._mlp if self._mlp is not None else None, len(known), self._ksz, self._kid,
+                       len(roots), self._roots)
         h = vp()
         check(_lib.gemm_library_create(ctypes.byref(d), ctypes.byref(h)), "gemm_library_create")
         self.value = h.value
@@ -327,6 +342,13 @@ def error_check(C, Cref, den, rows=0, cols=0, batch=0, ldc=0, strideC=0, pos=Non
     check(_lib.gemm_error_check(rows, cols, batch, ptr(C), ldc, strideC, n, ptr(pos), ptr(Cref), ptr(den),
                                 ctypes.byref(out), stream_handle(stream)), "gemm_error_check")
     return out.value
+
+
+def wait_selftest(limit_ns: int, stream=None) -> int:
+    """Runs the bounded-wait test hook; returns 1 if the never-arriving barrier completed, else 0."""
+    w = i32()
+    check(_lib.kselect_wait_selftest(limit_ns, ctypes.byref(w), stream_handle(stream)), "kselect_wait_selftest")
+    return w.value
 
 
 def device_status(clear: bool = True) -> int:
@@ -596,7 +618,7 @@ def exported_symbols() -> list[str]:
     return ["gemm_status_string", "gemm_last_cuda_error", "gemm_config_count", "gemm_config_id",
             "gemm_config_params", "gemm_split_choose", "gemm_split_factor", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
             "gemm_with_config", "gemm_host_pipeline", "gemm_strided_batched", "gemm_strided_batched_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
-            "gemm_benchmark_configs", "gemm_device_status", "kselect_normalise", "kselect_kmeans", "kselect_score",
+            "gemm_benchmark_configs", "gemm_device_status", "kselect_wait_selftest", "kselect_normalise", "kselect_kmeans", "kselect_score",
             "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_im2col3x3_nchw", "kselect_bias_act_nchw", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_regress", "kselect_tree_train", "kselect_tree_train_rf", "kselect_spectral_embedding", "kselect_cluster_geomean", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
             "gemm_grouped_plan_destroy", "gemm_grouped"]

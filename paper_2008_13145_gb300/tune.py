@@ -272,6 +272,38 @@ def evaluate(perf_test: np.ndarray, shapes_test, deployment: dict, all_ids: list
             "chosen_cols": chosen.tolist()}
 
 
+def train_forest(perf_train: np.ndarray, shapes_train, cols: list[int], n_trees: int = 16, max_features: int = 2,
+                 seed: int = 0) -> list[list[dict]]:
+    """Random-forest selector (Tables 1-2's RandomForest as a runtime classifier):
+    n_trees type-A trees, each on a bootstrap of the training sizes with
+    max_features of the 4 size features per node, all draws seeded inputs."""
+    ks = _ks()
+    y = np.argmax(perf_train[:, cols], axis=1).astype(np.int32)
+    F = features(shapes_train)
+    rng = wl.rng_for(seed, 91)
+    boot = rng.integers(0, len(y), (n_trees, len(y)))
+    draws = rng.integers(0, 2 ** 32, (n_trees, 8192, 4), dtype=np.uint64).astype(np.uint32)
+    return [ks.tree_train_rf(F[boot[b]], y[boot[b]], len(cols), max_features, draws[b], None, 1)
+            for b in range(n_trees)]
+
+
+def forest_deploy(deploy_path: str, table_path: str, n_trees: int = 16, seed: int = 0, split_seed: int = 1) -> dict:
+    """The deployment at deploy_path (same deployed kernels, known table and MLP)
+    with a random forest trained on the same training sizes as its selector."""
+    shapes, perf, ids, _ = load_table(table_path)
+    dep = json.load(open(deploy_path))
+    tr, te = wl.train_test_split(len(shapes), split_seed)
+    col_of = {cid: j for j, cid in enumerate(ids)}
+    cols = [col_of[c] for c in dep["config_ids"]]
+    out = {k: v for k, v in dep.items() if k != "meta"}
+    out["forest"] = train_forest(perf[tr], [shapes[i] for i in tr], cols, n_trees, seed=seed)
+    ev = evaluate(perf[te], [shapes[i] for i in te], {k: v for k, v in out.items() if k != "known"}, ids)
+    out["meta"] = {**dep.get("meta", {}), "selector": f"random forest, {n_trees} trees, 2 of 4 features per node",
+                   "forest_seed": seed,
+                   "scores": {key: v for key, v in ev.items() if key != "chosen_cols"}}
+    return out
+
+
 def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard", split_seed: int = 1,
            method: str = "kmeans") -> dict:
     shapes, perf, ids, precision = load_table(table_path)
@@ -613,6 +645,11 @@ def main(argv=None):
     vg.add_argument("--sweep", required=True)
     vg.add_argument("--out", required=True)
     vg.add_argument("--layout", default="nhwc", choices=["nhwc", "batched"])
+    fo = sub.add_parser("forest")
+    fo.add_argument("--deploy", required=True)
+    fo.add_argument("--table", required=True)
+    fo.add_argument("--trees", type=int, default=16)
+    fo.add_argument("--out", required=True)
     nw = sub.add_parser("network")
     nw.add_argument("--net", required=True, choices=sorted(wl.NETWORKS))
     nw.add_argument("--deploy", required=True)
@@ -648,6 +685,12 @@ def main(argv=None):
         with open(a.out, "w") as f:
             json.dump(r, f, indent=1)
         print(json.dumps({k: {"config": v["config"], "tflops": v["tflops"]} for k, v in r.items()}, indent=1))
+        return
+    if a.cmd == "forest":
+        r = forest_deploy(a.deploy, a.table, a.trees)
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps(r["meta"]["scores"], indent=1))
         return
     if a.cmd == "network":
         r = network_study(a.net, a.deploy, a.sweep)

@@ -150,3 +150,54 @@ def test_random_forest_tree_matches_oracle(ks, seed, m):
         same_tree(got, want)
         if m == 4:
             same_tree(got, ks.tree_train(F[boot], y[boot], 3, depth, leaf))
+
+
+def test_forest_selector_votes_like_the_oracle(ks):
+    """A deployment with a forest: select_kernel is the majority vote of the trees
+    (lowest label on ties), each tree walked as the oracle walks it."""
+    from paper_2008_13145_gb300 import workloads as wl
+    rng = np.random.default_rng(77)
+    shapes = wl.shape_grid(300, 21)
+    F = np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
+    y = ((np.log(F[:, 0]) > 6).astype(np.int32) + (np.log(F[:, 2]) > 6.5) * 2 + (F[:, 3] > 4)) % 4
+    y = y.astype(np.int32)
+    trees = []
+    for b in range(9):
+        boot = rng.integers(0, 300, 300)
+        draws = rng.integers(0, 2 ** 32, (8192, 4), dtype=np.uint64).astype(np.uint32)
+        trees.append(ks.tree_train_rf(F[boot], y[boot], 4, 2, draws))
+    ids = [11, 22, 33, 44]
+    h = ks.Handle({"precision": 0, "config_ids": ids, "nodes": [], "forest": trees})
+    Q = np.array([[s.M, s.N, s.K, s.batch] for s in wl.shape_grid(500, 22)], np.float64)
+    votes = np.zeros((len(Q), 4), np.int64)
+    for t in trees:
+        votes[np.arange(len(Q)), osel.tree_predict(t, Q)] += 1
+    want = [ids[int(np.argmax(v))] for v in votes]  # argmax: lowest label among the tied maxima
+    got = [ks.select_kernel(h, *map(int, q)) for q in Q]
+    assert got == want
+
+
+def test_forest_deployment_validation(ks):
+    leaf = lambda c: {"feature": -1, "threshold": 0.0, "left": -1, "right": -1, "label": c}
+    split = {"feature": 0, "threshold": 100.0, "left": 1, "right": 2, "label": 0}
+    ok = {"precision": 0, "config_ids": [5, 7]}
+    h = ks.Handle({**ok, "forest": [[split, leaf(0), leaf(1)], [leaf(1)], [leaf(1)]]})
+    assert ks.select_kernel(h, 50, 1, 1, 1) == 7 and ks.select_kernel(h, 500, 1, 1, 1) == 7
+    h = ks.Handle({**ok, "forest": [[split, leaf(0), leaf(1)], [leaf(0)]]})
+    assert ks.select_kernel(h, 50, 1, 1, 1) == 5  # 2 votes for label 0
+    assert ks.select_kernel(h, 500, 1, 1, 1) == 5  # a 1-1 tie goes to the lower label
+    with pytest.raises(ks.KSelectError):  # a leaf label outside the deployed set
+        ks.Handle({**ok, "forest": [[leaf(0)], [leaf(2)]]})
+    # raw ABI: two trees sharing a node, and a root out of range
+    nodes = (ks.TreeNode * 3)(ks.TreeNode(0, 1, 2, 0, 100.0), ks.TreeNode(-1, -1, -1, 0, 0.0),
+                              ks.TreeNode(-1, -1, -1, 1, 0.0))
+    ids = (ks.i32 * 2)(5, 7)
+    for roots in ([0, 1], [0, 3], [0, -1]):
+        r = (ks.i32 * 2)(*roots)
+        d = ks.Deployment(0, 2, ids, 3, nodes, None, 0, None, None, 2, r)
+        hv = ks.vp()
+        assert ks._lib.gemm_library_create(ks.ctypes.byref(d), ks.ctypes.byref(hv)) == -1, roots
+    r = (ks.i32 * 300)(*([0] * 300))
+    d = ks.Deployment(0, 2, ids, 3, nodes, None, 0, None, None, 300, r)
+    hv = ks.vp()
+    assert ks._lib.gemm_library_create(ks.ctypes.byref(d), ks.ctypes.byref(hv)) == -1

@@ -168,3 +168,23 @@ def test_mixed_family_deployment_through_gemm(lib, torch):
         ref, den = og.gemm(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, B, nthreads=og.max_threads())
         assert og.error_ratio(out.result(sh.N), ref, den) <= 1e-5, (sh, ks.select_kernel(h, sh.M, sh.N, sh.K, sh.batch))
     assert fams == {0, 3}, fams
+
+
+def test_bounded_wait_gives_up_and_context_survives(lib, torch):
+    """The failure path: a bounded mbarrier wait on a barrier that nothing arrives
+    at gives up after its limit (1 ms here), records code 1 in the status word,
+    the host reads it as GEMM_ERR_TIMEOUT and clears it, and tensor-core GEMMs
+    on the same context are correct afterwards."""
+    import time
+    ks = lib
+    assert ks.device_status() == 0
+    t0 = time.perf_counter()
+    assert ks.wait_selftest(1_000_000) == 0
+    assert time.perf_counter() - t0 < 5.0
+    st = ks.i32()
+    assert ks._lib.gemm_device_status(ks.ctypes.byref(st), 0) == -5 and st.value == 1  # GEMM_ERR_TIMEOUT, kept
+    assert ks.device_status(clear=True) == 1
+    assert ks.device_status() == 0
+    C, ref, den = run(ks, torch, tc_ids(ks, "bf16")[8], "bf16", wl.Shape(128, 128, 128, 1, "N", "T"), 1.0, 0.0, seed=1)
+    assert og.error_ratio(C, ref, den) <= FAMILIES["bf16"][1]
+    assert ks.device_status() == 0
