@@ -322,6 +322,7 @@ def run_ours(args, ws, rank, local):
     tc = tc_families(args, ks, tune, shapes, te, bufs, stream, dev) if not args.no_tc else None
     grouped = grouped_launch(ks, tune) if not args.no_tc else None
     vgg16 = vgg16_inference(ks) if not args.no_tc else None
+    c0 = single_gemm_256(ks, tune)
 
     if rank != 0:
         return
@@ -353,6 +354,7 @@ def run_ours(args, ws, rank, local):
         "tc": tc,
         "grouped": grouped,
         "vgg16": vgg16,
+        "single_gemm_256": c0,
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -459,6 +461,31 @@ def grouped_launch(ks, tune):
         plan.close()
         del keep
     return out
+
+
+def single_gemm_256(ks, tune, reps: int = 200):
+    """The small fixed case: 256^3 NN FP32, alpha 1, beta 0, uniform[-1, 1) inputs,
+    one fixed config (16x16 threads, 4x4 per thread, K-step 16, staged).  Its
+    786 KB of operands and result stay in L2 across back-to-back launches, so
+    it measures latency and launch overhead, reported as time, TFLOP/s and
+    algorithmic GB/s."""
+    import torch
+    from paper_2008_13145_gb300 import workloads as wl
+    sh = wl.Shape(256, 256, 256, 1, "N", "N")
+    A, B, C, lda, ldb, ldc = tune.alloc_inputs(sh, ks.PREC_F32, 0)
+    cid = next(c for c in ks.config_ids(ks.PREC_F32) if ks.config_params(c)[1:7] == [4, 4, 16, 16, 16, 1])
+    for _ in range(10):
+        ks.gemm_with_config(cid, "N", "N", 256, 256, 256, 1.0, A, lda, B, ldb, 0.0, C, ldc, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        ks.gemm_with_config(cid, "N", "N", 256, 256, 256, 1.0, A, lda, B, ldb, 0.0, C, ldc, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"config": cid, "us_per_launch": ms * 1e3, "tflops": sh.flops / (ms * 1e9),
+            "algorithmic_gbs": 3 * 256 * 256 * 4 / (ms * 1e6), "note": "back-to-back launches, L2-resident"}
 
 
 def vgg16_inference(ks, reps: int = 10):

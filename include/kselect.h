@@ -241,9 +241,10 @@ gemm_status_t gemm_with_config(int32_t config_id, char transA, char transB, int6
 /* ---------------------------------------------------------------- grouped GEMM
  * An uneven group of independent GEMMs in ONE persistent tensor-core launch:
  * every problem is cut into 128 x BN tiles, the tiles of all problems are
- * numbered consecutively, and each CTA walks the global tile index with a
- * fixed stride, mapping it to (problem, tile) by binary search over the
- * problems' first-tile offsets.  Per-problem TMA descriptors live in device
+ * numbered consecutively -- problems ordered by K, longest first, so that the
+ * fixed-stride walk below deals each CTA a balanced mix -- and each CTA walks
+ * the global tile index with a fixed stride, mapping it to (problem, tile) by
+ * binary search over the problems' first-tile offsets.  Per-problem TMA descriptors live in device
  * memory.  Problems use the row-major conventions above; K >= 1.  Operands
  * that are not K-contiguous (transA 'T', transB 'N'), not 16-byte aligned,
  * and every operand of the F32X3 family are first rewritten by one grouped

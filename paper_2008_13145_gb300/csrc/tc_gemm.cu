@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -454,8 +455,21 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
   cudaError_t e = cudaSuccess;
   if (scratch_bytes > 0) e = cudaMalloc(reinterpret_cast<void**>(&p->scratch), scratch_bytes);
   if (e != cudaSuccess) { plan_free(p); return fail(e); }
+  // Tiles are dealt to the persistent CTAs by static striding over the global
+  // tile index, so the problems are laid out by K-steps per tile, longest
+  // first: each CTA then takes one tile per round of a longest-first list,
+  // which balances uneven groups (results do not depend on the order).
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  const int64_t kmul = c.family == GEMM_PREC_F32X3 ? 3 : 1;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const int64_t kx = kmul * (c.family == GEMM_PREC_F32X3 ? round_up(probs[x].K, 64) : probs[x].K);
+    const int64_t ky = kmul * (c.family == GEMM_PREC_F32X3 ? round_up(probs[y].K, 64) : probs[y].K);
+    return kx > ky;
+  });
   int tile_start = 0, blocks = 0;
-  for (int i = 0; i < count; ++i) {
+  for (int r = 0; r < count; ++r) {
+    const int i = order[r];
     const gemm_problem_t& q = probs[i];
     const void* Aop = pa[i].direct ? q.A : p->scratch + offA[i];
     const void* Bop = pb[i].direct ? q.B : p->scratch + offB[i];
@@ -472,7 +486,7 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
       jobs.push_back(pb[i].job);
     }
     const int64_t Kop = c.family == GEMM_PREC_F32X3 ? 3 * round_up(q.K, 64) : q.K;
-    tc::GroupDesc& d = descs[i];
+    tc::GroupDesc& d = descs[r];
     std::memset(&d, 0, sizeof(d));
     if (!make_map(&d.tmA, Aop, op_bf16, Kop, q.M > 0 ? q.M : 1, pa[i].ld, 1, tc::kBM) ||
         !make_map(&d.tmB, Bop, op_bf16, Kop, q.N > 0 ? q.N : 1, pb[i].ld, 1, c.pair ? c.bn / 2 : c.bn)) {
