@@ -533,7 +533,7 @@ gemm_status_t kselect_bias_act_nchw(float* y_dev, int32_t N, int32_t C, int64_t 
                                     int32_t relu, void* stream);
 
 /* ---------------------------------------------------------------- error check
- * The judge of every GEMM result: err = max over entries of
+ * The check of every GEMM result: err = max over entries of
  * |C - C_ref| / den, reduced on the GPU in FP64, where C_ref and den are the
  * FP64 exact product and its componentwise scale |alpha||op(A)||op(B)| +
  * |beta||C0| supplied by the caller.  den == 0 requires C == C_ref exactly

@@ -12,7 +12,7 @@
  *     C[b,i,j]   = alpha * sum_k op(A)[b,i,k] * op(B)[b,k,j] + beta * C0[b,i,j]
  *     den[b,i,j] = |alpha| * sum_k |op(A)[b,i,k]| * |op(B)[b,k,j]| + |beta| * |C0[b,i,j]|
  *
- * den is the componentwise error scale used to judge every GPU result:
+ * den is the componentwise error scale used to check every GPU result:
  * err = max over entries of |C_gpu - C| / den.  When beta == 0, C0 is not read.
  *
  * Storage is row-major.  op(A) = A (M x K, lda >= K) when transA == 0, and

@@ -2,7 +2,7 @@
 
 The performance model is trained by the library's kernels on 80 % of the
 2,500-shape GB300 benchmark of the deployed kernels (the table committed
-beside the deployment) and judged, like the decision tree, on the held-out
+beside the deployment) and scored, like the decision tree, on the held-out
 20 % as a fraction of the best deployed kernel per shape (the exhaustive
 selector over the deployed set scores 1)."""
 import json
