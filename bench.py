@@ -147,6 +147,32 @@ def cpu_oracle_sample(shapes, budget_s: float, nthreads: int):
                                    f"({flops / 1e9:.1f} GFLOP in {t_used:.1f} s, {nthreads} threads)")
 
 
+def cpu_details(nthreads: int) -> dict:
+    """The FP64 oracle on the small fixed case (256^3 NN, one thread and all
+    threads) and on every VGG16 GEMM at batch 1 (all threads): GFLOP/s."""
+    from oracle import gemm as og
+    og.build()
+    out = {}
+    sh = wl.Shape(256, 256, 256, 1, "N", "N")
+    A, B, _ = wl.gemm_inputs(sh, seed=0)
+    for name, nt in (("single_gemm_256_1_thread", 1), (f"single_gemm_256_{nthreads}_threads", nthreads)):
+        t0 = time.perf_counter()
+        og.gemm("N", "N", 256, 256, 256, 1.0, A, B, nthreads=nt)
+        out[name] = sh.flops / (time.perf_counter() - t0) / 1e9
+    layers, total_f, total_t = {}, 0, 0.0
+    for n, (name, sh) in enumerate(wl.vgg16_layers(1)):
+        A, B, _ = wl.gemm_inputs(sh, seed=10 + n)
+        t0 = time.perf_counter()
+        og.gemm(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, A, B, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        layers[name] = sh.flops / dt / 1e9
+        total_f, total_t = total_f + sh.flops, total_t + dt
+    out["vgg16_batch1_layers"] = layers
+    out["vgg16_batch1_total"] = {"gflops": total_f / total_t / 1e9, "seconds": total_t, "threads": nthreads}
+    out["unit"] = "GFLOP/s"
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -330,7 +356,8 @@ def run_ours(args, ws, rank, local):
     if ws == 1 and not args.no_cpu:
         from oracle import gemm as og
         v, desc = cpu_oracle_sample(shapes, args.ref_budget, og.max_threads())
-        cpu = {"value": v, "unit": "TFLOP/s", "cores": og.max_threads(), "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": og.max_threads(), "kind": "oracle", "sample": desc,
+               "details": cpu_details(og.max_threads())}
     clocks = clk.summary()
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
@@ -484,8 +511,22 @@ def single_gemm_256(ks, tune, reps: int = 200):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    return {"config": cid, "us_per_launch": ms * 1e3, "tflops": sh.flops / (ms * 1e9),
-            "algorithmic_gbs": 3 * 256 * 256 * 4 / (ms * 1e6), "note": "back-to-back launches, L2-resident"}
+    out = {"config": cid, "us_per_launch": ms * 1e3, "tflops": sh.flops / (ms * 1e9),
+           "algorithmic_gbs": 3 * 256 * 256 * 4 / (ms * 1e6), "note": "back-to-back launches, L2-resident"}
+    # the same product with the kernel the FP32 deployment selects
+    h = ks.Handle(json.load(open(os.path.join(DEPLOY, "f32.json"))))
+    for _ in range(10):
+        ks.gemm(h, "N", "N", 256, 256, 256, 1.0, A, lda, B, ldb, 0.0, C, ldc, 1)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        ks.gemm(h, "N", "N", 256, 256, 256, 1.0, A, lda, B, ldb, 0.0, C, ldc, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    out["selected"] = {"config": ks.select_kernel(h, 256, 256, 256, 1), "us_per_launch": ms * 1e3,
+                       "tflops": sh.flops / (ms * 1e9)}
+    return out
 
 
 def vgg16_inference(ks, reps: int = 10):
