@@ -26,6 +26,7 @@
 
 namespace ks {
 namespace {
+constexpr int kRasterGroup = 8;
 
 constexpr int kTcBn[3] = {64, 128, 256};
 constexpr int kTcStages[3] = {2, 3, 4};
@@ -355,7 +356,10 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
     a.tiles_n = (g.N + c.bn - 1) / c.bn;
     a.num_tiles = a.tiles_m * a.tiles_n * g.batch;
     a.k_blocks = (int)((Kop + (op_bf16 ? 63 : 31)) / (op_bf16 ? 64 : 32));
-    a.raster = 0;
+    // Grouped raster: 8 tile rows (units) per group bound the operand slices the
+    // SMs' tiles in flight read at once (8 A + ~10 B slices for 152 CTAs).
+    a.raster = 2;
+    a.group_m = std::max(1, std::min(a.tiles_m, kRasterGroup));
     a.alpha = g.alpha; a.beta = g.beta;
     a.C = g.C; a.ldc = g.ldc; a.strideC = g.strideC; a.vecC = g.vecC;
     a.status = status;

@@ -24,7 +24,9 @@ namespace tc {
 struct TcArgs {
   int M, N, K, batch;
   int tiles_m, tiles_n, num_tiles, k_blocks;
-  int raster;  // 0: consecutive tiles walk M (reuse the B slice), 1: walk N
+  int raster;   // 0: consecutive tiles walk M (reuse the B slice), 1: walk N,
+                // 2: groups of group_m tile rows, each walked along N (L2 locality)
+  int group_m;  // raster 2: tile rows (units) per group, >= 1
   float alpha, beta;
   float* C;
   int64_t ldc, strideC;
@@ -67,7 +69,18 @@ __device__ __forceinline__ void tile_coords(const TcArgs& p, int tile, int& b, i
   const int per = p.tiles_m * p.tiles_n;
   b = tile / per;
   const int t = tile - b * per;
-  if (p.raster == 0) {
+  if (p.raster == 2) {
+    // Tile rows in groups of group_m (the last group may be shorter); inside a
+    // group the index runs down the group's rows first, then along N, so the
+    // tiles in flight at once share a few A and B slices that stay in L2.
+    const int per_group = p.group_m * p.tiles_n;
+    const int g = t / per_group;
+    const int first = g * p.group_m;
+    const int rows = min(p.group_m, p.tiles_m - first);
+    const int r = t - g * per_group;
+    tm = first + r % rows;
+    tn = r / rows;
+  } else if (p.raster == 0) {
     tm = t % p.tiles_m;
     tn = t / p.tiles_m;
   } else {
