@@ -472,19 +472,25 @@ def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
 
 def grouped_launch(ks, tune):
     """The 256-problem uneven group in one persistent launch per family, with
-    the tile configuration the grouped autotuner picked, replayed from a CUDA graph."""
+    the tile configuration the group classifier picks for it (gemm_grouped_select
+    on the family's deployed selector; the autotuner's fastest config for this
+    group when no selector is deployed), replayed from a CUDA graph."""
     gpath = os.path.join(DEPLOY, "grouped.json")
     if not os.path.exists(gpath):
         return None
     g = json.load(open(gpath))
     out = {}
     for name, r in g.items():
-        fam = ks.family_of(r["config"])
+        fam = ks.PRECISIONS[name]
         probs, keep, flops = tune.grouped_workload(fam)
-        plan = ks.GroupedPlan(r["config"], probs)
+        cid = ks.grouped_select(ks.Handle(r["selector"]), probs) if r.get("selector") else r["config"]
+        plan = ks.GroupedPlan(cid, probs)
         ms = tune.time_grouped_graph(plan, reps=20, warmup=3)
-        out[name] = {"value": flops / (ms * 1e9), "unit": "TFLOP/s", "ms_per_launch": ms, "config": r["config"],
-                     "problems": len(probs), "gflop": flops / 1e9}
+        out[name] = {"value": flops / (ms * 1e9), "unit": "TFLOP/s", "ms_per_launch": ms, "config": cid,
+                     "problems": len(probs), "gflop": flops / 1e9,
+                     "selector": "group tree" if r.get("selector") else "fastest on this group"}
+        if r.get("selector_scores"):
+            out[name]["selector_held_out_geomean"] = r["selector_scores"]["tree"]["geomean"]
         plan.close()
         del keep
     return out

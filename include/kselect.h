@@ -274,6 +274,15 @@ gemm_status_t gemm_grouped_plan_create(int32_t config_id, int32_t count, const g
 gemm_status_t gemm_grouped_run(gemm_grouped_plan_t plan, void* stream);
 void gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
 
+/* Tile-shape selection for a group (the benchmark / prune / classify loop run
+ * on groups instead of single GEMMs): the handle's deployment is a set of
+ * grouped-launch configs with a tree (or forest) over the group features
+ * (median M, median N, median K, number of problems) -- the lower median of
+ * each -- in place of (M, N, K, batch).  Returns the config id, or a negative
+ * gemm_status_t (INVALID_ARG for a NULL handle or problems, count < 1, or a
+ * negative size). */
+int32_t gemm_grouped_select(gemm_handle_t handle, int32_t count, const gemm_problem_t* problems);
+
 /* One-shot form: plan, run, synchronise `stream`, release the plan. */
 gemm_status_t gemm_grouped(int32_t config_id, int32_t count, const gemm_problem_t* problems, void* stream);
 

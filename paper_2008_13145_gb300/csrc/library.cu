@@ -498,6 +498,24 @@ int32_t select_kernel(gemm_handle_t h, int64_t M, int64_t N, int64_t K, int64_t 
   return h->ids[best];
 }
 
+// The grouped launch's tile shape by the same classifier: a deployment whose
+// trees read (median M, median N, median K, problem count) of the group.
+int32_t gemm_grouped_select(gemm_handle_t h, int32_t count, const gemm_problem_t* problems) {
+  if (!h || count < 1 || !problems) return GEMM_ERR_INVALID_ARG;
+  std::vector<int64_t> m(count), n(count), k(count);
+  for (int i = 0; i < count; ++i) {
+    if (problems[i].M < 0 || problems[i].N < 0 || problems[i].K < 0) return GEMM_ERR_INVALID_ARG;
+    m[i] = problems[i].M;
+    n[i] = problems[i].N;
+    k[i] = problems[i].K;
+  }
+  const int mid = (count - 1) / 2;  // lower median
+  std::nth_element(m.begin(), m.begin() + mid, m.end());
+  std::nth_element(n.begin(), n.begin() + mid, n.end());
+  std::nth_element(k.begin(), k.begin() + mid, k.end());
+  return select_kernel(h, m[mid], n[mid], k[mid], count);
+}
+
 // gemm_with_config with explicit batch strides (elements).  A and B strides may
 // be anything >= 0 (0 reuses one matrix for every batch entry); C's must keep
 // the batch entries' outputs apart.

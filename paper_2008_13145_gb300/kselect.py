@@ -87,6 +87,7 @@ _sig("gemm_grouped_plan_create", i32, [i32, i32, ctypes.POINTER(Problem), vp, ct
 _sig("gemm_grouped_run", i32, [vp, vp])
 _sig("gemm_grouped_plan_destroy", None, [vp])
 _sig("gemm_grouped", i32, [i32, i32, ctypes.POINTER(Problem), vp])
+_sig("gemm_grouped_select", i32, [vp, i32, ctypes.POINTER(Problem)])
 _sig("mlp_features", i32, [i32, vp, vp, vp])
 _sig("mlp_forward", i32, [i32, vp, vp, vp, vp])
 _sig("mlp_loss_grad", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
@@ -536,6 +537,15 @@ def tree_train_rf(features: np.ndarray, labels: np.ndarray, n_classes: int, max_
 
 
 # ---------------------------------------------------------------- grouped GEMM
+def grouped_select(handle: Handle, problems) -> int:
+    """Config id the handle's group classifier picks for these problems (dicts as for GroupedPlan)."""
+    arr = _problems(problems)
+    r = _lib.gemm_grouped_select(handle.value, len(problems), arr)
+    if r < 0:
+        raise KSelectError(r, "gemm_grouped_select")
+    return r
+
+
 def _problems(problems):
     """problems: iterable of dicts with M, N, K, transA, transB, alpha, beta, A, lda, B, ldb, C, ldc."""
     arr = (Problem * len(problems))()
@@ -621,4 +631,4 @@ def exported_symbols() -> list[str]:
             "gemm_benchmark_configs", "gemm_device_status", "kselect_wait_selftest", "kselect_normalise", "kselect_kmeans", "kselect_score",
             "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_im2col3x3_nchw", "kselect_bias_act_nchw", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_regress", "kselect_tree_train", "kselect_tree_train_rf", "kselect_spectral_embedding", "kselect_cluster_geomean", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
-            "gemm_grouped_plan_destroy", "gemm_grouped"]
+            "gemm_grouped_plan_destroy", "gemm_grouped", "gemm_grouped_select"]

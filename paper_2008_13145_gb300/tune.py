@@ -503,10 +503,10 @@ def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, spl
 
 
 # ---------------------------------------------------------------- grouped launch (autotuned tile shape)
-def grouped_workload(family: int, n: int = 256, seed: int = 3, data_seed: int = 500):
-    """Device buffers of the uneven group (M, N, K log-uniform in [32, 4096]), K-contiguous operands."""
+def grouped_workload(family: int, n: int = 256, seed: int = 3, data_seed: int = 500, lo: int = 32, hi: int = 4096):
+    """Device buffers of an uneven group (M, N, K log-uniform in [lo, hi]), K-contiguous operands."""
     probs, keep = [], []
-    for i, sh in enumerate(wl.grouped_problems(n, seed)):
+    for i, sh in enumerate(wl.grouped_problems(n, seed, lo, hi)):
         A, B, C, lda, ldb, ldc = alloc_inputs(sh, family, data_seed + i)
         keep.append((A, B, C))
         probs.append(dict(M=sh.M, N=sh.N, K=sh.K, transA="N", transB="T", A=A, lda=lda, B=B, ldb=ldb, C=C, ldc=ldc))
@@ -553,6 +553,111 @@ def grouped_tune(families=("tf32", "bf16", "f32x3")) -> dict:
         best = max(res, key=lambda r: r["tflops"])
         out[name] = {"config": best["config"], "tflops": best["tflops"], "gflop": flops / 1e9, "all": res}
         del keep
+    return out
+
+
+# ---------------------------------------------------------------- grouped tile-shape selector
+GROUP_COUNTS = (16, 32, 64, 128, 256)
+GROUP_RANGES = ((32, 512), (64, 1024), (128, 2048), (32, 4096), (256, 4096))
+
+
+def group_specs(n_groups: int = 100, seed: int = 11) -> list[tuple[int, int, int, int]]:
+    """Seeded groups (problem count, lo, hi, problem seed): the count and the
+    log-uniform size range of each group drawn from the sets above."""
+    rng = wl.rng_for(seed, 101)
+    return [(int(GROUP_COUNTS[rng.integers(len(GROUP_COUNTS))]), *GROUP_RANGES[rng.integers(len(GROUP_RANGES))],
+             1000 + g) for g in range(n_groups)]
+
+
+def group_features(problems) -> list[int]:
+    """(median M, median N, median K, count), lower medians, as gemm_grouped_select reads them."""
+    c = len(problems)
+    med = lambda v: sorted(v)[(c - 1) // 2]
+    return [med([q["M"] for q in problems]), med([q["N"] for q in problems]), med([q["K"] for q in problems]), c]
+
+
+def grouped_sweep(family: str, specs, out_path: str, reps: int = 5, log=sys.stderr) -> tuple[np.ndarray, np.ndarray]:
+    """The benchmark step on groups: every tile config of the family timed on
+    every group (CUDA-graph replay of one grouped launch).  Resumable JSONL.
+    Returns (TFLOP/s n_groups x configs, features n_groups x 4)."""
+    ks = _ks()
+    fam = ks.PRECISIONS[family]
+    ids = ks.config_ids(fam)
+    done = {}
+    if os.path.exists(out_path):
+        for line in open(out_path):
+            if line.strip():
+                r = json.loads(line)
+                done[r["g"]] = r
+    t0 = time.time()
+    with open(out_path, "a") as f:
+        for g, (count, lo, hi, seed) in enumerate(specs):
+            if g in done:
+                continue
+            probs, keep, flops = grouped_workload(fam, count, seed, 700 + g, lo, hi)
+            tf = []
+            for cid in ids:
+                plan = ks.GroupedPlan(cid, probs)
+                tf.append(flops / (time_grouped_graph(plan, reps=reps) * 1e9))
+                plan.close()
+            rec = {"g": g, "spec": [count, lo, hi, seed], "features": group_features(probs), "config_ids": ids,
+                   "tflops": tf}
+            f.write(json.dumps(rec) + "\n")
+            f.flush()
+            done[g] = rec
+            del keep
+            if log and (g % 20 == 0 or g == len(specs) - 1):
+                log.write(f"[grouped sweep {family}] {g + 1}/{len(specs)}  {time.time() - t0:.0f}s\n")
+                log.flush()
+    recs = [done[g] for g in range(len(specs))]
+    return np.array([r["tflops"] for r in recs]), np.array([r["features"] for r in recs], np.float64)
+
+
+def grouped_study(family: str, sweep_path: str, n_groups: int = 100, k: int = 4, tree: str = "B", seed: int = 0,
+                  split_seed: int = 1) -> dict:
+    """Benchmark, prune and classify on groups: the grouped sweep, k-means over
+    the standard-normalised per-group vectors, a tree on the group features;
+    held-out groups scored against the per-group best tile config."""
+    import torch
+    ks = _ks()
+    specs = group_specs(n_groups)
+    perf, F = grouped_sweep(family, specs, sweep_path)
+    ids = ks.config_ids(ks.PRECISIONS[family])
+    tr, te = wl.train_test_split(n_groups, split_seed)
+    pr = prune(perf[tr], k, seed)
+    y = np.argmax(perf[tr][:, pr["cols"]], axis=1).astype(np.int32)
+    depth, leaf = TREES[tree]
+    nodes = ks.tree_train(F[tr], y, len(pr["cols"]), depth, leaf)
+    dep = {"precision": ks.PRECISIONS[family], "config_ids": [ids[c] for c in pr["cols"]], "nodes": nodes}
+    h = ks.Handle(dep)
+    col = {c: j for j, c in enumerate(ids)}
+    chosen = [col[ks.select_kernel(h, *map(int, F[i]))] for i in te]
+    P = torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda()
+    scores = {"deployed_max": ks.score(P, pr["cols"]),
+              "tree": ks.score(P, pr["cols"], chosen=torch.from_numpy(np.asarray(chosen, np.int32)).cuda()),
+              "single_best": ks.score(P, [int(np.argmax(np.exp(np.mean(np.log(perf[tr] / perf[tr].max(1, keepdims=True)),
+                                                                       axis=0))))])}
+    return {"selector": dep, "scores": scores, "n_groups": n_groups, "n_train": len(tr), "n_test": len(te),
+            "features": "median M, median N, median K, problem count", "specs": [list(x) for x in specs]}
+
+
+def grouped_deploy(grouped_path: str, studies: dict[str, str]) -> dict:
+    """grouped.json with each family's group classifier: "config" becomes the
+    selector's choice for the 256-problem reference group (M, N, K
+    log-uniform in [32, 4096], seed 3), "exhaustive_config" keeps the fastest
+    config timed on that group."""
+    ks = _ks()
+    out = json.load(open(grouped_path))
+    ref = [dict(M=s.M, N=s.N, K=s.K) for s in wl.grouped_problems(256, 3)]
+    for fam, path in studies.items():
+        st = json.load(open(path))
+        h = ks.Handle(st["selector"])
+        entry = out[fam]
+        entry.setdefault("exhaustive_config", entry["config"])
+        entry["config"] = ks.select_kernel(h, *group_features(ref))
+        entry["selector"] = st["selector"]
+        entry["selector_scores"] = st["scores"]
+        entry["selector_groups"] = {"n_groups": st["n_groups"], "features": st["features"]}
     return out
 
 
@@ -640,6 +745,16 @@ def main(argv=None):
     st.add_argument("--out", required=True)
     gr = sub.add_parser("grouped")
     gr.add_argument("--out", required=True)
+    gs = sub.add_parser("grouped_select")
+    gs.add_argument("--family", required=True, choices=["tf32", "bf16", "f32x3"])
+    gs.add_argument("--sweep", required=True)
+    gs.add_argument("--groups", type=int, default=100)
+    gs.add_argument("--k", type=int, default=4)
+    gs.add_argument("--out", required=True)
+    gd = sub.add_parser("grouped_deploy")
+    gd.add_argument("--grouped", required=True)
+    gd.add_argument("--studies", nargs="+", required=True, help="family=path pairs")
+    gd.add_argument("--out", required=True)
     vg = sub.add_parser("vgg")
     vg.add_argument("--deploy", required=True)
     vg.add_argument("--sweep", required=True)
@@ -679,6 +794,19 @@ def main(argv=None):
         with open(a.out, "w") as f:
             json.dump(r, f, indent=1)
         print(json.dumps(r))
+        return
+    if a.cmd == "grouped_deploy":
+        r = grouped_deploy(a.grouped, dict(x.split("=", 1) for x in a.studies))
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps({k: {"config": v["config"], "exhaustive_config": v["exhaustive_config"]}
+                          for k, v in r.items()}, indent=1))
+        return
+    if a.cmd == "grouped_select":
+        r = grouped_study(a.family, a.sweep, a.groups, a.k)
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps({"config_ids": r["selector"]["config_ids"], "scores": r["scores"]}, indent=1))
         return
     if a.cmd == "grouped":
         r = grouped_tune()

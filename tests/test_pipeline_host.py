@@ -201,3 +201,22 @@ def test_forest_deployment_validation(ks):
     d = ks.Deployment(0, 2, ids, 3, nodes, None, 0, None, None, 300, r)
     hv = ks.vp()
     assert ks._lib.gemm_library_create(ks.ctypes.byref(d), ks.ctypes.byref(hv)) == -1
+
+
+def test_grouped_select_reads_group_medians(ks):
+    """gemm_grouped_select: the deployment's tree walked on (lower median M, N, K, count)."""
+    from paper_2008_13145_gb300 import tune
+    leaf = lambda c: {"feature": -1, "threshold": 0.0, "left": -1, "right": -1, "label": c}
+    nodes = [{"feature": 2, "threshold": 500.0, "left": 1, "right": 2, "label": 0}, leaf(0),
+             {"feature": 3, "threshold": 40.0, "left": 3, "right": 4, "label": 0}, leaf(1), leaf(2)]
+    h = ks.Handle({"precision": 2, "config_ids": [1100, 1117, 1105], "nodes": nodes})
+    rng = np.random.default_rng(5)
+    for count in (1, 2, 7, 33, 64):
+        for _ in range(5):
+            probs = [dict(M=int(rng.integers(1, 3000)), N=int(rng.integers(1, 3000)), K=int(rng.integers(1, 3000)),
+                          A=0, lda=1, B=0, ldb=1, C=0, ldc=1) for _ in range(count)]
+            f = tune.group_features(probs)
+            assert f[3] == count and f[2] == sorted(q["K"] for q in probs)[(count - 1) // 2]
+            assert ks.grouped_select(h, probs) == ks.select_kernel(h, *f)
+    with pytest.raises(ks.KSelectError):
+        ks.grouped_select(h, [dict(M=-1, N=1, K=1, A=0, lda=1, B=0, ldb=1, C=0, ldc=1)])
