@@ -349,6 +349,7 @@ def run_ours(args, ws, rank, local):
     grouped = grouped_launch(ks, tune) if not args.no_tc else None
     vgg16 = vgg16_inference(ks) if not args.no_tc else None
     c0 = single_gemm_256(ks, tune)
+    serving = mlp_serving(ks, tune, dep)
 
     if rank != 0:
         return
@@ -382,6 +383,7 @@ def run_ours(args, ws, rank, local):
         "grouped": grouped,
         "vgg16": vgg16,
         "single_gemm_256": c0,
+        "mlp_serving": serving,
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -494,6 +496,28 @@ def grouped_launch(ks, tune):
         plan.close()
         del keep
     return out
+
+
+def mlp_serving(ks, tune, dep, n: int = 4096, reps: int = 100):
+    """The learned selector's batched inference kernel over n queued shapes
+    (seeded grid shapes): microseconds per batch."""
+    import torch
+    if not dep.get("mlp_params"):
+        return None
+    h = ks.Handle({k: v for k, v in dep.items() if k != "known"})
+    shapes = torch.from_numpy(tune.shape_rows(wl.shape_grid(n, 12))).cuda()
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(5):
+        ks.select_kernels_batched(h, shapes, ids)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        ks.select_kernels_batched(h, shapes, ids)
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    return {"queued_shapes": n, "us_per_batch": us, "shapes_per_s": n / (us * 1e-6)}
 
 
 def single_gemm_256(ks, tune, reps: int = 200):

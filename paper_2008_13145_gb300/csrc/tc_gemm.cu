@@ -173,6 +173,24 @@ cudaError_t launch_prep(int family, const PrepJob& j, int batch, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// Both operands of one GEMM in a single launch: blocks [0, na) rewrite A, the
+// rest B (one launch less when neither operand can be read in place).
+template <typename TIn, typename TOut, bool SPLIT>
+__global__ void prep_pair_kernel(const PrepJob ja, const PrepJob jb) {
+  const int na = ja.tiles_k * ja.tiles_r;
+  const int t = (int)blockIdx.x;
+  if (t < na) prep_tile<TIn, TOut, SPLIT>(ja, blockIdx.z, t / ja.tiles_k, t % ja.tiles_k);
+  else prep_tile<TIn, TOut, SPLIT>(jb, blockIdx.z, (t - na) / jb.tiles_k, (t - na) % jb.tiles_k);
+}
+
+cudaError_t launch_prep_pair(int family, const PrepJob& ja, const PrepJob& jb, int batch, cudaStream_t s) {
+  dim3 block(32, 8), grid((unsigned)(ja.tiles_k * ja.tiles_r + jb.tiles_k * jb.tiles_r), 1, (unsigned)batch);
+  if (family == GEMM_PREC_F32X3) prep_pair_kernel<float, __nv_bfloat16, true><<<grid, block, 0, s>>>(ja, jb);
+  else if (family == GEMM_PREC_BF16) prep_pair_kernel<__nv_bfloat16, __nv_bfloat16, false><<<grid, block, 0, s>>>(ja, jb);
+  else prep_pair_kernel<float, float, false><<<grid, block, 0, s>>>(ja, jb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prep_group(int family, const PrepJob* jobs, int n_jobs, int blocks, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
   dim3 block(32, 8);
@@ -335,12 +353,13 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
   const void* Aop = pa.direct ? g.A : scratch;
   const void* Bop = pb.direct ? g.B : scratch + round_up(pa.bytes, 256);
   cudaError_t e = cudaSuccess;
-  if (!pa.direct) {
-    pa.job.out = const_cast<void*>(Aop);
+  pa.job.out = const_cast<void*>(Aop);
+  pb.job.out = const_cast<void*>(Bop);
+  if (!pa.direct && !pb.direct) {
+    e = launch_prep_pair(c.family, pa.job, pb.job, g.batch, s);
+  } else if (!pa.direct) {
     e = launch_prep(c.family, pa.job, g.batch, s);
-  }
-  if (e == cudaSuccess && !pb.direct) {
-    pb.job.out = const_cast<void*>(Bop);
+  } else if (!pb.direct) {
     e = launch_prep(c.family, pb.job, g.batch, s);
   }
   gemm_status_t st = e == cudaSuccess ? GEMM_OK : fail(e);
