@@ -58,9 +58,13 @@ SPLIT_BASE = 2000  # ids of the FP32 split-K kind: SPLIT_BASE + base config
 
 # ---------------------------------------------------------------- Section 3.1
 def sweep(shapes: list[wl.Shape], precision: int, out_path: str, seed: int = 0, refine_ratio: float = 2.0,
-          min_total_ms: float = 2.0, config_ids: list[int] | None = None, log=sys.stderr) -> np.ndarray:
+          min_total_ms: float = 2.0, config_ids: list[int] | None = None, log=sys.stderr,
+          shard: tuple[int, int] = (0, 1)) -> np.ndarray | None:
     """Benchmark every config on every shape; append one JSON line per shape
-    to out_path and skip shapes already there (resume).  Returns GFLOP/s (n x c)."""
+    to out_path and skip shapes already there (resume).  Returns GFLOP/s (n x c).
+    With shard = (k, n) only the shapes with index % n == k are run (one box's
+    part of a sweep split over several; `merge_sweeps` joins the files) and
+    None is returned."""
     import torch
     ks = _ks()
     ids = list(config_ids) if config_ids is not None else ks.config_ids(precision)
@@ -74,7 +78,7 @@ def sweep(shapes: list[wl.Shape], precision: int, out_path: str, seed: int = 0, 
     t0 = time.time()
     with open(out_path, "a") as f:
         for i, sh in enumerate(shapes):
-            if i in done:
+            if i in done or i % shard[1] != shard[0]:
                 continue
             A, B, C, lda, ldb, ldc = alloc_inputs(sh, precision, seed + i)
             ms, st = ks.benchmark_configs(ids, sh.transA, sh.transB, sh.M, sh.N, sh.K, A, lda, B, ldb, C, ldc,
@@ -91,7 +95,24 @@ def sweep(shapes: list[wl.Shape], precision: int, out_path: str, seed: int = 0, 
                 log.write(f"[sweep] {i + 1}/{len(shapes)} {sh} best {best:.1f} TFLOP/s  {time.time() - t0:.0f}s\n")
                 log.flush()
         torch.cuda.synchronize()
+    if shard[1] > 1:
+        return None
     return table_from_records([done[i] for i in range(len(shapes))], shapes)
+
+
+def merge_sweeps(paths: list[str], out_path: str) -> int:
+    """Concatenate sweep files (shards of one sweep, or a resumed run) into one,
+    one record per shape index (the first one seen wins); returns the count."""
+    seen = {}
+    for p in paths:
+        for line in open(p):
+            if line.strip():
+                r = json.loads(line)
+                seen.setdefault(r["i"], line.strip())
+    with open(out_path, "w") as f:
+        for i in sorted(seen):
+            f.write(seen[i] + "\n")
+    return len(seen)
 
 
 def table_from_records(records, shapes) -> np.ndarray:
@@ -727,6 +748,12 @@ def main(argv=None):
     s.add_argument("--table", default=None)
     s.add_argument("--kind", default="all", choices=["all", "base", "split"],
                    help="FP32 only: every config, the 576 base configs, or the split-K kind")
+    s.add_argument("--shard", default="0/1", help="k/n: run the shapes with index % n == k")
+    mg = sub.add_parser("merge")
+    mg.add_argument("--sweeps", nargs="+", required=True)
+    mg.add_argument("--n", type=int, default=1000)
+    mg.add_argument("--seed", type=int, default=1)
+    mg.add_argument("--table", required=True)
     ml = sub.add_parser("mlp")
     ml.add_argument("--deploy", required=True)
     ml.add_argument("--sweep", required=True)
@@ -795,6 +822,14 @@ def main(argv=None):
             json.dump(r, f, indent=1)
         print(json.dumps(r))
         return
+    if a.cmd == "merge":
+        merged = a.table + ".jsonl"
+        count = merge_sweeps(a.sweeps, merged)
+        recs, shapes, perf = load_sweep(merged)
+        assert count == a.n and shapes == wl.shape_grid(a.n, a.seed), "shards do not cover the grid"
+        save_table(a.table, shapes, perf, recs[0]["config_ids"], int(recs[0]["precision"]))
+        print(json.dumps({"shapes": count, "table": a.table}))
+        return
     if a.cmd == "grouped_deploy":
         r = grouped_deploy(a.grouped, dict(x.split("=", 1) for x in a.studies))
         with open(a.out, "w") as f:
@@ -847,8 +882,9 @@ def main(argv=None):
         ids = ks.config_ids(prec)
         if a.kind != "all":
             ids = [c for c in ids if (c >= SPLIT_BASE) == (a.kind == "split")]
-        perf = sweep(shapes, prec, a.out, config_ids=ids)
-        if a.table:
+        k, n = (int(x) for x in a.shard.split("/"))
+        perf = sweep(shapes, prec, a.out, config_ids=ids, shard=(k, n))
+        if a.table and perf is not None:
             save_table(a.table, shapes, perf, ids, prec)
     else:
         dep = deploy(a.table, a.k, a.tree, a.seed, a.norm, method=a.method)
