@@ -61,6 +61,19 @@ typedef struct kselect_library* gemm_handle_t;
 const char* gemm_status_string(int32_t status);
 int32_t gemm_last_cuda_error(void);
 
+/* Debug-build hooks (no paper counterpart).  The library built with
+ * KS_DEBUG_BOUNDS (libkselect_debug.so, a subset of the FP32 configs) checks
+ * every global access of its FP32 kernels and of the split-K reduction
+ * against the bytes each operand may span from its base -- (batch - 1)
+ * strides + (rows - 1) leading dimensions + the row length -- and counts and
+ * skips any access outside.  kselect_debug_bounds_errors reads the count
+ * (synchronising the device; clear != 0 resets it); kselect_debug_shrink_extents
+ * declares the operand extents smaller by the given bytes on later calls (a
+ * test of the checker itself, which then flags accesses that are in fact
+ * inside the buffers).  Release builds return GEMM_ERR_UNSUPPORTED. */
+gemm_status_t kselect_debug_bounds_errors(int32_t* errors_out, int32_t clear);
+gemm_status_t kselect_debug_shrink_extents(int64_t a_bytes, int64_t b_bytes, int64_t c_bytes);
+
 /* ---------------------------------------------------------------- config space
  * Section 3: each work item computes an R x C output tile; tile sizes are
  * compile-time constants and the work-group shape is chosen per launch, giving

@@ -17,6 +17,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkselect.so")
+# Debug variant: every global access of the FP32 kernels checked against the
+# operands' extents (KS_DEBUG_BOUNDS), over every DEBUG_SUBSET-th SIMT config.
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_BUILD, "libkselect_debug.so")
+DEBUG_SUBSET = 7
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 N_SHARDS = 12
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -35,7 +40,7 @@ def _flags() -> list[str]:
             "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 
 
-def _units() -> list[tuple[str, str, list[str]]]:
+def _units(build_dir: str) -> list[tuple[str, str, list[str]]]:
     units = []
     for name in sorted(os.listdir(CSRC)):
         if not name.endswith(".cu"):
@@ -43,9 +48,9 @@ def _units() -> list[tuple[str, str, list[str]]]:
         src = os.path.join(CSRC, name)
         if name == "simt_shard.cu":
             for i in range(N_SHARDS):
-                units.append((src, os.path.join(BUILD, f"simt_shard_{i}.o"), [f"-DKS_SHARD={i}"]))
+                units.append((src, os.path.join(build_dir, f"simt_shard_{i}.o"), [f"-DKS_SHARD={i}"]))
         else:
-            units.append((src, os.path.join(BUILD, name[:-3] + ".o"), []))
+            units.append((src, os.path.join(build_dir, name[:-3] + ".o"), []))
     return units
 
 
@@ -60,16 +65,27 @@ def _digest(paths: list[str], extra: str) -> str:
 
 def build_library(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     """Compile (if sources changed) and link libkselect.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+    return _build(BUILD, LIB, [], force, jobs, verbose)
+
+
+def build_debug_library(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+    """The bounds-checking debug variant (libkselect_debug.so, same C ABI, a
+    subset of the FP32 configs); returns its path."""
+    return _build(DEBUG_BUILD, DEBUG_LIB, ["-DKS_DEBUG_BOUNDS", f"-DKS_SUBSET={DEBUG_SUBSET}"], force, jobs,
+                  verbose)
+
+
+def _build(build_dir: str, lib: str, defines: list[str], force: bool, jobs: int | None, verbose: bool) -> str:
+    os.makedirs(build_dir, exist_ok=True)
     srcs = [os.path.join(CSRC, n) for n in os.listdir(CSRC) if n.endswith((".cu", ".cuh", ".h"))]
     srcs.append(os.path.join(INCLUDE, "kselect.h"))
-    stamp_path = os.path.join(BUILD, "stamp")
-    digest = _digest(srcs, " ".join(_flags()) + os.uname().machine)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_path):
+    stamp_path = os.path.join(build_dir, "stamp")
+    digest = _digest(srcs, " ".join(_flags() + defines) + os.uname().machine)
+    if not force and os.path.exists(lib) and os.path.exists(stamp_path):
         if open(stamp_path).read() == digest:
-            return LIB
+            return lib
     cc = nvcc()
-    units = _units()
+    units = [(src, obj, extra + defines) for src, obj, extra in _units(build_dir)]
     jobs = jobs or max(1, os.cpu_count() or 1)
 
     def compile_one(u):
@@ -84,15 +100,15 @@ def build_library(force: bool = False, jobs: int | None = None, verbose: bool = 
         for msg in ex.map(compile_one, units):
             if verbose and msg.strip():
                 sys.stderr.write(msg)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [cc, ARCH, "-shared", "-cudart", "shared", "-o", tmp, *[u[1] for u in units]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_path, "w") as f:
         f.write(digest)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

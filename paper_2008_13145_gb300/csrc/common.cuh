@@ -43,7 +43,27 @@ struct GemmArgs {
   // covers k in [s * kchunk, min(K, (s + 1) * kchunk)) and C/ldc/strideC then
   // describe the partial-sum workspace (one M x ldc slab per z).
   int splits = 1, kchunk = 0;
+#ifdef KS_DEBUG_BOUNDS
+  // Debug build: the bytes each operand may touch from its base (A, B, C), and
+  // the device counter of accesses found outside them (each one is skipped).
+  const char* lo[3] = {nullptr, nullptr, nullptr};
+  int64_t ext[3] = {0, 0, 0};
+  int* err = nullptr;
+#endif
 };
+
+// True when [ptr, ptr + bytes) lies inside operand `op`'s extent; always true
+// outside the debug build (the check compiles away).
+__device__ __forceinline__ bool ks_in_bounds(const GemmArgs& p, int op, const void* ptr, int bytes) {
+#ifdef KS_DEBUG_BOUNDS
+  const char* c = static_cast<const char*>(ptr);
+  if (c < p.lo[op] || c + bytes > p.lo[op] + p.ext[op]) {
+    atomicAdd(p.err, 1);
+    return false;
+  }
+#endif
+  return true;
+}
 
 using LaunchFn = cudaError_t (*)(const GemmArgs&, cudaStream_t);
 using OccFn = int (*)();  // resident CTAs per SM on the current device, 0 on error

@@ -76,6 +76,34 @@ static bool is_trans(char t, int* out) {
   return false;
 }
 
+#ifdef KS_DEBUG_BOUNDS
+// Debug build: accesses outside an operand's extent are counted here (and skipped).
+__device__ int g_bounds_errors;
+static int64_t g_shrink[3] = {0, 0, 0};  // test hook: bytes taken off each declared extent
+
+static int* bounds_counter() {
+  void* p = nullptr;
+  return cudaGetSymbolAddress(&p, g_bounds_errors) == cudaSuccess ? static_cast<int*>(p) : nullptr;
+}
+
+// The bytes from each base pointer up to the last element a correct kernel may
+// touch: (batch - 1) strides + (rows - 1) leading dimensions + the row length.
+static void set_extents(GemmArgs* a, int elem) {
+  const int64_t ar = a->transA ? a->K : a->M, ac = a->transA ? a->M : a->K;
+  const int64_t br = a->transB ? a->N : a->K, bc = a->transB ? a->K : a->N;
+  auto span = [](int64_t batch, int64_t stride, int64_t rows, int64_t ld, int64_t cols) {
+    return rows > 0 && cols > 0 ? (batch - 1) * stride + (rows - 1) * ld + cols : 0;
+  };
+  a->lo[0] = static_cast<const char*>(a->A);
+  a->lo[1] = static_cast<const char*>(a->B);
+  a->lo[2] = reinterpret_cast<const char*>(a->C);
+  a->ext[0] = span(a->batch, a->strideA, ar, a->lda, ac) * elem - g_shrink[0];
+  a->ext[1] = span(a->batch, a->strideB, br, a->ldb, bc) * elem - g_shrink[1];
+  a->ext[2] = span(a->batch, a->strideC, a->M, a->ldc, a->N) * 4 - g_shrink[2];
+  a->err = bounds_counter();
+}
+#endif
+
 // Validates a GEMM request and fills GemmArgs.  elem = bytes per A/B element.
 static gemm_status_t make_args(char transA, char transB, int64_t M, int64_t N, int64_t K, float alpha,
                                const void* A, int64_t lda, const void* B, int64_t ldb, float beta,
@@ -105,6 +133,9 @@ static gemm_status_t make_args(char transA, char transB, int64_t M, int64_t N, i
   a->vecC = ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0);
   a->splits = 1;
   a->kchunk = (int)K;
+#ifdef KS_DEBUG_BOUNDS
+  set_extents(a, elem);
+#endif
   return GEMM_OK;
 }
 
@@ -199,7 +230,8 @@ static int split_for(int id, const GemmArgs& a, int* kchunk) {
 // C[b] = alpha * sum_s W[b, s] + beta * C[b], the splits summed in order s = 0, 1, ...
 // One thread per 4 consecutive columns of a row; W rows are 16-byte aligned (ldw % 4 == 0).
 __global__ void split_reduce_kernel(const float* __restrict__ W, int64_t ldw, int S, int M, int N, int batch,
-                                    float alpha, float beta, float* C, int64_t ldc, int64_t strideC, int vecC) {
+                                    float alpha, float beta, float* C, int64_t ldc, int64_t strideC, int vecC,
+                                    const GemmArgs chk) {
   const int n4 = (N + 3) / 4;
   const int64_t total = (int64_t)batch * M * n4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -207,13 +239,17 @@ __global__ void split_reduce_kernel(const float* __restrict__ W, int64_t ldw, in
     const int j = (int)(t - row * n4) * 4;
     const int64_t b = row / M, i = row - b * M;
     const float* w = W + ((b * S) * M + i) * ldw + j;
-    float4 acc = *reinterpret_cast<const float4*>(w);
-    for (int s = 1; s < S; ++s) {
-      const float4 v = *reinterpret_cast<const float4*>(w + (int64_t)s * M * ldw);
-      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < S; ++s) {
+      const float* ws = w + (int64_t)s * M * ldw;
+      if (!ks_in_bounds(chk, 0, ws, 16)) continue;  // operand 0 = the partial-tile workspace
+      const float4 v = *reinterpret_cast<const float4*>(ws);
+      if (s == 0) acc = v;
+      else { acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w; }
     }
     float o[4] = {alpha * acc.x, alpha * acc.y, alpha * acc.z, alpha * acc.w};
     float* c = C + b * strideC + i * ldc + j;
+    if (!ks_in_bounds(chk, 2, c, 4 * min(4, N - j))) continue;
     if (vecC && j + 3 < N) {
       if (beta != 0.f) {
         const float4 c0 = *reinterpret_cast<const float4*>(c);
@@ -274,12 +310,21 @@ static gemm_status_t launch_split(int base, const GemmArgs& a, int splits, int k
   p.vecC = 1;
   p.splits = splits;
   p.kchunk = kchunk;
+#ifdef KS_DEBUG_BOUNDS
+  p.lo[2] = static_cast<const char*>(w);  // the partial tiles go to the workspace
+  p.ext[2] = (int64_t)bytes;
+  GemmArgs chk = a;  // reduction: reads the workspace (slot 0), writes C (slot 2)
+  chk.lo[0] = static_cast<const char*>(w);
+  chk.ext[0] = (int64_t)bytes;
+#else
+  const GemmArgs& chk = a;
+#endif
   e = g_simt_split[base](p, s);
   if (e == cudaSuccess) {
     const int64_t total = (int64_t)a.batch * a.M * ((a.N + 3) / 4);
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     split_reduce_kernel<<<grid, 256, 0, s>>>(static_cast<const float*>(w), ldw, splits, a.M, a.N, a.batch, a.alpha,
-                                              a.beta, a.C, a.ldc, a.strideC, a.vecC);
+                                              a.beta, a.C, a.ldc, a.strideC, a.vecC, chk);
     e = cudaGetLastError();
   }
   cudaError_t ef = cudaFreeAsync(w, s);
@@ -365,6 +410,35 @@ const char* gemm_status_string(int32_t s) {
 }
 
 int32_t gemm_last_cuda_error(void) { return g_last_cuda_error; }
+
+gemm_status_t kselect_debug_bounds_errors(int32_t* out, int32_t clear) {
+#ifdef KS_DEBUG_BOUNDS
+  if (!out) return GEMM_ERR_INVALID_ARG;
+  int* c = bounds_counter();
+  if (!c) return GEMM_ERR_CUDA;
+  int v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, c, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(c, 0, sizeof(int));
+  if (e != cudaSuccess) { set_last_cuda_error(e); return GEMM_ERR_CUDA; }
+  *out = v;
+  return GEMM_OK;
+#else
+  (void)out; (void)clear;
+  return GEMM_ERR_UNSUPPORTED;
+#endif
+}
+
+gemm_status_t kselect_debug_shrink_extents(int64_t a_bytes, int64_t b_bytes, int64_t c_bytes) {
+#ifdef KS_DEBUG_BOUNDS
+  if (a_bytes < 0 || b_bytes < 0 || c_bytes < 0) return GEMM_ERR_INVALID_ARG;
+  g_shrink[0] = a_bytes; g_shrink[1] = b_bytes; g_shrink[2] = c_bytes;
+  return GEMM_OK;
+#else
+  (void)a_bytes; (void)b_bytes; (void)c_bytes;
+  return GEMM_ERR_UNSUPPORTED;
+#endif
+}
 
 int32_t gemm_config_count(int32_t precision) {
   if (precision == GEMM_PREC_F32) return kSimtConfigs + kSplitConfigs;
@@ -536,6 +610,9 @@ static gemm_status_t strided_args(int32_t id, char transA, char transB, int64_t 
   a->vecA = a->vecA && (strideA % per16 == 0);
   a->vecB = a->vecB && (strideB % per16 == 0);
   a->vecC = a->vecC && (strideC % 4 == 0);
+#ifdef KS_DEBUG_BOUNDS
+  set_extents(a, elem_bytes_of(id));
+#endif
   return GEMM_OK;
 }
 

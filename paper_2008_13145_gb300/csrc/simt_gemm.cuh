@@ -69,12 +69,14 @@ __device__ __forceinline__ void load_vec_smem(float* dst, const float* src) {
   }
 }
 
-// Global load of W consecutive floats at src[0..W), element q valid when q < lim;
-// one vector load when `vec` and all W are valid.
+// Global load of W consecutive floats at src[0..W) of operand `op`, element q
+// valid when q < lim; one vector load when `vec` and all W are valid.
 template <int W>
-__device__ __forceinline__ void load_vec_global(float* dst, const float* src, int lim, bool vec) {
+__device__ __forceinline__ void load_vec_global(float* dst, const float* src, int lim, bool vec, const GemmArgs& p,
+                                                int op) {
   if (vec && lim >= W) {
-    typename VecT<W>::T v = __ldg(reinterpret_cast<const typename VecT<W>::T*>(src));
+    typename VecT<W>::T v = ks_in_bounds(p, op, src, 4 * W) ? __ldg(reinterpret_cast<const typename VecT<W>::T*>(src))
+                                                             : typename VecT<W>::T{};
     if constexpr (W == 1) {
       dst[0] = v;
     } else if constexpr (W == 2) {
@@ -84,7 +86,7 @@ __device__ __forceinline__ void load_vec_global(float* dst, const float* src, in
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < W; ++q) dst[q] = (q < lim) ? __ldg(src + q) : 0.f;
+    for (int q = 0; q < W; ++q) dst[q] = (q < lim && ks_in_bounds(p, op, src + q, 4)) ? __ldg(src + q) : 0.f;
   }
 }
 
@@ -138,6 +140,7 @@ template <class Cfg>
 __device__ __forceinline__ void store_out(const GemmArgs& p, float* Cb, int gm, int gn, float v) {
   if (gm < p.M && gn < p.N) {
     float* dst = Cb + (int64_t)gm * p.ldc + gn;
+    if (!ks_in_bounds(p, 2, dst, 4)) return;
     float out = p.alpha * v;
     if (p.beta != 0.f) out = fmaf(p.beta, *dst, out);
     *dst = out;
@@ -150,6 +153,7 @@ __device__ __forceinline__ void store_out4(const GemmArgs& p, float* Cb, int gm,
   if (gm >= p.M) return;
   float* dst = Cb + (int64_t)gm * p.ldc + gn;
   if (p.vecC && gn + 3 < p.N) {
+    if (!ks_in_bounds(p, 2, dst, 16)) return;
     float4 o = make_float4(p.alpha * v[0], p.alpha * v[1], p.alpha * v[2], p.alpha * v[3]);
     if (p.beta != 0.f) {
       float4 c = *reinterpret_cast<const float4*>(dst);
@@ -237,18 +241,20 @@ __device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArg
         const int m = c / (BK / 4), kq = (c % (BK / 4)) * 4;
         const int gm = m0 + m, gk = k0 + kq;
         if (FAST) {
-          r[u] = __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gm * p.lda + gk));
+          r[u] = ks_in_bounds(p, 0, Ab + (int64_t)gm * p.lda + gk, 16)
+                     ? __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gm * p.lda + gk)) : float4{};
           continue;
         }
-        if (gm < p.M) load_vec_global<4>(v, Ab + (int64_t)gm * p.lda + gk, K - gk, p.vecA);
+        if (gm < p.M) load_vec_global<4>(v, Ab + (int64_t)gm * p.lda + gk, K - gk, p.vecA, p, 0);
       } else {  // stored K x M: chunk of 4 along m
         const int k = c / (BM / 4), mq = (c % (BM / 4)) * 4;
         const int gk = k0 + k, gm = m0 + mq;
         if (FAST) {
-          r[u] = __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gk * p.lda + gm));
+          r[u] = ks_in_bounds(p, 0, Ab + (int64_t)gk * p.lda + gm, 16)
+                     ? __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gk * p.lda + gm)) : float4{};
           continue;
         }
-        if (gk < K) load_vec_global<4>(v, Ab + (int64_t)gk * p.lda + gm, p.M - gm, p.vecA);
+        if (gk < K) load_vec_global<4>(v, Ab + (int64_t)gk * p.lda + gm, p.M - gm, p.vecA, p, 0);
       }
     }
     r[u] = make_float4(v[0], v[1], v[2], v[3]);
@@ -290,18 +296,20 @@ __device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArg
         const int k = c / (BN / 4), nq = (c % (BN / 4)) * 4;
         const int gk = k0 + k, gn = n0 + nq;
         if (FAST) {
-          r[u] = __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gk * p.ldb + gn));
+          r[u] = ks_in_bounds(p, 1, Bb + (int64_t)gk * p.ldb + gn, 16)
+                     ? __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gk * p.ldb + gn)) : float4{};
           continue;
         }
-        if (gk < K) load_vec_global<4>(v, Bb + (int64_t)gk * p.ldb + gn, p.N - gn, p.vecB);
+        if (gk < K) load_vec_global<4>(v, Bb + (int64_t)gk * p.ldb + gn, p.N - gn, p.vecB, p, 1);
       } else {  // stored N x K: chunk along k
         const int n = c / (BK / 4), kq = (c % (BK / 4)) * 4;
         const int gn = n0 + n, gk = k0 + kq;
         if (FAST) {
-          r[u] = __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gn * p.ldb + gk));
+          r[u] = ks_in_bounds(p, 1, Bb + (int64_t)gn * p.ldb + gk, 16)
+                     ? __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gn * p.ldb + gk)) : float4{};
           continue;
         }
-        if (gn < p.N) load_vec_global<4>(v, Bb + (int64_t)gn * p.ldb + gk, K - gk, p.vecB);
+        if (gn < p.N) load_vec_global<4>(v, Bb + (int64_t)gn * p.ldb + gk, K - gk, p.vecB, p, 1);
       }
     }
     r[u] = make_float4(v[0], v[1], v[2], v[3]);
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
           for (int i = 0; i < TM; ++i) {
             const int gm = m0 + Cfg::row(i, ty);
             if (gm < p.M) {
-              load_vec_global<4>(a[i], Ab + (int64_t)gm * p.lda + gk, klim, p.vecA);
+              load_vec_global<4>(a[i], Ab + (int64_t)gm * p.lda + gk, klim, p.vecA, p, 0);
             } else {
               a[i][0] = a[i][1] = a[i][2] = a[i][3] = 0.f;
             }
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
               const int r0 = ic * (Cfg::WY * CM) + ty * CM;
               float t[CM];
               if (k < klim) {
-                load_vec_global<CM>(t, Ab + (int64_t)(gk + k) * p.lda + m0 + r0, p.M - m0 - r0, p.vecA);
+                load_vec_global<CM>(t, Ab + (int64_t)(gk + k) * p.lda + m0 + r0, p.M - m0 - r0, p.vecA, p, 0);
               } else {
 #pragma unroll
                 for (int q = 0; q < CM; ++q) t[q] = 0.f;
@@ -450,7 +458,7 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
               const int c0 = jc * (Cfg::WX * CN) + tx * CN;
               float t[CN];
               if (k < klim) {
-                load_vec_global<CN>(t, Bb + (int64_t)(gk + k) * p.ldb + n0 + c0, p.N - n0 - c0, p.vecB);
+                load_vec_global<CN>(t, Bb + (int64_t)(gk + k) * p.ldb + n0 + c0, p.N - n0 - c0, p.vecB, p, 1);
               } else {
 #pragma unroll
                 for (int q = 0; q < CN; ++q) t[q] = 0.f;
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
           for (int j = 0; j < TN; ++j) {
             const int gn = n0 + Cfg::col(j, tx);
             float t[4] = {0.f, 0.f, 0.f, 0.f};
-            if (gn < p.N) load_vec_global<4>(t, Bb + (int64_t)gn * p.ldb + gk, klim, p.vecB);
+            if (gn < p.N) load_vec_global<4>(t, Bb + (int64_t)gn * p.ldb + gk, klim, p.vecB, p, 1);
 #pragma unroll
             for (int k = 0; k < 4; ++k) bv[k][j] = t[k];
           }

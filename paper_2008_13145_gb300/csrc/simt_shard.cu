@@ -12,9 +12,13 @@
 
 namespace ks {
 namespace {
+#ifndef KS_SUBSET
+#define KS_SUBSET 1  // debug builds instantiate every KS_SUBSET-th config only
+#endif
+
 template <int ID>
 void reg_one(LaunchFn* table, LaunchFn* split, OccFn* occ) {
-  if constexpr (ID % kSimtShards == KS_SHARD) {
+  if constexpr (ID % kSimtShards == KS_SHARD && ID % KS_SUBSET == 0) {
     table[ID] = &launch_simt<ID, false>;
     if constexpr (split_eligible(ID)) {
       split[ID] = &launch_simt<ID, true>;

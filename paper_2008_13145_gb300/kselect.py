@@ -4,7 +4,8 @@ Every function takes device buffers as torch tensors (or raw integer device
 pointers) and an optional stream (torch.cuda.Stream, raw handle, or None for
 torch's current stream).  A non-OK status raises ``KSelectError``.  Importing
 this module loads the compiled library and raises if it is missing: there is
-no fallback implementation.
+no fallback implementation.  With KSELECT_DEBUG_BOUNDS=1 in the environment it
+loads the bounds-checking debug build (libkselect_debug.so) instead.
 """
 from __future__ import annotations
 
@@ -13,10 +14,12 @@ import os
 
 import numpy as np
 
-from .build import LIB
+from .build import DEBUG_LIB, LIB
 
+if os.environ.get("KSELECT_DEBUG_BOUNDS") == "1":
+    LIB = DEBUG_LIB
 if not os.path.exists(LIB):
-    raise ImportError(f"libkselect.so is not built ({LIB}); run __graft_entry__.build() first")
+    raise ImportError(f"{os.path.basename(LIB)} is not built ({LIB}); run __graft_entry__.build() first")
 
 _lib = ctypes.CDLL(LIB)
 
@@ -61,6 +64,8 @@ def _sig(name, res, args):
 
 _sig("gemm_status_string", ctypes.c_char_p, [i32])
 _sig("gemm_last_cuda_error", i32, [])
+_sig("kselect_debug_bounds_errors", i32, [ctypes.POINTER(i32), i32])
+_sig("kselect_debug_shrink_extents", i32, [i64, i64, i64])
 _sig("gemm_config_count", i32, [i32])
 _sig("gemm_config_id", i32, [i32, i32])
 _sig("gemm_config_params", i32, [i32, ctypes.POINTER(i32)])
@@ -625,7 +630,8 @@ def select_kernels_batched(handle: Handle, shapes, ids_out, pred=None, stream=No
 
 def exported_symbols() -> list[str]:
     """Names of the C-ABI entry points this binding expects."""
-    return ["gemm_status_string", "gemm_last_cuda_error", "gemm_config_count", "gemm_config_id",
+    return ["gemm_status_string", "gemm_last_cuda_error", "kselect_debug_bounds_errors",
+            "kselect_debug_shrink_extents", "gemm_config_count", "gemm_config_id",
             "gemm_config_params", "gemm_split_choose", "gemm_split_factor", "gemm_library_create", "gemm_library_destroy", "select_kernel", "gemm",
             "gemm_with_config", "gemm_host_pipeline", "gemm_strided_batched", "gemm_strided_batched_with_config", "gemm_host", "gemm_benchmark", "gemm_error_check", "kselect_fill_uniform",
             "gemm_benchmark_configs", "gemm_device_status", "kselect_wait_selftest", "kselect_normalise", "kselect_kmeans", "kselect_score",
