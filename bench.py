@@ -447,11 +447,13 @@ def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
         ratio = np.minimum(exh / sel, 1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_push(f"timed_{name}")  # lets a profiler select this family's timed steps
         e0.record(stream)
         for _ in range(args.steps):
             run()
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
         ms = e0.elapsed_time(e1) / args.steps
         flops = sum(sh.flops for sh in shapes)
         # The same step captured once in a CUDA graph (kernels selected at capture) and replayed.

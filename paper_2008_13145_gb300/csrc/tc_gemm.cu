@@ -105,42 +105,83 @@ struct PrepJob {
   void* out;
   int64_t ld_out;
   int R, K, Kp, nseg, pattern;
-  int tiles_k, tiles_r, block_start;  // 32 x 32 tiles; first block of this job (grouped form)
+  int tiles_k, tiles_r, block_start;  // 64 x 64 tiles; first block of this job (grouped form)
+  int vec2;  // element pairs along the source's contiguous dimension may be read as one access
 };
+
+template <typename T>
+__device__ __forceinline__ float to_f32(T v) {
+  if constexpr (sizeof(T) == 2) return __bfloat162float(v);
+  else return (float)v;
+}
+
+// One 64 x 64 tile of a job.  A warp row reads 64 consecutive elements along
+// the source's contiguous dimension (two per lane, as one access when the job
+// allows), the tile turns in shared memory, and a warp row writes 64
+// consecutive K positions of one output row (two per lane).
+constexpr int kPrepWarps = 8;  // warps per pre-pass block; each takes 64 / kPrepWarps tile rows
 
 template <typename TIn, typename TOut, bool SPLIT>
 __device__ __forceinline__ void prep_tile(const PrepJob& j, int b, int tr, int tk) {
-  __shared__ float tile[32][33];
-  const int r0 = tr * 32, k0 = tk * 32;
+  __shared__ float tile[64][65];
+  const int r0 = tr * 64, k0 = tk * 64, lane = threadIdx.x;
   const TIn* src = static_cast<const TIn*>(j.in) + (int64_t)b * j.in_stride;
   const bool k_fast = (j.ks == 1);
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    int r, k;
-    if (k_fast) { r = r0 + i; k = k0 + threadIdx.x; } else { k = k0 + i; r = r0 + threadIdx.x; }
-    float v = 0.f;
-    if (r < j.R && k < j.K) {
-      if constexpr (sizeof(TIn) == 2) v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(src)[r * j.rs + k * j.ks]);
-      else v = (float)src[r * j.rs + k * j.ks];
+#pragma unroll
+  for (int it = 0; it < 64 / kPrepWarps; ++it) {
+    const int i = threadIdx.y + it * kPrepWarps;
+    int r, k;  // first element of this lane's pair; the second is the next along the contiguous dimension
+    if (k_fast) { r = r0 + i; k = k0 + 2 * lane; } else { k = k0 + i; r = r0 + 2 * lane; }
+    const bool in0 = r < j.R && k < j.K;
+    const bool in1 = k_fast ? (r < j.R && k + 1 < j.K) : (r + 1 < j.R && k < j.K);
+    const TIn* p = src + (int64_t)r * j.rs + (int64_t)k * j.ks;
+    float v0 = 0.f, v1 = 0.f;
+    if (j.vec2 && in1) {
+      if constexpr (sizeof(TIn) == 2) {
+        const __nv_bfloat162 w = *reinterpret_cast<const __nv_bfloat162*>(p);
+        v0 = __low2float(w);
+        v1 = __high2float(w);
+      } else {
+        const float2 w = *reinterpret_cast<const float2*>(p);
+        v0 = w.x;
+        v1 = w.y;
+      }
+    } else {
+      if (in0) v0 = to_f32(p[0]);
+      if (in1) v1 = to_f32(p[1]);
     }
-    if (k_fast) tile[i][threadIdx.x] = v; else tile[threadIdx.x][i] = v;
+    if (k_fast) { tile[i][2 * lane] = v0; tile[i][2 * lane + 1] = v1; }
+    else { tile[2 * lane][i] = v0; tile[2 * lane + 1][i] = v1; }
   }
   __syncthreads();
   TOut* dst = static_cast<TOut*>(j.out) + (int64_t)b * j.R * j.ld_out;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int r = r0 + i, k = k0 + threadIdx.x;
+#pragma unroll
+  for (int it = 0; it < 64 / kPrepWarps; ++it) {
+    const int i = threadIdx.y + it * kPrepWarps;
+    const int r = r0 + i, k = k0 + 2 * lane;
     if (r >= j.R || k >= j.Kp) continue;
-    const float x = tile[i][threadIdx.x];
+    const float x0 = tile[i][2 * lane], x1 = tile[i][2 * lane + 1];
+    const bool two = k + 1 < j.Kp;  // Kp and ld_out are even, so a pair is 2-element aligned
     if constexpr (!SPLIT) {
+      TOut* o = dst + (int64_t)r * j.ld_out + k;
       if constexpr (sizeof(TOut) == 2) {
-        reinterpret_cast<__nv_bfloat16*>(dst)[(int64_t)r * j.ld_out + k] = __float2bfloat16_rn(x);
+        if (two) *reinterpret_cast<__nv_bfloat162*>(o) = __floats2bfloat162_rn(x0, x1);
+        else o[0] = __float2bfloat16_rn(x0);
       } else {
-        dst[(int64_t)r * j.ld_out + k] = x;
+        if (two) *reinterpret_cast<float2*>(o) = make_float2(x0, x1);
+        else o[0] = x0;
       }
     } else {
-      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
       __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(dst) + (int64_t)r * j.ld_out + k;
-      for (int s = 0; s < j.nseg; ++s) o[(int64_t)s * j.Kp] = ((j.pattern >> s) & 1) ? lo : hi;
+      for (int sg = 0; sg < j.nseg; ++sg) {
+        const bool lo = (j.pattern >> sg) & 1;
+        __nv_bfloat16* os = o + (int64_t)sg * j.Kp;
+        if (two) *reinterpret_cast<__nv_bfloat162*>(os) = __halves2bfloat162(lo ? l0 : h0, lo ? l1 : h1);
+        else os[0] = lo ? l0 : h0;
+      }
     }
   }
 }
@@ -166,7 +207,7 @@ __global__ void prep_group_kernel(const PrepJob* jobs, int n_jobs) {
 }
 
 cudaError_t launch_prep(int family, const PrepJob& j, int batch, cudaStream_t s) {
-  dim3 block(32, 8), grid((unsigned)j.tiles_k, (unsigned)j.tiles_r, (unsigned)batch);
+  dim3 block(32, kPrepWarps), grid((unsigned)j.tiles_k, (unsigned)j.tiles_r, (unsigned)batch);
   if (family == GEMM_PREC_F32X3) prep_kernel<float, __nv_bfloat16, true><<<grid, block, 0, s>>>(j);
   else if (family == GEMM_PREC_BF16) prep_kernel<__nv_bfloat16, __nv_bfloat16, false><<<grid, block, 0, s>>>(j);
   else prep_kernel<float, float, false><<<grid, block, 0, s>>>(j);
@@ -184,7 +225,7 @@ __global__ void prep_pair_kernel(const PrepJob ja, const PrepJob jb) {
 }
 
 cudaError_t launch_prep_pair(int family, const PrepJob& ja, const PrepJob& jb, int batch, cudaStream_t s) {
-  dim3 block(32, 8), grid((unsigned)(ja.tiles_k * ja.tiles_r + jb.tiles_k * jb.tiles_r), 1, (unsigned)batch);
+  dim3 block(32, kPrepWarps), grid((unsigned)(ja.tiles_k * ja.tiles_r + jb.tiles_k * jb.tiles_r), 1, (unsigned)batch);
   if (family == GEMM_PREC_F32X3) prep_pair_kernel<float, __nv_bfloat16, true><<<grid, block, 0, s>>>(ja, jb);
   else if (family == GEMM_PREC_BF16) prep_pair_kernel<__nv_bfloat16, __nv_bfloat16, false><<<grid, block, 0, s>>>(ja, jb);
   else prep_pair_kernel<float, float, false><<<grid, block, 0, s>>>(ja, jb);
@@ -193,7 +234,7 @@ cudaError_t launch_prep_pair(int family, const PrepJob& ja, const PrepJob& jb, i
 
 cudaError_t launch_prep_group(int family, const PrepJob* jobs, int n_jobs, int blocks, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
-  dim3 block(32, 8);
+  dim3 block(32, kPrepWarps);
   if (family == GEMM_PREC_F32X3) prep_group_kernel<float, __nv_bfloat16, true><<<blocks, block, 0, s>>>(jobs, n_jobs);
   else if (family == GEMM_PREC_BF16)
     prep_group_kernel<__nv_bfloat16, __nv_bfloat16, false><<<blocks, block, 0, s>>>(jobs, n_jobs);
@@ -311,8 +352,13 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   const int64_t Kp = x3 ? round_up(K, 64) : round_up(K, 16 / op_elem);
   o.ld = o.direct ? ld : nseg * Kp;
   o.bytes = o.direct ? 0 : (int64_t)batch * R * o.ld * op_elem;
+  // Element pairs along the contiguous dimension are read as one access when
+  // every pair starts on a multiple of two elements: base, row and batch
+  // strides all even multiples of the element size.
+  const int64_t pair_bytes = 2 * in_elem;
+  const int vec2 = ((uintptr_t)ptr % pair_bytes == 0) && (ld % 2 == 0) && (stride % 2 == 0);
   o.job = PrepJob{ptr, stride, kcontig ? ld : 1, kcontig ? 1 : ld, nullptr, o.ld, R, K, (int)Kp, nseg, pattern,
-                  (int)((Kp + 31) / 32), (R + 31) / 32, 0};
+                  (int)((Kp + 63) / 64), (R + 63) / 64, 0, vec2};
   return o;
 }
 
