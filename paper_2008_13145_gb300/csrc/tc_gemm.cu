@@ -62,7 +62,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D map over a (batch, rows, K) K-contiguous operand; box = (128-byte K slice) x box_rows.
+// 3-D map over a (batch, rows, inner) operand whose `inner` dimension is
+// contiguous; box = (128-byte inner slice) x box_rows.  K-major operands pass
+// (inner, rows) = (K, R); MN-major ones (R, K).
 bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t K, int64_t rows, int64_t ld, int64_t batch,
               int box_rows) {
   auto fn = encode_fn();
@@ -331,15 +333,17 @@ gemm_status_t fail(cudaError_t e) {
 // How one operand reaches the kernel: in place, or through a rewrite job.
 struct OperandPlan {
   bool direct;
+  bool mn;         // read in place as MN-major tiles (BF16 stored MN-contiguous)
   int64_t ld;      // leading dimension the kernel reads
   int64_t bytes;   // scratch bytes (0 when direct)
   PrepJob job;     // filled when !direct (out set later)
 };
 
 // Operand of logical shape R x K (rows of op(A), or columns of op(B) = rows of
-// B^T).  `kcontig` says whether it is stored R x K (K contiguous).
+// B^T).  `kcontig` says whether it is stored R x K (K contiguous); `mn_ext` is
+// the extent along R that one CTA loads per slice (128 for A, BN or BN / 2 for B).
 OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t stride, bool kcontig, int R, int K,
-                         int batch, int pattern) {
+                         int batch, int pattern, int mn_ext) {
   const bool x3 = c.family == GEMM_PREC_F32X3;
   const int64_t in_elem = c.family == GEMM_PREC_BF16 ? 2 : 4;
   const int64_t op_elem = c.family == GEMM_PREC_TF32 ? 4 : 2;
@@ -348,6 +352,12 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   // tensor map's third dimension steps R x ld); otherwise the pre-pass packs it.
   o.direct = !x3 && kcontig && ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0) &&
              (batch == 1 || stride == (int64_t)R * ld);
+  // A BF16 operand stored K x R (R contiguous) is read in place as MN-major
+  // tiles of whole 64-wide boxes when it is 16-byte aligned and batch-packed
+  // (K x ld per entry).
+  o.mn = !o.direct && c.family == GEMM_PREC_BF16 && !kcontig && mn_ext % tc::kMnBox == 0 &&
+         ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0) && (batch == 1 || stride == (int64_t)K * ld);
+  if (o.mn) o.direct = true;
   const int nseg = x3 ? 3 : 1;
   const int64_t Kp = x3 ? round_up(K, 64) : round_up(K, 16 / op_elem);
   o.ld = o.direct ? ld : nseg * Kp;
@@ -389,8 +399,9 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
   if (!status) return fail(cudaGetLastError());
 
   // op(A) rows are M, stored M x K when transA = 0; op(B)^T rows are N, stored N x K when transB = 1.
-  OperandPlan pa = plan_operand(c, g.A, g.lda, g.strideA, !g.transA, g.M, g.K, g.batch, /*hi,hi,lo*/ 0b100);
-  OperandPlan pb = plan_operand(c, g.B, g.ldb, g.strideB, g.transB != 0, g.N, g.K, g.batch, /*hi,lo,hi*/ 0b010);
+  const int b_ext = c.pair ? c.bn / 2 : c.bn;
+  OperandPlan pa = plan_operand(c, g.A, g.lda, g.strideA, !g.transA, g.M, g.K, g.batch, /*hi,hi,lo*/ 0b100, tc::kBM);
+  OperandPlan pb = plan_operand(c, g.B, g.ldb, g.strideB, g.transB != 0, g.N, g.K, g.batch, /*hi,lo,hi*/ 0b010, b_ext);
   char* scratch = nullptr;
   if (pa.bytes + pb.bytes > 0) {
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), pa.bytes + pb.bytes + 256, s);
@@ -411,9 +422,13 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
   gemm_status_t st = e == cudaSuccess ? GEMM_OK : fail(e);
   const int64_t Kop = c.family == GEMM_PREC_F32X3 ? 3 * round_up(g.K, 64) : g.K;
   CUtensorMap ma, mb;
-  if (st == GEMM_OK && (!make_map(&ma, Aop, op_bf16, Kop, g.M, pa.ld, g.batch, tc::kBM) ||
-                        !make_map(&mb, Bop, op_bf16, Kop, g.N, pb.ld, g.batch, c.pair ? c.bn / 2 : c.bn)))
-    st = GEMM_ERR_MISALIGNED;
+  const int bk = op_bf16 ? 64 : 32;
+  const bool map_ok = st == GEMM_OK &&
+                      (pa.mn ? make_map(&ma, Aop, op_bf16, g.M, Kop, pa.ld, g.batch, bk)
+                             : make_map(&ma, Aop, op_bf16, Kop, g.M, pa.ld, g.batch, tc::kBM)) &&
+                      (pb.mn ? make_map(&mb, Bop, op_bf16, g.N, Kop, pb.ld, g.batch, bk)
+                             : make_map(&mb, Bop, op_bf16, Kop, g.N, pb.ld, g.batch, b_ext));
+  if (st == GEMM_OK && !map_ok) st = GEMM_ERR_MISALIGNED;
   if (st == GEMM_OK) {
     tc::TcArgs a;
     a.M = g.M; a.N = g.N; a.K = (int)Kop; a.batch = g.batch;
@@ -427,6 +442,7 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
     a.group_m = std::max(1, std::min(a.tiles_m, kRasterGroup));
     a.alpha = g.alpha; a.beta = g.beta;
     a.C = g.C; a.ldc = g.ldc; a.strideC = g.strideC; a.vecC = g.vecC;
+    a.a_mn = pa.mn; a.b_mn = pb.mn;
     a.status = status;
     tc::GroupArgs none{nullptr, 0};
     e = fn(ma, mb, a, none, s);
@@ -508,8 +524,8 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
       return GEMM_ERR_INVALID_ARG;
     if (!q.A || !q.B || !q.C || q.ldc < q.N) return GEMM_ERR_INVALID_ARG;
     if (q.lda < (ta ? q.M : q.K) || q.ldb < (tb ? q.K : q.N)) return GEMM_ERR_INVALID_ARG;
-    pa[i] = plan_operand(c, q.A, q.lda, 0, !ta, (int)q.M, (int)q.K, 1, 0b100);
-    pb[i] = plan_operand(c, q.B, q.ldb, 0, tb != 0, (int)q.N, (int)q.K, 1, 0b010);
+    pa[i] = plan_operand(c, q.A, q.lda, 0, !ta, (int)q.M, (int)q.K, 1, 0b100, tc::kBM);
+    pb[i] = plan_operand(c, q.B, q.ldb, 0, tb != 0, (int)q.N, (int)q.K, 1, 0b010, c.pair ? c.bn / 2 : c.bn);
     if (!pa[i].direct) { offA[i] = scratch_bytes; scratch_bytes += round_up(pa[i].bytes, 256); }
     if (!pb[i].direct) { offB[i] = scratch_bytes; scratch_bytes += round_up(pb[i].bytes, 256); }
     const int tm = row_units(q.M, c.pair), tn = (int)((q.N + c.bn - 1) / c.bn);
@@ -557,8 +573,13 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
     const int64_t Kop = c.family == GEMM_PREC_F32X3 ? 3 * round_up(q.K, 64) : q.K;
     tc::GroupDesc& d = descs[r];
     std::memset(&d, 0, sizeof(d));
-    if (!make_map(&d.tmA, Aop, op_bf16, Kop, q.M > 0 ? q.M : 1, pa[i].ld, 1, tc::kBM) ||
-        !make_map(&d.tmB, Bop, op_bf16, Kop, q.N > 0 ? q.N : 1, pb[i].ld, 1, c.pair ? c.bn / 2 : c.bn)) {
+    const int64_t Mr = q.M > 0 ? q.M : 1, Nr = q.N > 0 ? q.N : 1;
+    const int bk = op_bf16 ? 64 : 32;
+    const bool ok_a = pa[i].mn ? make_map(&d.tmA, Aop, op_bf16, Mr, Kop, pa[i].ld, 1, bk)
+                               : make_map(&d.tmA, Aop, op_bf16, Kop, Mr, pa[i].ld, 1, tc::kBM);
+    const bool ok_b = pb[i].mn ? make_map(&d.tmB, Bop, op_bf16, Nr, Kop, pb[i].ld, 1, bk)
+                               : make_map(&d.tmB, Bop, op_bf16, Kop, Nr, pb[i].ld, 1, c.pair ? c.bn / 2 : c.bn);
+    if (!ok_a || !ok_b) {
       plan_free(p);
       return GEMM_ERR_MISALIGNED;
     }
@@ -571,6 +592,8 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
     d.tiles_n = (int)((q.N + c.bn - 1) / c.bn);
     d.tile_start = tile_start;
     d.vecC = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0);
+    d.a_mn = pa[i].mn;
+    d.b_mn = pb[i].mn;
     d.alpha = q.alpha;
     d.beta = q.beta;
     tile_start += d.tiles_m * d.tiles_n;

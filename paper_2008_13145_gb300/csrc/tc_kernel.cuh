@@ -1,7 +1,9 @@
 // Persistent warp-specialised tcgen05 GEMM for sm_103a.
 //
 // C[b] = alpha * A[b] * B[b]^T + beta * C[b] with A (M x K) and B (N x K)
-// both K-contiguous in global memory (BF16, or FP32 read as TF32).  Tiles of
+// K-contiguous in global memory (BF16, or FP32 read as TF32); a BF16 operand
+// may instead be MN-contiguous (A stored K x M, B stored K x N), in which case
+// it is staged as MN-major tiles and the MMA reads it transposed.  Tiles of
 // 128 x BN outputs are distributed over persistent CTAs; each CTA runs
 //   warp 4      : TMA producer (one elected lane) filling a STAGES-deep ring
 //                 of 128-byte-swizzled A/B slices, 128 bytes of K per slice;
@@ -31,6 +33,7 @@ struct TcArgs {
   float* C;
   int64_t ldc, strideC;
   int vecC;
+  int a_mn, b_mn;  // operand staged MN-major (BF16 only)
   int* status;
 };
 
@@ -42,6 +45,7 @@ struct alignas(64) GroupDesc {
   float* C;
   int64_t ldc;
   int M, N, k_blocks, tiles_m, tiles_n, tile_start, vecC;
+  int a_mn, b_mn;
   float alpha, beta;
 };
 
@@ -52,6 +56,7 @@ struct GroupArgs {
 
 constexpr int kThreads = 192;
 constexpr int kBM = 128;
+constexpr int kMnBox = 64;  // MN elements of one MN-major TMA box (a 128-byte BF16 row)
 
 template <int BN, int STAGES, bool TF32>
 struct TcCfg {
@@ -63,6 +68,13 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;     // 128, 256 or 512: power of two >= 32
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+  // MN-major staging: one TMA box is 64 MN elements (a 128-byte row) by BK K
+  // rows; the boxes of a slice lie MN-block after MN-block.  The 128-byte
+  // swizzle atom is 8 K rows of one box, so the MMA descriptor steps 8 K rows
+  // by 1 KB (SBO) and one MN block by MN_BOX_BYTES (LBO), and each MMA's K
+  // range starts KMMA rows (KMMA x 128 bytes) further on.
+  static constexpr int MN_BOX = kMnBox;
+  static constexpr int MN_BOX_BYTES = BK * 128;
 };
 
 __device__ __forceinline__ void tile_coords(const TcArgs& p, int tile, int& b, int& tm, int& tn) {
@@ -95,7 +107,7 @@ struct TileLoc {
   const CUtensorMap* mb;
   float* C;
   int64_t ldc, strideC;
-  int M, N, k_blocks, b, tm, tn, vecC;
+  int M, N, k_blocks, b, tm, tn, vecC, a_mn, b_mn;
   float alpha, beta;
 };
 
@@ -116,12 +128,13 @@ __device__ __forceinline__ TileLoc locate(const TcArgs& p, const GroupArgs& g, c
     const GroupDesc& d = g.descs[lo];
     const int t = tile - d.tile_start;
     L.ma = &d.tmA; L.mb = &d.tmB; L.C = d.C; L.ldc = d.ldc; L.strideC = 0;
-    L.M = d.M; L.N = d.N; L.k_blocks = d.k_blocks; L.b = 0; L.vecC = d.vecC;
+    L.M = d.M; L.N = d.N; L.k_blocks = d.k_blocks; L.b = 0; L.vecC = d.vecC; L.a_mn = d.a_mn; L.b_mn = d.b_mn;
     L.alpha = d.alpha; L.beta = d.beta;
     if (p.raster == 0) { L.tm = t % d.tiles_m; L.tn = t / d.tiles_m; } else { L.tn = t % d.tiles_n; L.tm = t / d.tiles_n; }
   } else {
     L.ma = ma; L.mb = mb; L.C = p.C; L.ldc = p.ldc; L.strideC = p.strideC;
     L.M = p.M; L.N = p.N; L.k_blocks = p.k_blocks; L.vecC = p.vecC; L.alpha = p.alpha; L.beta = p.beta;
+    L.a_mn = p.a_mn; L.b_mn = p.b_mn;
     tile_coords(p, tile, L.b, L.tm, L.tn);
   }
   if (PAIR) L.tm = 2 * L.tm + rank;
@@ -209,8 +222,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!(ok = mbar_wait(&empty_bar[stage], phase ^ 1, p.status, kStatusTimeoutEmpty))) break;
           uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
           mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
-          tma_load_3d(sa, L.ma, &full_bar[stage], kb * Cfg::BK, L.tm * kBM, L.b);
-          if constexpr (PAIR) {
+          if (!TF32 && L.a_mn) {
+#pragma unroll
+            for (int j = 0; j < kBM / Cfg::MN_BOX; ++j)
+              tma_load_3d(sa + j * Cfg::MN_BOX_BYTES, L.ma, &full_bar[stage], L.tm * kBM + j * Cfg::MN_BOX,
+                          kb * Cfg::BK, L.b);
+          } else {
+            tma_load_3d(sa, L.ma, &full_bar[stage], kb * Cfg::BK, L.tm * kBM, L.b);
+          }
+          if (!TF32 && L.b_mn) {
+            // This CTA's boxes of the slice: all BN / 64, or its half of them in a pair.
+            constexpr int NB = (PAIR ? BN / 2 : BN) / Cfg::MN_BOX;
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj) {
+              const int j = (PAIR ? rank * NB : 0) + jj;
+              uint8_t* dst = sa + Cfg::A_BYTES + j * Cfg::MN_BOX_BYTES;
+              if constexpr (PAIR)
+                tma_load_3d_mcast(dst, L.mb, &full_bar[stage], L.tn * BN + j * Cfg::MN_BOX, kb * Cfg::BK, L.b,
+                                  (uint16_t)0x3);
+              else
+                tma_load_3d(dst, L.mb, &full_bar[stage], L.tn * BN + j * Cfg::MN_BOX, kb * Cfg::BK, L.b);
+            }
+          } else if constexpr (PAIR) {
             tma_load_3d_mcast(sa + Cfg::A_BYTES + rank * (Cfg::B_BYTES / 2), L.mb, &full_bar[stage], kb * Cfg::BK,
                               L.tn * BN + rank * (BN / 2), L.b, (uint16_t)0x3);
           } else {
@@ -236,14 +269,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA issuer
     if (elect_one()) {
-      constexpr uint32_t idesc = instr_desc<TF32>(kBM, BN, false, false);
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
       uint32_t acc_phase = 0;
       bool ok = true;
       for (int tile = unit0; tile < p.num_tiles && ok; tile += units) {
-        const int k_blocks = GROUPED ? locate<true, PAIR>(p, g, &tmA, &tmB, tile, rank).k_blocks : p.k_blocks;
+        int k_blocks = p.k_blocks, a_mn = p.a_mn, b_mn = p.b_mn;
+        if constexpr (GROUPED) {
+          const TileLoc L = locate<true, PAIR>(p, g, &tmA, &tmB, tile, rank);
+          k_blocks = L.k_blocks;
+          a_mn = L.a_mn;
+          b_mn = L.b_mn;
+        }
+        if constexpr (TF32) a_mn = b_mn = 0;
+        const uint32_t idesc = instr_desc<TF32>(kBM, BN, a_mn != 0, b_mn != 0);
+        // K-major: the next MMA's K range starts KMMA elements along the swizzled
+        // 128-byte row; MN-major: KMMA K rows further on, MN blocks MN_BOX_BYTES apart.
+        const uint32_t a_step = a_mn ? Cfg::KMMA * 128 : Cfg::KMMA * Cfg::ELEM;
+        const uint32_t b_step = b_mn ? Cfg::KMMA * 128 : Cfg::KMMA * Cfg::ELEM;
+        const uint32_t a_lbo = a_mn ? Cfg::MN_BOX_BYTES : 16;
+        const uint32_t b_lbo = b_mn ? Cfg::MN_BOX_BYTES : 16;
         if (!(ok = mbar_wait(&acce_bar[acc], acc_phase ^ 1, p.status, kStatusTimeoutAccEmpty))) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
@@ -254,9 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t b_addr = a_addr + Cfg::A_BYTES;
 #pragma unroll
           for (int k = 0; k < Cfg::BK / Cfg::KMMA; ++k) {
-            const uint32_t koff = (uint32_t)(k * Cfg::KMMA * Cfg::ELEM);  // bytes along the swizzled row
-            const uint64_t ad = smem_desc_sw128(a_addr + koff, 16, 1024);
-            const uint64_t bd = smem_desc_sw128(b_addr + koff, 16, 1024);
+            const uint64_t ad = smem_desc_sw128(a_addr + (uint32_t)k * a_step, a_lbo, 1024);
+            const uint64_t bd = smem_desc_sw128(b_addr + (uint32_t)k * b_step, b_lbo, 1024);
             mma<TF32>(d_tmem, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
           }
           // frees the slot (in both CTAs of a pair) once these MMAs have read it

@@ -78,6 +78,36 @@ def test_every_config_ragged(lib, torch, fam):
     assert ks.device_status() == 0
 
 
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("T", "T")])
+def test_bf16_mn_major_every_config(lib, torch, ta, tb):
+    """BF16 operands stored MN-contiguous (A as K x M, B as K x N) with 16-byte
+    aligned rows are read in place as MN-major tiles: all 18 configs (CTA pairs
+    with BN 64 take the pre-pass for B), two tiles plus a ragged tail in M and
+    N, K not a multiple of the slice, two batch entries, alpha and beta."""
+    ks = lib
+    bad = []
+    for cid in tc_ids(ks, "bf16"):
+        C, ref, den = run(ks, torch, cid, "bf16", wl.Shape(300, 333, 136, 2, ta, tb), -0.5, 0.25, seed=12)
+        err = og.error_ratio(C, ref, den)
+        if not err <= FAMILIES["bf16"][1]:
+            bad.append((cid, ks.config_params(cid), err))
+    assert not bad, bad
+    assert ks.device_status() == 0
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("T", "T")])
+def test_bf16_mn_major_integer_exact(lib, torch, ta, tb):
+    """Small integers are exact in BF16 and their sums in FP32, so reading an
+    MN-major operand transposed must give the FP64 product bit for bit, in a
+    single-CTA and a CTA-pair config."""
+    ks = lib
+    ids = tc_ids(ks, "bf16")
+    for cid in (ids[4], ids[17]):
+        C, ref, _ = run(ks, torch, cid, "bf16", wl.Shape(200, 260, 320, 2, ta, tb), 1.0, 1.0, seed=13,
+                        kind="integer", bound=16)
+        assert np.array_equal(C.astype(np.float64), ref), cid
+
+
 @pytest.mark.parametrize("fam", list(FAMILIES))
 @pytest.mark.parametrize("ta,tb", TRANS)
 def test_layouts_and_unaligned_ld(lib, torch, fam, ta, tb):
