@@ -5,11 +5,45 @@
 
 #include <array>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/kselect.h"
 
 namespace ks {
+
+// ------------------------------------------------------------------ programmatic dependent launch
+// The GEMM path's kernels are launched with programmatic stream serialisation:
+// a kernel may be scheduled while the previous kernel in the stream drains
+// (its launch and prologue overlap that tail), so it passes pdl_wait() before
+// its first access to global memory, which returns once the previous grid has
+// completed and its writes are visible (immediately when launched without the
+// attribute).  pdl_launch_dependents() lets the next kernel be scheduled as
+// soon as every CTA of this grid has run it; the next kernel still waits for
+// this grid to complete before touching memory.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch `kern` with programmatic stream serialisation (plus `extra`
+// attributes); only for kernels that call pdl_wait() before touching memory.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       const cudaLaunchAttribute* extra, int n_extra, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[4];
+  int n = 0;
+  for (int i = 0; i < n_extra && n < 3; ++i) attr[n++] = extra[i];
+  attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[n].val.programmaticStreamSerializationAllowed = 1;
+  ++n;
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ------------------------------------------------------------------ FP32 SIMT config space
 // id = ((((tm_i * 4 + tn_i) * 6 + wg_i) * 3 + bk_i) * 2 + staged); see kselect.h.

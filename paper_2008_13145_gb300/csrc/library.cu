@@ -232,6 +232,8 @@ static int split_for(int id, const GemmArgs& a, int* kchunk) {
 __global__ void split_reduce_kernel(const float* __restrict__ W, int64_t ldw, int S, int M, int N, int batch,
                                     float alpha, float beta, float* C, int64_t ldc, int64_t strideC, int vecC,
                                     const GemmArgs chk) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int n4 = (N + 3) / 4;
   const int64_t total = (int64_t)batch * M * n4;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -323,9 +325,8 @@ static gemm_status_t launch_split(int base, const GemmArgs& a, int splits, int k
   if (e == cudaSuccess) {
     const int64_t total = (int64_t)a.batch * a.M * ((a.N + 3) / 4);
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    split_reduce_kernel<<<grid, 256, 0, s>>>(static_cast<const float*>(w), ldw, splits, a.M, a.N, a.batch, a.alpha,
-                                              a.beta, a.C, a.ldc, a.strideC, a.vecC, chk);
-    e = cudaGetLastError();
+    e = launch_pdl(split_reduce_kernel, dim3(grid), dim3(256), 0, s, nullptr, 0, static_cast<const float*>(w), ldw,
+                   splits, a.M, a.N, a.batch, a.alpha, a.beta, a.C, a.ldc, a.strideC, a.vecC, chk);
   }
   cudaError_t ef = cudaFreeAsync(w, s);
   if (e == cudaSuccess) e = ef;

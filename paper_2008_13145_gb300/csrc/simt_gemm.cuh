@@ -342,6 +342,8 @@ __device__ __forceinline__ void store_slice_b(const float4 (&r)[Cfg::RB], const 
 template <class Cfg, bool SPLIT>
 __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
   constexpr int TM = Cfg::TM, TN = Cfg::TN, BK = Cfg::BK, CM = Cfg::CM, CN = Cfg::CN;
+  pdl_wait();
+  pdl_launch_dependents();
   const int tid = threadIdx.x;
   const int tx = tid % Cfg::WX, ty = tid / Cfg::WX;
   const int m0 = blockIdx.x * Cfg::BM, n0 = blockIdx.y * Cfg::BN;
@@ -511,8 +513,7 @@ cudaError_t launch_simt(const GemmArgs& a, cudaStream_t s) {
     }
   }
   dim3 grid((a.M + Cfg::BM - 1) / Cfg::BM, (a.N + Cfg::BN - 1) / Cfg::BN, SPLIT ? a.batch * a.splits : a.batch);
-  kern<<<grid, Cfg::T, Cfg::SMEM_BYTES, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, dim3(Cfg::T), Cfg::SMEM_BYTES, s, nullptr, 0, a);
 }
 
 // Resident CTAs per SM of the split instance of config ID on the current device (0 on error).

@@ -126,6 +126,8 @@ constexpr int kPrepWarps = 8;  // warps per pre-pass block; each takes 64 / kPre
 template <typename TIn, typename TOut, bool SPLIT>
 __device__ __forceinline__ void prep_tile(const PrepJob& j, int b, int tr, int tk) {
   __shared__ float tile[64][65];
+  pdl_wait();
+  pdl_launch_dependents();
   const int r0 = tr * 64, k0 = tk * 64, lane = threadIdx.x;
   const TIn* src = static_cast<const TIn*>(j.in) + (int64_t)b * j.in_stride;
   const bool k_fast = (j.ks == 1);
@@ -210,10 +212,10 @@ __global__ void prep_group_kernel(const PrepJob* jobs, int n_jobs) {
 
 cudaError_t launch_prep(int family, const PrepJob& j, int batch, cudaStream_t s) {
   dim3 block(32, kPrepWarps), grid((unsigned)j.tiles_k, (unsigned)j.tiles_r, (unsigned)batch);
-  if (family == GEMM_PREC_F32X3) prep_kernel<float, __nv_bfloat16, true><<<grid, block, 0, s>>>(j);
-  else if (family == GEMM_PREC_BF16) prep_kernel<__nv_bfloat16, __nv_bfloat16, false><<<grid, block, 0, s>>>(j);
-  else prep_kernel<float, float, false><<<grid, block, 0, s>>>(j);
-  return cudaGetLastError();
+  if (family == GEMM_PREC_F32X3) return launch_pdl(prep_kernel<float, __nv_bfloat16, true>, grid, block, 0, s, nullptr, 0, j);
+  if (family == GEMM_PREC_BF16)
+    return launch_pdl(prep_kernel<__nv_bfloat16, __nv_bfloat16, false>, grid, block, 0, s, nullptr, 0, j);
+  return launch_pdl(prep_kernel<float, float, false>, grid, block, 0, s, nullptr, 0, j);
 }
 
 // Both operands of one GEMM in a single launch: blocks [0, na) rewrite A, the
@@ -228,20 +230,24 @@ __global__ void prep_pair_kernel(const PrepJob ja, const PrepJob jb) {
 
 cudaError_t launch_prep_pair(int family, const PrepJob& ja, const PrepJob& jb, int batch, cudaStream_t s) {
   dim3 block(32, kPrepWarps), grid((unsigned)(ja.tiles_k * ja.tiles_r + jb.tiles_k * jb.tiles_r), 1, (unsigned)batch);
-  if (family == GEMM_PREC_F32X3) prep_pair_kernel<float, __nv_bfloat16, true><<<grid, block, 0, s>>>(ja, jb);
-  else if (family == GEMM_PREC_BF16) prep_pair_kernel<__nv_bfloat16, __nv_bfloat16, false><<<grid, block, 0, s>>>(ja, jb);
-  else prep_pair_kernel<float, float, false><<<grid, block, 0, s>>>(ja, jb);
-  return cudaGetLastError();
+  if (family == GEMM_PREC_F32X3)
+    return launch_pdl(prep_pair_kernel<float, __nv_bfloat16, true>, grid, block, 0, s, nullptr, 0, ja, jb);
+  if (family == GEMM_PREC_BF16)
+    return launch_pdl(prep_pair_kernel<__nv_bfloat16, __nv_bfloat16, false>, grid, block, 0, s, nullptr, 0, ja, jb);
+  return launch_pdl(prep_pair_kernel<float, float, false>, grid, block, 0, s, nullptr, 0, ja, jb);
 }
 
 cudaError_t launch_prep_group(int family, const PrepJob* jobs, int n_jobs, int blocks, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
   dim3 block(32, kPrepWarps);
-  if (family == GEMM_PREC_F32X3) prep_group_kernel<float, __nv_bfloat16, true><<<blocks, block, 0, s>>>(jobs, n_jobs);
-  else if (family == GEMM_PREC_BF16)
-    prep_group_kernel<__nv_bfloat16, __nv_bfloat16, false><<<blocks, block, 0, s>>>(jobs, n_jobs);
-  else prep_group_kernel<float, float, false><<<blocks, block, 0, s>>>(jobs, n_jobs);
-  return cudaGetLastError();
+  // The job table is written once when the plan is made, so reading it before
+  // the programmatic wait in prep_tile is safe.
+  if (family == GEMM_PREC_F32X3)
+    return launch_pdl(prep_group_kernel<float, __nv_bfloat16, true>, dim3(blocks), block, 0, s, nullptr, 0, jobs, n_jobs);
+  if (family == GEMM_PREC_BF16)
+    return launch_pdl(prep_group_kernel<__nv_bfloat16, __nv_bfloat16, false>, dim3(blocks), block, 0, s, nullptr, 0,
+                      jobs, n_jobs);
+  return launch_pdl(prep_group_kernel<float, float, false>, dim3(blocks), block, 0, s, nullptr, 0, jobs, n_jobs);
 }
 
 // ---------------------------------------------------------------- main kernel launch
@@ -289,8 +295,8 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc
     __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);
   }
   const int units = std::min(a.num_tiles, slots_cache[dev & 63]);
-  cfg.gridDim = dim3((unsigned)(PAIR ? 2 * units : units), 1, 1);
-  return cudaLaunchKernelEx(&cfg, kern, ma, mb, a, g);
+  return launch_pdl(kern, dim3((unsigned)(PAIR ? 2 * units : units), 1, 1), cfg.blockDim, cfg.dynamicSmemBytes, s,
+                    cfg.attrs, (int)cfg.numAttrs, ma, mb, a, g);
 }
 
 using TcLaunch = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const tc::TcArgs&, const tc::GroupArgs&,

@@ -209,6 +209,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (PAIR) cluster_sync();  // the peer's multicasts target barriers initialised above
   tc_fence_after();
   const uint32_t tmem_base = tmem_base_sh;
+  // The prologue above (barriers, TMEM, tensor-map prefetch) touches no global
+  // memory, so it may overlap the previous kernel's tail.
+  pdl_wait();
+  pdl_launch_dependents();
 
   if (warp == 4) {
     // ---------------------------------------------------------------- TMA producer
