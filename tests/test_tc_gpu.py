@@ -108,6 +108,23 @@ def test_bf16_mn_major_integer_exact(lib, torch, ta, tb):
         assert np.array_equal(C.astype(np.float64), ref), cid
 
 
+@pytest.mark.parametrize("ta,tb", TRANS)
+def test_x3_every_config_any_layout_odd_ld(lib, torch, ta, tb):
+    """Split-BF16 x3 in all 18 configs with odd leading dimensions (so the
+    pre-pass takes its unpaired loads), K not a multiple of the 64-wide slice,
+    ragged M and N tails and two batch entries."""
+    ks = lib
+    bad = []
+    for cid in tc_ids(ks, "f32x3"):
+        C, ref, den = run(ks, torch, cid, "f32x3", wl.Shape(300, 333, 137, 2, ta, tb), 0.75, -0.5, seed=14,
+                          ld_multiple=1)
+        err = og.error_ratio(C, ref, den)
+        if not err <= FAMILIES["f32x3"][1]:
+            bad.append((cid, ks.config_params(cid), err))
+    assert not bad, bad
+    assert ks.device_status() == 0
+
+
 @pytest.mark.parametrize("fam", list(FAMILIES))
 @pytest.mark.parametrize("ta,tb", TRANS)
 def test_layouts_and_unaligned_ld(lib, torch, fam, ta, tb):
