@@ -100,7 +100,8 @@ int* status_word() {
 // One rewrite job: out[b][r][seg * Kp + k] for r < R, k < Kp (zero for k >= K)
 // from the logical R x K operand whose element (r, k) of batch entry b sits at
 // in[b * in_stride + r * rs + k * ks].  Copy (nseg 1, same type) or x3 split
-// (FP32 in, BF16 out; bit s of `pattern` set = segment s holds lo, else hi).
+// (FP32 in, BF16 out, nseg 2: segment 0 holds hi, segment 1 lo, as bit s of
+// `pattern` set = segment s holds lo).
 struct PrepJob {
   const void* in;
   int64_t in_stride, rs, ks;
@@ -364,7 +365,7 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   o.mn = !o.direct && c.family == GEMM_PREC_BF16 && !kcontig && mn_ext % tc::kMnBox == 0 &&
          ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0) && (batch == 1 || stride == (int64_t)K * ld);
   if (o.mn) o.direct = true;
-  const int nseg = x3 ? 3 : 1;
+  const int nseg = x3 ? 2 : 1;
   const int64_t Kp = x3 ? round_up(K, 64) : round_up(K, 16 / op_elem);
   o.ld = o.direct ? ld : nseg * Kp;
   o.bytes = o.direct ? 0 : (int64_t)batch * R * o.ld * op_elem;
@@ -406,8 +407,8 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
 
   // op(A) rows are M, stored M x K when transA = 0; op(B)^T rows are N, stored N x K when transB = 1.
   const int b_ext = c.pair ? c.bn / 2 : c.bn;
-  OperandPlan pa = plan_operand(c, g.A, g.lda, g.strideA, !g.transA, g.M, g.K, g.batch, /*hi,hi,lo*/ 0b100, tc::kBM);
-  OperandPlan pb = plan_operand(c, g.B, g.ldb, g.strideB, g.transB != 0, g.N, g.K, g.batch, /*hi,lo,hi*/ 0b010, b_ext);
+  OperandPlan pa = plan_operand(c, g.A, g.lda, g.strideA, !g.transA, g.M, g.K, g.batch, /*hi,lo*/ 0b10, tc::kBM);
+  OperandPlan pb = plan_operand(c, g.B, g.ldb, g.strideB, g.transB != 0, g.N, g.K, g.batch, /*hi,lo*/ 0b10, b_ext);
   char* scratch = nullptr;
   if (pa.bytes + pb.bytes > 0) {
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), pa.bytes + pb.bytes + 256, s);
@@ -426,14 +427,17 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
     e = launch_prep(c.family, pb.job, g.batch, s);
   }
   gemm_status_t st = e == cudaSuccess ? GEMM_OK : fail(e);
-  const int64_t Kop = c.family == GEMM_PREC_F32X3 ? 3 * round_up(g.K, 64) : g.K;
+  // x3: the K' loop covers 3 segments of round_up(K, 64); the operands hold 2.
+  const bool x3 = c.family == GEMM_PREC_F32X3;
+  const int64_t Kop = x3 ? 3 * round_up(g.K, 64) : g.K;
+  const int64_t Kmap = x3 ? 2 * round_up(g.K, 64) : g.K;
   CUtensorMap ma, mb;
   const int bk = op_bf16 ? 64 : 32;
   const bool map_ok = st == GEMM_OK &&
-                      (pa.mn ? make_map(&ma, Aop, op_bf16, g.M, Kop, pa.ld, g.batch, bk)
-                             : make_map(&ma, Aop, op_bf16, Kop, g.M, pa.ld, g.batch, tc::kBM)) &&
-                      (pb.mn ? make_map(&mb, Bop, op_bf16, g.N, Kop, pb.ld, g.batch, bk)
-                             : make_map(&mb, Bop, op_bf16, Kop, g.N, pb.ld, g.batch, b_ext));
+                      (pa.mn ? make_map(&ma, Aop, op_bf16, g.M, Kmap, pa.ld, g.batch, bk)
+                             : make_map(&ma, Aop, op_bf16, Kmap, g.M, pa.ld, g.batch, tc::kBM)) &&
+                      (pb.mn ? make_map(&mb, Bop, op_bf16, g.N, Kmap, pb.ld, g.batch, bk)
+                             : make_map(&mb, Bop, op_bf16, Kmap, g.N, pb.ld, g.batch, b_ext));
   if (st == GEMM_OK && !map_ok) st = GEMM_ERR_MISALIGNED;
   if (st == GEMM_OK) {
     tc::TcArgs a;
@@ -449,6 +453,7 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
     a.alpha = g.alpha; a.beta = g.beta;
     a.C = g.C; a.ldc = g.ldc; a.strideC = g.strideC; a.vecC = g.vecC;
     a.a_mn = pa.mn; a.b_mn = pb.mn;
+    a.seg_blocks = x3 ? (int)(round_up(g.K, 64) / 64) : 0;
     a.status = status;
     tc::GroupArgs none{nullptr, 0};
     e = fn(ma, mb, a, none, s);
@@ -530,8 +535,8 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
       return GEMM_ERR_INVALID_ARG;
     if (!q.A || !q.B || !q.C || q.ldc < q.N) return GEMM_ERR_INVALID_ARG;
     if (q.lda < (ta ? q.M : q.K) || q.ldb < (tb ? q.K : q.N)) return GEMM_ERR_INVALID_ARG;
-    pa[i] = plan_operand(c, q.A, q.lda, 0, !ta, (int)q.M, (int)q.K, 1, 0b100, tc::kBM);
-    pb[i] = plan_operand(c, q.B, q.ldb, 0, tb != 0, (int)q.N, (int)q.K, 1, 0b010, c.pair ? c.bn / 2 : c.bn);
+    pa[i] = plan_operand(c, q.A, q.lda, 0, !ta, (int)q.M, (int)q.K, 1, /*hi,lo*/ 0b10, tc::kBM);
+    pb[i] = plan_operand(c, q.B, q.ldb, 0, tb != 0, (int)q.N, (int)q.K, 1, /*hi,lo*/ 0b10, c.pair ? c.bn / 2 : c.bn);
     if (!pa[i].direct) { offA[i] = scratch_bytes; scratch_bytes += round_up(pa[i].bytes, 256); }
     if (!pb[i].direct) { offB[i] = scratch_bytes; scratch_bytes += round_up(pb[i].bytes, 256); }
     const int tm = row_units(q.M, c.pair), tn = (int)((q.N + c.bn - 1) / c.bn);
@@ -576,15 +581,17 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
       blocks += pb[i].job.tiles_k * pb[i].job.tiles_r;
       jobs.push_back(pb[i].job);
     }
-    const int64_t Kop = c.family == GEMM_PREC_F32X3 ? 3 * round_up(q.K, 64) : q.K;
+    const bool x3 = c.family == GEMM_PREC_F32X3;
+    const int64_t Kop = x3 ? 3 * round_up(q.K, 64) : q.K;  // K' loop; the operands hold 2 segments
+    const int64_t Kmap = x3 ? 2 * round_up(q.K, 64) : q.K;
     tc::GroupDesc& d = descs[r];
     std::memset(&d, 0, sizeof(d));
     const int64_t Mr = q.M > 0 ? q.M : 1, Nr = q.N > 0 ? q.N : 1;
     const int bk = op_bf16 ? 64 : 32;
-    const bool ok_a = pa[i].mn ? make_map(&d.tmA, Aop, op_bf16, Mr, Kop, pa[i].ld, 1, bk)
-                               : make_map(&d.tmA, Aop, op_bf16, Kop, Mr, pa[i].ld, 1, tc::kBM);
-    const bool ok_b = pb[i].mn ? make_map(&d.tmB, Bop, op_bf16, Nr, Kop, pb[i].ld, 1, bk)
-                               : make_map(&d.tmB, Bop, op_bf16, Kop, Nr, pb[i].ld, 1, c.pair ? c.bn / 2 : c.bn);
+    const bool ok_a = pa[i].mn ? make_map(&d.tmA, Aop, op_bf16, Mr, Kmap, pa[i].ld, 1, bk)
+                               : make_map(&d.tmA, Aop, op_bf16, Kmap, Mr, pa[i].ld, 1, tc::kBM);
+    const bool ok_b = pb[i].mn ? make_map(&d.tmB, Bop, op_bf16, Nr, Kmap, pb[i].ld, 1, bk)
+                               : make_map(&d.tmB, Bop, op_bf16, Kmap, Nr, pb[i].ld, 1, c.pair ? c.bn / 2 : c.bn);
     if (!ok_a || !ok_b) {
       plan_free(p);
       return GEMM_ERR_MISALIGNED;
@@ -600,6 +607,7 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
     d.vecC = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0);
     d.a_mn = pa[i].mn;
     d.b_mn = pb[i].mn;
+    d.seg_blocks = x3 ? (int)(round_up(q.K, 64) / 64) : 0;
     d.alpha = q.alpha;
     d.beta = q.beta;
     tile_start += d.tiles_m * d.tiles_n;

@@ -34,6 +34,10 @@ struct TcArgs {
   int64_t ldc, strideC;
   int vecC;
   int a_mn, b_mn;  // operand staged MN-major (BF16 only)
+  // Split-BF16 x3: the operands hold [hi | lo] segments of seg_blocks K-slices
+  // each and the K' = 3 x segment loop reads A as hi, hi, lo and B as hi, lo,
+  // hi; 0 for the other families.
+  int seg_blocks;
   int* status;
 };
 
@@ -45,7 +49,7 @@ struct alignas(64) GroupDesc {
   float* C;
   int64_t ldc;
   int M, N, k_blocks, tiles_m, tiles_n, tile_start, vecC;
-  int a_mn, b_mn;
+  int a_mn, b_mn, seg_blocks;
   float alpha, beta;
 };
 
@@ -107,7 +111,7 @@ struct TileLoc {
   const CUtensorMap* mb;
   float* C;
   int64_t ldc, strideC;
-  int M, N, k_blocks, b, tm, tn, vecC, a_mn, b_mn;
+  int M, N, k_blocks, b, tm, tn, vecC, a_mn, b_mn, seg_blocks;
   float alpha, beta;
 };
 
@@ -129,12 +133,13 @@ __device__ __forceinline__ TileLoc locate(const TcArgs& p, const GroupArgs& g, c
     const int t = tile - d.tile_start;
     L.ma = &d.tmA; L.mb = &d.tmB; L.C = d.C; L.ldc = d.ldc; L.strideC = 0;
     L.M = d.M; L.N = d.N; L.k_blocks = d.k_blocks; L.b = 0; L.vecC = d.vecC; L.a_mn = d.a_mn; L.b_mn = d.b_mn;
+    L.seg_blocks = d.seg_blocks;
     L.alpha = d.alpha; L.beta = d.beta;
     if (p.raster == 0) { L.tm = t % d.tiles_m; L.tn = t / d.tiles_m; } else { L.tn = t % d.tiles_n; L.tm = t / d.tiles_n; }
   } else {
     L.ma = ma; L.mb = mb; L.C = p.C; L.ldc = p.ldc; L.strideC = p.strideC;
     L.M = p.M; L.N = p.N; L.k_blocks = p.k_blocks; L.vecC = p.vecC; L.alpha = p.alpha; L.beta = p.beta;
-    L.a_mn = p.a_mn; L.b_mn = p.b_mn;
+    L.a_mn = p.a_mn; L.b_mn = p.b_mn; L.seg_blocks = p.seg_blocks;
     tile_coords(p, tile, L.b, L.tm, L.tn);
   }
   if (PAIR) L.tm = 2 * L.tm + rank;
@@ -225,14 +230,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < L.k_blocks; ++kb) {
           if (!(ok = mbar_wait(&empty_bar[stage], phase ^ 1, p.status, kStatusTimeoutEmpty))) break;
           uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
+          // K coordinates of this slice in A and B (x3: segment g of the K'
+          // loop reads A's hi, hi, lo and B's hi, lo, hi segment).
+          int xa = kb * Cfg::BK, xb = kb * Cfg::BK;
+          if (!TF32 && L.seg_blocks > 0) {
+            const int g = kb / L.seg_blocks, kk = kb - g * L.seg_blocks;
+            xa = ((g == 2 ? L.seg_blocks : 0) + kk) * Cfg::BK;
+            xb = ((g == 1 ? L.seg_blocks : 0) + kk) * Cfg::BK;
+          }
           mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
           if (!TF32 && L.a_mn) {
 #pragma unroll
             for (int j = 0; j < kBM / Cfg::MN_BOX; ++j)
-              tma_load_3d(sa + j * Cfg::MN_BOX_BYTES, L.ma, &full_bar[stage], L.tm * kBM + j * Cfg::MN_BOX,
-                          kb * Cfg::BK, L.b);
+              tma_load_3d(sa + j * Cfg::MN_BOX_BYTES, L.ma, &full_bar[stage], L.tm * kBM + j * Cfg::MN_BOX, xa,
+                          L.b);
           } else {
-            tma_load_3d(sa, L.ma, &full_bar[stage], kb * Cfg::BK, L.tm * kBM, L.b);
+            tma_load_3d(sa, L.ma, &full_bar[stage], xa, L.tm * kBM, L.b);
           }
           if (!TF32 && L.b_mn) {
             // This CTA's boxes of the slice: all BN / 64, or its half of them in a pair.
@@ -242,16 +255,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int j = (PAIR ? rank * NB : 0) + jj;
               uint8_t* dst = sa + Cfg::A_BYTES + j * Cfg::MN_BOX_BYTES;
               if constexpr (PAIR)
-                tma_load_3d_mcast(dst, L.mb, &full_bar[stage], L.tn * BN + j * Cfg::MN_BOX, kb * Cfg::BK, L.b,
-                                  (uint16_t)0x3);
+                tma_load_3d_mcast(dst, L.mb, &full_bar[stage], L.tn * BN + j * Cfg::MN_BOX, xb, L.b, (uint16_t)0x3);
               else
-                tma_load_3d(dst, L.mb, &full_bar[stage], L.tn * BN + j * Cfg::MN_BOX, kb * Cfg::BK, L.b);
+                tma_load_3d(dst, L.mb, &full_bar[stage], L.tn * BN + j * Cfg::MN_BOX, xb, L.b);
             }
           } else if constexpr (PAIR) {
-            tma_load_3d_mcast(sa + Cfg::A_BYTES + rank * (Cfg::B_BYTES / 2), L.mb, &full_bar[stage], kb * Cfg::BK,
+            tma_load_3d_mcast(sa + Cfg::A_BYTES + rank * (Cfg::B_BYTES / 2), L.mb, &full_bar[stage], xb,
                               L.tn * BN + rank * (BN / 2), L.b, (uint16_t)0x3);
           } else {
-            tma_load_3d(sa + Cfg::A_BYTES, L.mb, &full_bar[stage], kb * Cfg::BK, L.tn * BN, L.b);
+            tma_load_3d(sa + Cfg::A_BYTES, L.mb, &full_bar[stage], xb, L.tn * BN, L.b);
           }
           if (++stage == STAGES) {
             stage = 0;
