@@ -279,18 +279,27 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc
   if (!(__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & bit)) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    int occ = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, tc::kThreads, Cfg::SMEM_BYTES);
+    // Resident CTAs per SM from the kernel's own resources: shared memory
+    // (plus the 1 KB the system reserves per CTA), registers and TMEM columns.
+    // The runtime's occupancy query reports one CTA per SM for these kernels
+    // whatever their size, while the SM runs as many as these resources allow.
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
+    int smem_sm = 0, sms = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    occ = std::min(occ, 512 / Cfg::TMEM_COLS);  // every resident CTA must fit in TMEM
-    int slots = std::max(occ, 1) * sms;
+    const int regs = (fa.numRegs + 7) / 8 * 8;
+    int occ = std::min(smem_sm / (Cfg::SMEM_BYTES + (int)fa.sharedSizeBytes + 1024), 65536 / (regs * tc::kThreads));
+    occ = std::max(1, std::min(occ, 512 / Cfg::TMEM_COLS));  // every resident CTA must fit in TMEM
+    int slots = occ * sms;
     if (PAIR) {
+      // The cluster query places one pair per two SMs; scale it by the CTAs per SM.
       int clusters = 0;
       cfg.gridDim = dim3(2 * sms, 1, 1);
       e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
       if (e != cudaSuccess) return e;
-      slots = std::max(1, std::min(clusters, slots / 2));  // in pairs
+      slots = std::max(1, std::min(clusters * occ, slots / 2));  // in pairs
     }
     slots_cache[dev & 63] = slots;
     __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);

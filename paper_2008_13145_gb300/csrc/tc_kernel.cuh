@@ -71,8 +71,8 @@ struct TcCfg {
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;     // 128, 256 or 512: power of two >= 32
-  // Epilogue staging: 32 rows x 32 FP32 columns per epilogue warp.
-  static constexpr int EPI_BYTES = 4 * 32 * 32 * 4;
+  // Epilogue staging: 32 rows x 16 FP32 columns per epilogue warp.
+  static constexpr int EPI_BYTES = 4 * 32 * 16 * 4;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
   // MN-major staging: one TMA box is 64 MN elements (a 128-byte row) by BK K
   // rows; the boxes of a slice lie MN-block after MN-block.  The 128-byte
@@ -150,47 +150,53 @@ __device__ __forceinline__ TileLoc locate(const TcArgs& p, const GroupArgs& g, c
 
 // Stores one 32 x 32 chunk of C (rows row0 + lane of this warp's 32-row
 // quadrant, columns n0 .. n0 + 31) from the registers of tcgen05.ld, where
-// lane t holds row t.  The chunk goes through this warp's 4 KB staging
-// buffer (128-byte rows, 16-byte pieces XOR-swizzled by row, so both passes
-// are free of bank conflicts) and is written back four rows per instruction,
-// each row a contiguous 128-byte run of C; beta != 0 reads C the same way.
+// lane t holds row t.  Each 16-column half goes through this warp's 2 KB
+// staging buffer (64-byte rows; the 16-byte piece q of row t sits at
+// (t & 1) * 4 + (q ^ ((t >> 1) & 3)) within its 128-byte bank line, so both
+// passes are free of bank conflicts) and is written back eight rows per
+// instruction, each row a contiguous 64-byte run of C; beta != 0 reads C the
+// same way.
 __device__ __forceinline__ void store_chunk32(const TileLoc& p, float* cbase, int row0, int n0, float* stage,
                                               const uint32_t (&r)[32], int lane) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    float4 v = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
-                           __uint_as_float(r[4 * q + 3]));
-    *reinterpret_cast<float4*>(stage + lane * 32 + ((q ^ (lane & 7)) << 2)) = v;
-  }
-  __syncwarp();
-  const int q = lane & 7, n = n0 + 4 * q;
-#pragma unroll 2
-  for (int i = 0; i < 8; ++i) {
-    const int rr = 4 * i + (lane >> 3), row = row0 + rr;
-    const float4 v = *reinterpret_cast<const float4*>(stage + rr * 32 + ((q ^ (rr & 7)) << 2));
-    if (row >= p.M || n >= p.N) continue;
-    float* crow = cbase + (int64_t)row * p.ldc;
-    if (p.vecC && n + 3 < p.N) {
-      float4 o = make_float4(p.alpha * v.x, p.alpha * v.y, p.alpha * v.z, p.alpha * v.w);
-      if (p.beta != 0.f) {
-        const float4 c = *reinterpret_cast<const float4*>(crow + n);
-        o.x = fmaf(p.beta, c.x, o.x); o.y = fmaf(p.beta, c.y, o.y);
-        o.z = fmaf(p.beta, c.z, o.z); o.w = fmaf(p.beta, c.w, o.w);
-      }
-      *reinterpret_cast<float4*>(crow + n) = o;
-    } else {
-      const float e4[4] = {v.x, v.y, v.z, v.w};
+  for (int h = 0; h < 2; ++h) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (n + e < p.N) {
-          float o = p.alpha * e4[e];
-          if (p.beta != 0.f) o = fmaf(p.beta, crow[n + e], o);
-          crow[n + e] = o;
+    for (int q = 0; q < 4; ++q) {
+      const int c = 16 * h + 4 * q;
+      const float4 v = make_float4(__uint_as_float(r[c]), __uint_as_float(r[c + 1]), __uint_as_float(r[c + 2]),
+                                   __uint_as_float(r[c + 3]));
+      *reinterpret_cast<float4*>(stage + lane * 16 + ((q ^ ((lane >> 1) & 3)) << 2)) = v;
+    }
+    __syncwarp();
+    const int q = lane & 3, n = n0 + 16 * h + 4 * q;
+#pragma unroll 2
+    for (int i = 0; i < 4; ++i) {
+      const int rr = 8 * i + (lane >> 2), row = row0 + rr;
+      const float4 v = *reinterpret_cast<const float4*>(stage + rr * 16 + ((q ^ ((rr >> 1) & 3)) << 2));
+      if (row >= p.M || n >= p.N) continue;
+      float* crow = cbase + (int64_t)row * p.ldc;
+      if (p.vecC && n + 3 < p.N) {
+        float4 o = make_float4(p.alpha * v.x, p.alpha * v.y, p.alpha * v.z, p.alpha * v.w);
+        if (p.beta != 0.f) {
+          const float4 c = *reinterpret_cast<const float4*>(crow + n);
+          o.x = fmaf(p.beta, c.x, o.x); o.y = fmaf(p.beta, c.y, o.y);
+          o.z = fmaf(p.beta, c.z, o.z); o.w = fmaf(p.beta, c.w, o.w);
+        }
+        *reinterpret_cast<float4*>(crow + n) = o;
+      } else {
+        const float e4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (n + e < p.N) {
+            float o = p.alpha * e4[e];
+            if (p.beta != 0.f) o = fmaf(p.beta, crow[n + e], o);
+            crow[n + e] = o;
+          }
         }
       }
     }
+    __syncwarp();  // the staging buffer is refilled by the next half
   }
-  __syncwarp();  // the staging buffer is refilled by the next chunk
 }
 
 // PAIR: the kernel runs in clusters of two CTAs that compute vertically
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const TileLoc L = locate<GROUPED, PAIR>(p, g, &tmA, &tmB, tile, rank);
       const int row0 = L.tm * kBM + warp * 32;
       float* cbase = L.C + (int64_t)L.b * L.strideC;
-      float* stage = reinterpret_cast<float*>(smem + STAGES * Cfg::STAGE_BYTES) + warp * 32 * 32;
+      float* stage = reinterpret_cast<float*>(smem + STAGES * Cfg::STAGE_BYTES) + warp * 32 * 16;
       const uint32_t tbase = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
