@@ -280,17 +280,19 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     // Resident CTAs per SM from the kernel's own resources: shared memory
-    // (plus the 1 KB the system reserves per CTA), registers and TMEM columns.
+    // (plus what the system reserves per CTA), registers and TMEM columns.
     // The runtime's occupancy query reports one CTA per SM for these kernels
     // whatever their size, while the SM runs as many as these resources allow.
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
-    int smem_sm = 0, sms = 0;
+    int smem_sm = 0, sms = 0, reserved = 0, regs_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     const int regs = (fa.numRegs + 7) / 8 * 8;
-    int occ = std::min(smem_sm / (Cfg::SMEM_BYTES + (int)fa.sharedSizeBytes + 1024), 65536 / (regs * tc::kThreads));
+    int occ = std::min(smem_sm / (Cfg::SMEM_BYTES + (int)fa.sharedSizeBytes + reserved), regs_sm / (regs * tc::kThreads));
     occ = std::max(1, std::min(occ, 512 / Cfg::TMEM_COLS));  // every resident CTA must fit in TMEM
     int slots = occ * sms;
     if (PAIR) {
