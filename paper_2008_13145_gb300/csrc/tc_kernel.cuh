@@ -42,8 +42,9 @@ struct TcArgs {
 };
 
 // One problem of a grouped launch, in device memory: its two tensor maps
-// (64-byte aligned, as TMA requires), its C, and its first global tile index.
-struct alignas(64) GroupDesc {
+// (128-byte aligned by their type, beyond the 64 bytes TMA requires), its C,
+// and its first global tile index.
+struct alignas(128) GroupDesc {
   CUtensorMap tmA;
   CUtensorMap tmB;
   float* C;
