@@ -85,7 +85,10 @@ gemm_status_t kselect_debug_shrink_extents(int64_t a_bytes, int64_t b_bytes, int
  * (BN slot * 3 + stage slot) * 2 + pair) use a 128 x BN tile per CTA with BN in
  * {64,128,256}, a shared-memory ring of {2,3,4} stages, and either one CTA per
  * tile or a cluster of two CTAs on vertically adjacent tiles that share the B
- * slice by TMA multicast: 18 configs per family.
+ * slice by TMA multicast: 18 configs per family.  Operands are read in place by
+ * TMA when K-contiguous (BF16 also when MN-contiguous), 16-byte aligned and
+ * batch-packed; others, and every F32X3 operand (split once into BF16 hi and
+ * lo parts), are first rewritten by a pre-pass kernel.
  *
  * Split-K kind (Section 6 describes comparison libraries whose kernels for
  * tall, skinny matrices compute partial results combined by a final
@@ -259,9 +262,10 @@ gemm_status_t gemm_with_config(int32_t config_id, char transA, char transB, int6
  * the global tile index with a fixed stride, mapping it to (problem, tile) by
  * binary search over the problems' first-tile offsets.  Per-problem TMA descriptors live in device
  * memory.  Problems use the row-major conventions above; K >= 1.  Operands
- * that are not K-contiguous (transA 'T', transB 'N'), not 16-byte aligned,
- * and every operand of the F32X3 family are first rewritten by one grouped
- * pre-pass launch into plan-owned scratch.
+ * the kernel cannot read in place (TF32 ones that are not K-contiguous, i.e.
+ * transA 'T' or transB 'N'; any not 16-byte aligned; every F32X3 operand) are
+ * first rewritten by one grouped pre-pass launch into plan-owned scratch; BF16
+ * operands are read in place in either storage order.
  *
  * A plan validates the problems, encodes their descriptors, uploads them and
  * allocates its scratch once (gemm_grouped_plan_create synchronises
