@@ -138,7 +138,7 @@ def _oracle_inputs(one):
 def cpu_oracle_sample(shapes, budget_s: float, nthreads: int):
     """FP64 oracle throughput on a bounded sample: the full product of batch
     entry 0 of the held-out shapes, in order, until the time budget is spent.
-    Returns (TFLOP/s, description)."""
+    Returns (TFLOP/s, description, seconds measured)."""
     from oracle import gemm as og
     og.build()
     flops, t_used, n_shapes = 0, 0.0, 0
@@ -153,7 +153,7 @@ def cpu_oracle_sample(shapes, budget_s: float, nthreads: int):
         if t_used >= budget_s:
             break
     return flops / t_used / 1e12, (f"full FP64 product of batch entry 0 of the first {n_shapes} held-out shapes "
-                                   f"({flops / 1e9:.1f} GFLOP in {t_used:.1f} s, {nthreads} threads)")
+                                   f"({flops / 1e9:.1f} GFLOP in {t_used:.1f} s, {nthreads} threads)"), t_used
 
 
 def cpu_details(nthreads: int) -> dict:
@@ -186,7 +186,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     shapes, _ = test_shapes()
-    steps, t_all, val = [], 0.0, None
+    steps, secs = [], []
     from oracle import gemm as og
     og.build()
     nthreads = og.max_threads()
@@ -194,17 +194,21 @@ def run_reference(args, ws, rank):
     # REF_TOTAL_S of oracle work (the per-step budget shrinks as K + W grows).
     budget = min(args.ref_budget, max(0.3, REF_TOTAL_S / (args.warmup + args.steps)))
     for s in range(args.warmup + args.steps):
-        v, desc = cpu_oracle_sample(shapes, budget, nthreads)
+        v, desc, t = cpu_oracle_sample(shapes, budget, nthreads)
         if s >= args.warmup:
             steps.append(v)
+            secs.append(t)
     val = statistics.median(steps)
-    # A step of the workload is every held-out shape; the sampled rate implies its time.
+    # Each step is a bounded sample of the workload; ms_per_step is the time a
+    # timed step took, and the whole step's time is what the sampled rate implies.
     full_flops = sum(sh.flops for sh in shapes)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": full_flops / (val * 1e12) * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(secs) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "kind": "fp64 triple-loop CPU oracle",
-                       "ms_per_step": "time of one whole step implied by the sampled throughput"},
+                       "step": f"a bounded sample of the workload (about {budget:.1f} s of oracle work)",
+                       "ms_per_step": "measured time of one sampled step (median over the timed steps)",
+                       "ms_per_full_step_implied": full_flops / (val * 1e12) * 1e3},
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": nthreads, "kind": "oracle", "sample": desc},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -361,6 +365,7 @@ def run_ours(args, ws, rank, local):
     e2e = job_throughput(ws, flops, args.steps, ms_e2e)
 
     tc = tc_families(args, ks, tune, shapes, te, bufs, stream, dev) if not args.no_tc else None
+    tc_large = tc_large_shapes(ks) if not args.no_tc else None
     grouped = grouped_launch(ks, tune) if not args.no_tc else None
     vgg16 = vgg16_inference(ks) if not args.no_tc else None
     c0 = single_gemm_256(ks, tune)
@@ -371,7 +376,7 @@ def run_ours(args, ws, rank, local):
     cpu = None
     if ws == 1 and not args.no_cpu:
         from oracle import gemm as og
-        v, desc = cpu_oracle_sample(shapes, args.ref_budget, og.max_threads())
+        v, desc, _ = cpu_oracle_sample(shapes, args.ref_budget, og.max_threads())
         cpu = {"value": v, "unit": "TFLOP/s", "cores": og.max_threads(), "kind": "oracle", "sample": desc,
                "details": cpu_details(og.max_threads())}
     clocks = clk.summary()
@@ -395,6 +400,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": e2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "selectors": selectors,
         "tc": tc,
+        "tc_large": tc_large,
         "grouped": grouped,
         "vgg16": vgg16,
         "single_gemm_256": c0,
@@ -486,6 +492,70 @@ def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
             out[name]["families_deployed"] = sorted({ks.family_of(c) for c in dep["config_ids"]})
         if fb is not bufs:
             del fb
+    return out
+
+
+def measured_peaks() -> tuple[float, str]:
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed in isolation: the
+    burst cuBLAS figure measured on the GB300s when the file is
+    present, else the recorded fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    return 1900.0, "fallback (1.9 PFLOP/s bf16 burst)"
+
+
+def tc_large_shapes(ks, n: int = 8192, reps: int = 10, warmup: int = 3):
+    """The tensor-core families on large shapes: n^3 NN and NT through gemm()
+    with each family's deployed handle (its decision tree picks the kernel),
+    CUDA-event timed over `reps` back-to-back launches after `warmup`; every
+    operand is 256 MB (FP32) or 128 MB (BF16), so the inputs exceed L2.  Each
+    line also gives the fastest of the family's configs on the same product
+    and the roofline fraction: BF16 against the measured dense BF16 peak, TF32
+    against that peak times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s),
+    split-BF16 x3 as delivered FP32-accurate flops against the BF16 peak / 3
+    (three BF16 products per product)."""
+    import torch
+    bf16_peak, src = measured_peaks()
+    peaks = {"bf16": bf16_peak, "tf32": bf16_peak * 1.1 / 2.25, "f32x3": bf16_peak / 3}
+    flops = 2.0 * n ** 3
+    A32 = torch.empty(n * n, device="cuda")
+    B32 = torch.empty(n * n, device="cuda")
+    ks.fill_uniform(A32, n, n, n, 1, 71)
+    ks.fill_uniform(B32, n, n, n, 1, 72)
+    C = torch.empty(n * n, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(run):
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"shape": f"{n}^3", "peak_source": src, "timing": f"{warmup} warm-up + {reps} timed back-to-back launches"}
+    for name, fam in (("bf16", ks.PREC_BF16), ("tf32", ks.PREC_TF32), ("f32x3", ks.PREC_F32X3)):
+        dpath = os.path.join(DEPLOY, f"{name}.json")
+        if not os.path.exists(dpath):
+            continue
+        h = ks.Handle(json.load(open(dpath)))
+        A, B = (A32.to(torch.bfloat16), B32.to(torch.bfloat16)) if fam == ks.PREC_BF16 else (A32, B32)
+        for tb in ("N", "T"):
+            ms = timed(lambda: ks.gemm(h, "N", tb, n, n, n, 1.0, A, n, B, n, 0.0, C, n, 1))
+            best_ms, best_id = min((timed(lambda c=c: ks.gemm_with_config(c, "N", tb, n, n, n, 1.0, A, n, B, n, 0.0,
+                                                                             C, n, 1)), c)
+                                   for c in ks.config_ids(fam))
+            tf = flops / (ms * 1e9)
+            out[f"{name}_N{tb}"] = {"value": tf, "unit": "TFLOP/s", "ms": ms,
+                                    "config": ks.select_kernel(h, n, n, n, 1),
+                                    "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks[name],
+                                                 "unit": "TFLOP/s", "frac": tf / peaks[name]},
+                                    "best_config": best_id, "best_value": flops / (best_ms * 1e9)}
+        del A, B
     return out
 
 

@@ -48,7 +48,9 @@ typedef enum {
 /* Kernel families (and precision classes of a handle).  F32: the FP32 SIMT family.  TF32: tcgen05 kind::tf32 on
  * FP32 storage.  BF16: tcgen05 kind::f16 on BF16 storage.  F32X3: FP32
  * storage split into BF16 hi/lo parts, three tcgen05 products accumulated in
- * FP32.  C is FP32 in every family, accumulation is FP32 in every family. */
+ * FP32 (for K < 64 three parts and six products, which keep FP32-level
+ * accuracy where few terms are summed).  C is FP32 in every family,
+ * accumulation is FP32 in every family. */
 typedef enum {
   GEMM_PREC_F32 = 0,
   GEMM_PREC_TF32 = 1,
@@ -82,10 +84,10 @@ gemm_status_t kselect_debug_shrink_extents(int64_t a_bytes, int64_t b_bytes, int
  * shape (WX along N, WY along M) in {8x8, 16x16, 32x8, 8x32, 16x8, 8x16}, the
  * K-step BK in {8,16,32} and shared-memory staging on/off: 576 configs, ids
  * 0..575.  Tensor-core families (ids 1000 + 100*(family-1) + index, index =
- * (BN slot * 3 + stage slot) * 2 + pair) use a 128 x BN tile per CTA with BN in
- * {64,128,256}, a shared-memory ring of {2,3,4} stages, and either one CTA per
- * tile or a cluster of two CTAs on vertically adjacent tiles that share the B
- * slice by TMA multicast: 18 configs per family.  Operands are read in place by
+ * (BN slot * 3 + stage slot) * 2) use a 128 x BN tile per CTA with BN in
+ * {64,128,256} and a shared-memory ring of {2,3,4} stages: 9 configs per family
+ * (the odd indexes are reserved and name no kernel: GEMM_ERR_NO_KERNEL).
+ * gemm_config_id(family, i) = 1000 + 100*(family-1) + 2*i.  Operands are read in place by
  * TMA when K-contiguous (BF16 also when MN-contiguous), 16-byte aligned and
  * batch-packed; others, and every F32X3 operand (split once into BF16 hi and
  * lo parts), are first rewritten by a pre-pass kernel.
@@ -106,7 +108,7 @@ gemm_status_t kselect_debug_shrink_extents(int64_t a_bytes, int64_t b_bytes, int
  *
  * gemm_config_params writes 8 integers:
  *   F32: {family=0, TM, TN, WX, WY, BK, staged, splitk (0 or 1)}
- *   TC : {family, BM=128, BN, BK (elements per 128-byte row), stages, pair (0 or 1), 0, 0}
+ *   TC : {family, BM=128, BN, BK (elements per 128-byte row), stages, 0, 0, 0}
  */
 int32_t gemm_config_count(int32_t precision);
 int32_t gemm_config_id(int32_t precision, int32_t index);
@@ -131,16 +133,22 @@ int32_t gemm_split_factor(int32_t config_id, int64_t M, int64_t N, int64_t K, in
 
 /* ---------------------------------------------------------------- deployment
  * Section 5: the deployed set (<= 16 configs of one family) and a decision
- * tree mapping (M, N, K, batch) to one of them, evaluated as nested ifs in the
+ * tree mapping the sizes to one of them, evaluated as nested ifs in the
  * launcher.  Node j is a leaf when feature < 0; otherwise sizes with
- * value(feature) <= threshold go to `left`, others to `right`.  Features:
- * 0 = M, 1 = N, 2 = K, 3 = batch.  A leaf's label indexes config_ids.
+ * value(feature) <= threshold go to `left`, others to `right`.  Features
+ * (GEMM_TREE_FEATURES of them, kselect_selector_features): 0 = M, 1 = N,
+ * 2 = K, 3 = batch, 4 = M * N * batch, the number of outputs.  The paper's
+ * tree reads the matrix sizes; the output count is one more function of them
+ * that a depth-limited tree cannot form from axis-aligned splits, and it is
+ * what sets how many output tiles there are to spread over the SMs (whether
+ * a split-K kernel pays).  A leaf's label indexes config_ids.
  * Optional MLP parameters (GEMM_MLP_PARAMS floats, layout W1 7x64, b1, W2
  * 64x64, b2, W3 64x8, b3) let select_kernels_batched rank the deployed set. */
 #define GEMM_MAX_DEPLOYED 16
 #define GEMM_MAX_TREE_NODES 65536
 #define GEMM_MAX_TREES 256
 #define GEMM_MLP_PARAMS 5192
+#define GEMM_TREE_FEATURES 5
 
 typedef struct {
   int32_t feature;
@@ -300,8 +308,45 @@ void gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
  * negative size). */
 int32_t gemm_grouped_select(gemm_handle_t handle, int32_t count, const gemm_problem_t* problems);
 
-/* One-shot form: plan, run, synchronise `stream`, release the plan. */
-gemm_status_t gemm_grouped(int32_t config_id, int32_t count, const gemm_problem_t* problems, void* stream);
+/* One-shot form with an explicit config: plan, run, synchronise `stream`,
+ * release the plan (allocates and synchronises: not for graph capture). */
+gemm_status_t gemm_grouped_with_config(int32_t config_id, int32_t count, const gemm_problem_t* problems,
+                                       void* stream);
+
+/* The library call for a group (Section 5: the selector runs inside the call,
+ * before the launch).  `handle` holds a group selector -- a deployment of
+ * grouped-launch configs whose tree reads the group features (see
+ * gemm_grouped_select), as written for each family by the group autotuner --
+ * and picks the tile configuration; `precision` is the class asked for:
+ * GEMM_PREC_TF32, GEMM_PREC_BF16 (BF16 operands), or GEMM_PREC_F32X3 /
+ * GEMM_PREC_F32 (FP32 operands at FP32-level accuracy, run by the split-BF16
+ * family).  A selected config of another family gives GEMM_ERR_NO_KERNEL.
+ *
+ * Asynchronous on `stream`, with no host synchronisation and no allocation
+ * once the handle's workspace on this device is large enough: the problems'
+ * descriptors and pre-pass jobs are encoded on the host and written into that
+ * workspace by small kernels that carry them as launch parameters, then the
+ * pre-pass (if any operand needs one) and the persistent grouped launch run.
+ * The call can therefore be captured in a CUDA graph; the graph holds the
+ * descriptors, and each replay rewrites them before its launch.  The
+ * workspace grows only outside a capture, on a call that needs more (that
+ * call allocates), or through gemm_grouped_reserve; a call under capture
+ * that would need to grow it, or that is the device's first tensor-core call,
+ * returns GEMM_ERR_UNSUPPORTED and enqueues nothing.  A workspace that was
+ * outgrown stays allocated until the handle is destroyed, so graphs captured
+ * before a growth stay valid; no graph holding this call may be replayed
+ * after its handle is destroyed.  Calls with one handle whose work overlaps
+ * on the GPU (different streams without ordering, or concurrent graph
+ * replays) share the workspace and race; calls ordered on one stream do not.
+ * Problem rules as for plans (K >= 1; A, B, C valid until the launch has run). */
+gemm_status_t gemm_grouped(gemm_handle_t handle, int32_t count, const gemm_problem_t* problems,
+                           int32_t precision, void* stream);
+
+/* Grows the handle's workspace on the current device to what gemm_grouped
+ * needs for this group (allocates when it grows), so that later calls whose
+ * groups need no more can be captured. */
+gemm_status_t gemm_grouped_reserve(gemm_handle_t handle, int32_t count, const gemm_problem_t* problems,
+                                   int32_t precision);
 
 /* Section 3.1 (data collection): warm-up launches, then timed repetitions.
  * Runs `warmup` untimed launches and one timed probe launch, then times one
@@ -309,12 +354,12 @@ gemm_status_t gemm_grouped(int32_t config_id, int32_t count, const gemm_problem_
  * probe time clamped to [min_reps, max_reps], and writes the mean
  * milliseconds per launch (the paper's total time over a number of
  * iterations).  alpha = 1, beta = 0.  Synchronises `stream`.  Inputs are
- * whatever the buffers hold. */
+ * whatever the buffers hold.  out_reps (may be NULL) receives R. */
 gemm_status_t gemm_benchmark(int32_t config_id, char transA, char transB, int64_t M, int64_t N,
                              int64_t K, const void* A_dev, int64_t lda, const void* B_dev,
                              int64_t ldb, float* C_dev, int64_t ldc, int64_t batch,
                              int32_t warmup, int32_t min_reps, int32_t max_reps,
-                             double min_total_ms, double* out_ms, void* stream);
+                             double min_total_ms, double* out_ms, int32_t* out_reps, void* stream);
 
 /* Section 3.1, over a configuration list on one set of sizes.  Pass 1 times
  * one warm launch of every config (a launch longer than 2 ms is its own
@@ -323,12 +368,17 @@ gemm_status_t gemm_benchmark(int32_t config_id, char transA, char transB, int64_
  * whose pass-1 time is <= refine_ratio x the fastest; the others keep their
  * pass-1 time.  out_ms[c] is the time per launch (0 when out_status[c] != 0;
  * configs that cannot run this request report their status and are skipped).
- * Stops at the first GEMM_ERR_CUDA, which it returns.  Synchronises `stream`. */
+ * Optional outputs (each may be NULL): out_probe_ms[c], the pass-1 time (0 when
+ * the config did not run), and out_reps[c], the launches averaged into
+ * out_ms[c]: 1 for a pass-1 time, R in [min_reps, max_reps] for a pass-2 run,
+ * 0 when the config did not run.  Stops at the first GEMM_ERR_CUDA, which it
+ * returns.  Synchronises `stream`. */
 gemm_status_t gemm_benchmark_configs(int32_t n_configs, const int32_t* config_ids, char transA, char transB,
                                      int64_t M, int64_t N, int64_t K, const void* A_dev, int64_t lda,
                                      const void* B_dev, int64_t ldb, float* C_dev, int64_t ldc, int64_t batch,
                                      int32_t warmup, int32_t min_reps, int32_t max_reps, double min_total_ms,
-                                     double refine_ratio, double* out_ms, int32_t* out_status, void* stream);
+                                     double refine_ratio, double* out_ms, int32_t* out_status,
+                                     double* out_probe_ms, int32_t* out_reps, void* stream);
 
 /* ---------------------------------------------------------------- pruning pipeline (Sections 3.4, 4)
  * Section 3.4: per row of an n_rows x n_cols throughput table (row-major,
@@ -424,7 +474,8 @@ gemm_status_t kselect_knn(int32_t n_train, int32_t n_query, int32_t d, const flo
                           void* stream);
 
 /* Section 4.1 "Decision tree" pruning (host): a multi-output regression tree
- * from the sizes (features, n x 4 doubles: M, N, K, batch) to the normalised
+ * from the sizes (features, n x GEMM_TREE_FEATURES doubles as
+ * kselect_selector_features writes them) to the normalised
  * performance vectors Y (n x d floats, host), grown best-first to at most
  * max_leaves leaves: the leaf whose best split (features in order, midpoint
  * thresholds ascending, first best kept) removes the most squared error is
@@ -440,17 +491,32 @@ gemm_status_t kselect_tree_regress(int32_t n, int32_t d, const double* features,
 
 /* Section 5.1 classifier comparison (host): one random-forest tree -- the CART
  * of kselect_tree_train, except that node j (depth-first preorder) may split
- * only on max_features of the 4 features: the first max_features entries of
- * the permutation (0, 1, 2, 3) after partial Fisher-Yates steps t = 0, 1, ...
- * that swap entry t with entry t + draws[4 j + t] mod (4 - t); it becomes a
- * leaf when none of them splits it.  draws: 4 x max_nodes uint32 (host),
- * ignored when max_features == 4. */
+ * only on max_features of the F = GEMM_TREE_FEATURES features: the first
+ * max_features entries of the permutation (0, 1, ..., F - 1) after partial
+ * Fisher-Yates steps t = 0, 1, ... that swap entry t with entry
+ * t + draws[F j + t] mod (F - t); it becomes a leaf when none of them splits
+ * it.  draws: F x max_nodes uint32 (host), ignored when max_features == F. */
 gemm_status_t kselect_tree_train_rf(int32_t n, const double* features, const int32_t* labels, int32_t n_classes,
                                     int32_t max_depth, int32_t min_leaf, int32_t max_features, const uint32_t* draws,
                                     gemm_tree_node_t* out_nodes, int32_t max_nodes, int32_t* out_n_nodes);
 
-/* Section 5.1 (host): CART classification tree on features (n x 4 doubles:
- * M, N, K, batch) and labels (n, in [0, n_classes)).  Gini impurity with the
+/* Section 5.1 (host): the selector's feature rows of n sizes (sizes: n rows
+ * of M, N, K, batch) as the tree reads them: features_out, n x
+ * GEMM_TREE_FEATURES doubles (M, N, K, batch, M * N * batch).  INVALID_ARG on
+ * null pointers, n < 0 or a negative size. */
+gemm_status_t kselect_selector_features(int32_t n, const int64_t* sizes, double* features_out);
+
+/* Section 5.1 (host): the training label of each size, the index j (into
+ * cols, 0..n_sel-1) of its best deployed configuration, perf[row, cols[j]]
+ * largest, lowest j on ties (perf: n_rows x n_cols doubles, row-major;
+ * cols: n_sel column indexes).  INVALID_ARG on null pointers, sizes < 1, a
+ * column outside [0, n_cols) or a NaN throughput. */
+gemm_status_t kselect_best_labels(int32_t n_rows, int32_t n_cols, const double* perf, int32_t n_sel,
+                                  const int32_t* cols, int32_t* labels_out);
+
+/* Section 5.1 (host): CART classification tree on features (n x
+ * GEMM_TREE_FEATURES doubles, kselect_selector_features) and labels (n, in
+ * [0, n_classes)).  Gini impurity with the
  * class sum in class order; thresholds at midpoints of consecutive distinct
  * values; features in order, thresholds ascending, first best split kept; a
  * node is a leaf when pure, at max_depth (< 0: unlimited) or without a split

@@ -307,6 +307,31 @@ def best_split(F: np.ndarray, y: np.ndarray, n_classes: int, min_leaf: int, feat
     return best
 
 
+def selector_features(sizes) -> np.ndarray:
+    """Section 5.1: the classifier maps the matrix sizes to a deployed kernel.
+    Its feature row here is the sizes and the number of outputs, (M, N, K,
+    batch, M * N * batch): one more function of the sizes, which a
+    depth-limited tree of axis-aligned splits cannot form (a reading of
+    "matrix sizes").  sizes: n x 4 (M, N, K, batch)."""
+    s = np.asarray(sizes, np.float64).reshape(-1, 4)
+    return np.column_stack([s, s[:, 0] * s[:, 1] * s[:, 3]])
+
+
+def best_labels(perf: np.ndarray, cols) -> np.ndarray:
+    """Section 5.1: each training size is labelled with the deployed kernel
+    that ran it fastest -- the position j in ``cols`` of the largest
+    perf[i, cols[j]], the first such j on ties."""
+    perf = np.asarray(perf, np.float64)
+    out = np.empty(perf.shape[0], np.int64)
+    for i in range(perf.shape[0]):
+        best = 0
+        for j in range(len(cols)):
+            if perf[i, cols[j]] > perf[i, cols[best]]:
+                best = j
+        out[i] = best
+    return out
+
+
 def feature_subset(draw_row: np.ndarray, n_features: int, m: int) -> list[int]:
     """The m features a random-forest node may split on: the first m entries of a
     partial Fisher-Yates shuffle of 0..n_features-1 in which step t swaps entry t

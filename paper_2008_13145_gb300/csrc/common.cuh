@@ -129,6 +129,16 @@ void set_last_cuda_error(cudaError_t e);
 
 // The library handle: an immutable deployment plus a per-device cache of the
 // MLP parameters (filled on first use by select_kernels_batched).
+// The selector's feature row of one size (Section 5.1 reads the sizes; the
+// fifth feature is the number of outputs, M * N * batch).
+inline void selector_features(int64_t M, int64_t N, int64_t K, int64_t batch, double f[GEMM_TREE_FEATURES]) {
+  f[0] = (double)M;
+  f[1] = (double)N;
+  f[2] = (double)K;
+  f[3] = (double)batch;
+  f[4] = (double)M * (double)N * (double)batch;
+}
+
 struct kselect_library {
   int precision;
   std::vector<int32_t> ids;
@@ -139,8 +149,17 @@ struct kselect_library {
   std::vector<int32_t> known_ids;
   std::mutex dev_mu;
   float* dev_mlp[64] = {nullptr};
+  // gemm_grouped's workspace per device (descriptors, pre-pass jobs and
+  // scratch); buffers it outgrew stay allocated until the handle is destroyed,
+  // because graphs captured earlier still name them.
+  char* dev_ws[64] = {nullptr};
+  int64_t dev_ws_bytes[64] = {0};
+  std::vector<char*> retired_ws;
   ~kselect_library() {
     for (float* p : dev_mlp)
       if (p) cudaFree(p);
+    for (char* p : dev_ws)
+      if (p) cudaFree(p);
+    for (char* p : retired_ws) cudaFree(p);
   }
 };

@@ -54,7 +54,8 @@ static int family_of(int id) {
   if (split_base_of(id) >= 0) return GEMM_PREC_F32;
   if (id >= kTcBase && id < kTcBase + 300) {
     int fam = (id - kTcBase) / 100, idx = (id - kTcBase) % 100;
-    if (idx < kTcConfigsPerFamily) return fam + 1;  // 1 TF32, 2 BF16, 3 F32X3
+    // 1 TF32, 2 BF16, 3 F32X3; odd indices are reserved slots without a kernel
+    if (idx < kTcConfigsPerFamily && idx % 2 == 0) return fam + 1;
   }
   return -1;
 }
@@ -443,14 +444,14 @@ gemm_status_t kselect_debug_shrink_extents(int64_t a_bytes, int64_t b_bytes, int
 
 int32_t gemm_config_count(int32_t precision) {
   if (precision == GEMM_PREC_F32) return kSimtConfigs + kSplitConfigs;
-  if (precision >= GEMM_PREC_TF32 && precision <= GEMM_PREC_F32X3) return kTcConfigsPerFamily;
+  if (precision >= GEMM_PREC_TF32 && precision <= GEMM_PREC_F32X3) return kTcConfigsPerFamily / 2;
   return GEMM_ERR_INVALID_ARG;
 }
 
 int32_t gemm_config_id(int32_t precision, int32_t index) {
   const int32_t n = gemm_config_count(precision);
   if (n < 0 || index < 0 || index >= n) return GEMM_ERR_INVALID_ARG;
-  if (precision != GEMM_PREC_F32) return kTcBase + 100 * (precision - 1) + index;
+  if (precision != GEMM_PREC_F32) return kTcBase + 100 * (precision - 1) + 2 * index;  // even slots only
   if (index < kSimtConfigs) return index;
   int j = index - kSimtConfigs;
   for (int b = 0; b < kSimtConfigs; ++b)
@@ -501,7 +502,7 @@ gemm_status_t gemm_library_create(const gemm_deployment_t* d, gemm_handle_t* out
       if (nd.feature < 0) {
         if (nd.label < 0 || nd.label >= d->n_configs) return GEMM_ERR_INVALID_ARG;
       } else {
-        if (nd.feature > 3 || !std::isfinite(nd.threshold)) return GEMM_ERR_INVALID_ARG;
+        if (nd.feature >= GEMM_TREE_FEATURES || !std::isfinite(nd.threshold)) return GEMM_ERR_INVALID_ARG;
         stack.push_back(nd.left);
         stack.push_back(nd.right);
       }
@@ -548,7 +549,8 @@ int32_t select_kernel(gemm_handle_t h, int64_t M, int64_t N, int64_t K, int64_t 
     if (it != h->known.end() && *it == key) return h->known_ids[it - h->known.begin()];
   }
   if (h->nodes.empty()) return h->ids[0];
-  const double f[4] = {(double)M, (double)N, (double)K, (double)batch};
+  double f[GEMM_TREE_FEATURES];
+  selector_features(M, N, K, batch, f);
   auto walk = [&](int j) -> int {  // leaf label of the tree rooted at j
     for (int steps = 0; steps <= (int)h->nodes.size(); ++steps) {
       const gemm_tree_node_t& nd = h->nodes[j];
@@ -806,9 +808,10 @@ gemm_status_t gemm_host_pipeline(gemm_handle_t h, int32_t count, const gemm_host
 gemm_status_t gemm_benchmark(int32_t id, char transA, char transB, int64_t M, int64_t N, int64_t K,
                              const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                              int64_t batch, int32_t warmup, int32_t min_reps, int32_t max_reps,
-                             double min_total_ms, double* out_ms, void* stream) {
+                             double min_total_ms, double* out_ms, int32_t* out_reps, void* stream) {
   if (!out_ms || warmup < 0 || min_reps < 1 || max_reps < min_reps) return GEMM_ERR_INVALID_ARG;
   *out_ms = 0.0;
+  if (out_reps) *out_reps = 0;
   if (family_of(id) < 0) return GEMM_ERR_NO_KERNEL;
   GemmArgs a;
   bool noop = false;
@@ -848,6 +851,7 @@ gemm_status_t gemm_benchmark(int32_t id, char transA, char transB, int64_t M, in
   float total = 0.f;
   cudaEventElapsedTime(&total, e0, e1);
   *out_ms = (double)total / reps;
+  if (out_reps) *out_reps = reps;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return GEMM_OK;

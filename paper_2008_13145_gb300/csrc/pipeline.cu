@@ -335,8 +335,9 @@ struct TreeBuilder {
   int n_classes, max_depth, min_leaf, max_nodes;
   std::vector<gemm_tree_node_t> nodes;
   bool overflow = false;
-  int max_features = 4;             // < 4: random-forest node feature subsets
-  const uint32_t* draws = nullptr;  // 4 per node, in node (preorder) order
+  static constexpr int kF = GEMM_TREE_FEATURES;
+  int max_features = kF;            // < kF: random-forest node feature subsets
+  const uint32_t* draws = nullptr;  // kF per node, in node (preorder) order
 
   // 1 - sum_c (cnt_c / n)^2, summed in class order.
   double gini(const std::vector<double>& cnt, double n) const {
@@ -364,14 +365,16 @@ struct TreeBuilder {
     if (counts[label] == n || (max_depth >= 0 && depth >= max_depth)) return me;
     // Features this node may split on: all, or the first max_features entries of a
     // partial Fisher-Yates shuffle driven by the node's draws, taken in order.
-    bool allowed[4] = {true, true, true, true};
-    if (max_features < 4) {
-      int perm[4] = {0, 1, 2, 3};
+    bool allowed[kF];
+    for (int f = 0; f < kF; ++f) allowed[f] = true;
+    if (max_features < kF) {
+      int perm[kF];
+      for (int f = 0; f < kF; ++f) perm[f] = f;
       for (int t = 0; t < max_features; ++t) {
-        const int j = t + (int)(draws[4 * (size_t)me + t] % (uint32_t)(4 - t));
+        const int j = t + (int)(draws[kF * (size_t)me + t] % (uint32_t)(kF - t));
         std::swap(perm[t], perm[j]);
       }
-      for (int f = 0; f < 4; ++f) allowed[f] = false;
+      for (int f = 0; f < kF; ++f) allowed[f] = false;
       for (int t = 0; t < max_features; ++t) allowed[perm[t]] = true;
     }
     // Best split: features in order, thresholds ascending, first best kept.
@@ -379,16 +382,16 @@ struct TreeBuilder {
     double bt = 0.0, bw = 0.0;
     std::vector<int> order(idx);
     std::vector<double> cl(n_classes), cr(n_classes);
-    for (int f = 0; f < 4; ++f) {
+    for (int f = 0; f < kF; ++f) {
       if (!allowed[f]) continue;
-      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return F[4 * a + f] < F[4 * b + f]; });
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return F[kF * a + f] < F[kF * b + f]; });
       std::fill(cl.begin(), cl.end(), 0.0);
       for (int c = 0; c < n_classes; ++c) cr[c] = counts[c];
       for (int p = 0; p + 1 < n; ++p) {
         const int c = y[order[p]];
         cl[c] += 1.0;
         cr[c] -= 1.0;
-        const double xa = F[4 * order[p] + f], xb = F[4 * order[p + 1] + f];
+        const double xa = F[kF * order[p] + f], xb = F[kF * order[p + 1] + f];
         if (!(xa < xb)) continue;
         const double nl = (double)(p + 1), nr = (double)(n - p - 1);
         if (nl < min_leaf || nr < min_leaf) continue;
@@ -402,7 +405,7 @@ struct TreeBuilder {
     }
     if (bf < 0) return me;
     std::vector<int> left, right;
-    for (int i : idx) (F[4 * i + bf] <= bt ? left : right).push_back(i);
+    for (int i : idx) (F[kF * i + bf] <= bt ? left : right).push_back(i);
     nodes[me].feature = bf;
     nodes[me].threshold = bt;
     const int l = grow(left, depth + 1);
@@ -424,6 +427,7 @@ struct TreeBuilder {
 constexpr double kGainTie = 1e-9;
 
 struct RegressionTree {
+  static constexpr int kF = GEMM_TREE_FEATURES;
   const double* F;
   const float* Y;
   int d;
@@ -457,13 +461,13 @@ struct RegressionTree {
       for (int j = 0; j < d; ++j) mean[j] += Y[(size_t)i * d + j];
     for (int j = 0; j < d; ++j) mean[j] /= n;
     std::vector<int> order(idx);
-    for (int f = 0; f < 4; ++f) {
-      std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return F[4 * a + f] < F[4 * c + f]; });
+    for (int f = 0; f < kF; ++f) {
+      std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return F[kF * a + f] < F[kF * c + f]; });
       std::fill(L.begin(), L.end(), 0.0);
       for (int p = 0; p + 1 < n; ++p) {
         const float* row = Y + (size_t)order[p] * d;
         for (int j = 0; j < d; ++j) L[j] += (double)row[j] - mean[j];
-        const double xa = F[4 * order[p] + f], xb = F[4 * order[p + 1] + f];
+        const double xa = F[kF * order[p] + f], xb = F[kF * order[p + 1] + f];
         if (!(xa < xb)) continue;
         double s2 = 0.0;
         for (int j = 0; j < d; ++j) s2 += L[j] * L[j];
@@ -661,17 +665,18 @@ gemm_status_t kselect_top_n(int32_t n_rows, int32_t n_cols, const float* perf, i
 }
 
 // Section 5.1 classifier comparison: one random-forest tree (CART restricted to
-// per-node feature subsets drawn from `draws`, 4 uint32 per node).
+// per-node feature subsets drawn from `draws`, GEMM_TREE_FEATURES uint32 per node).
 gemm_status_t kselect_tree_train_rf(int32_t n, const double* features, const int32_t* labels, int32_t n_classes,
                                     int32_t max_depth, int32_t min_leaf, int32_t max_features, const uint32_t* draws,
                                     gemm_tree_node_t* out_nodes, int32_t max_nodes, int32_t* out_n_nodes) {
   if (n < 1 || !features || !labels || n_classes < 1 || min_leaf < 1 || !out_nodes || max_nodes < 1 ||
-      !out_n_nodes || max_features < 1 || max_features > 4 || (max_features < 4 && !draws))
+      !out_n_nodes || max_features < 1 || max_features > GEMM_TREE_FEATURES ||
+      (max_features < GEMM_TREE_FEATURES && !draws))
     return GEMM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
     if (labels[i] < 0 || labels[i] >= n_classes) return GEMM_ERR_INVALID_ARG;
-    for (int f = 0; f < 4; ++f)
-      if (!std::isfinite(features[4 * i + f])) return GEMM_ERR_INVALID_ARG;
+    for (int f = 0; f < GEMM_TREE_FEATURES; ++f)
+      if (!std::isfinite(features[GEMM_TREE_FEATURES * i + f])) return GEMM_ERR_INVALID_ARG;
   }
   TreeBuilder tb{features, labels, n_classes, max_depth, min_leaf, max_nodes, {}, false, max_features, draws};
   std::vector<int> idx(n);
@@ -683,7 +688,36 @@ gemm_status_t kselect_tree_train_rf(int32_t n, const double* features, const int
   return GEMM_OK;
 }
 
-// Section 5.1: CART classifier from (M, N, K, batch) to a deployed kernel.
+// Section 5.1: the selector's feature rows of a list of sizes.
+gemm_status_t kselect_selector_features(int32_t n, const int64_t* sizes, double* out) {
+  if (n < 0 || (n > 0 && (!sizes || !out))) return GEMM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int64_t* r = sizes + 4 * (size_t)i;
+    if (r[0] < 0 || r[1] < 0 || r[2] < 0 || r[3] < 0) return GEMM_ERR_INVALID_ARG;
+    selector_features(r[0], r[1], r[2], r[3], out + GEMM_TREE_FEATURES * (size_t)i);
+  }
+  return GEMM_OK;
+}
+
+// Section 5.1: each training size is labelled with its best deployed kernel.
+gemm_status_t kselect_best_labels(int32_t n_rows, int32_t n_cols, const double* perf, int32_t n_sel,
+                                  const int32_t* cols, int32_t* labels_out) {
+  if (n_rows < 1 || n_cols < 1 || n_sel < 1 || !perf || !cols || !labels_out) return GEMM_ERR_INVALID_ARG;
+  for (int j = 0; j < n_sel; ++j)
+    if (cols[j] < 0 || cols[j] >= n_cols) return GEMM_ERR_INVALID_ARG;
+  for (int i = 0; i < n_rows; ++i) {
+    const double* row = perf + (size_t)i * n_cols;
+    int best = 0;
+    for (int j = 0; j < n_sel; ++j) {
+      if (std::isnan(row[cols[j]])) return GEMM_ERR_INVALID_ARG;
+      if (row[cols[j]] > row[cols[best]]) best = j;
+    }
+    labels_out[i] = best;
+  }
+  return GEMM_OK;
+}
+
+// Section 5.1: CART classifier from the sizes' feature rows to a deployed kernel.
 gemm_status_t kselect_tree_train(int32_t n, const double* features, const int32_t* labels, int32_t n_classes,
                                  int32_t max_depth, int32_t min_leaf, gemm_tree_node_t* out_nodes, int32_t max_nodes,
                                  int32_t* out_n_nodes) {
@@ -692,8 +726,8 @@ gemm_status_t kselect_tree_train(int32_t n, const double* features, const int32_
     return GEMM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
     if (labels[i] < 0 || labels[i] >= n_classes) return GEMM_ERR_INVALID_ARG;
-    for (int f = 0; f < 4; ++f)
-      if (!std::isfinite(features[4 * i + f])) return GEMM_ERR_INVALID_ARG;
+    for (int f = 0; f < GEMM_TREE_FEATURES; ++f)
+      if (!std::isfinite(features[GEMM_TREE_FEATURES * i + f])) return GEMM_ERR_INVALID_ARG;
   }
   TreeBuilder tb{features, labels, n_classes, max_depth, min_leaf, max_nodes, {}, false};
   std::vector<int> idx(n);
@@ -721,7 +755,7 @@ gemm_status_t kselect_tree_regress(int32_t n, int32_t d, const double* features,
                                    int32_t* labels_out, float* centres_out, int32_t* n_leaves_out) {
   if (n < 1 || d < 1 || !features || !Y || max_leaves < 1 || !labels_out || !centres_out || !n_leaves_out)
     return GEMM_ERR_INVALID_ARG;
-  for (int64_t i = 0; i < (int64_t)n * 4; ++i)
+  for (int64_t i = 0; i < (int64_t)n * GEMM_TREE_FEATURES; ++i)
     if (!std::isfinite(features[i])) return GEMM_ERR_INVALID_ARG;
   for (int64_t i = 0; i < (int64_t)n * d; ++i)
     if (!std::isfinite(Y[i])) return GEMM_ERR_INVALID_ARG;
@@ -739,7 +773,7 @@ gemm_status_t kselect_tree_regress(int32_t n, int32_t d, const double* features,
     if (pick < 0) break;
     const RegressionTree::Split sp = splits[pick];
     std::vector<int> left, right;
-    for (int i : leaves[pick]) (features[4 * i + sp.f] <= sp.thr ? left : right).push_back(i);
+    for (int i : leaves[pick]) (features[GEMM_TREE_FEATURES * i + sp.f] <= sp.thr ? left : right).push_back(i);
     leaves[pick] = std::move(left);
     leaves.push_back(std::move(right));
     splits[pick] = rt.best(leaves[pick]);

@@ -30,7 +30,8 @@ extern "C" gemm_status_t gemm_benchmark_configs(int32_t n_configs, const int32_t
                                                 int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                                                 int64_t batch, int32_t warmup, int32_t min_reps, int32_t max_reps,
                                                 double min_total_ms, double refine_ratio, double* out_ms,
-                                                int32_t* out_status, void* stream) {
+                                                int32_t* out_status, double* out_probe_ms, int32_t* out_reps,
+                                                void* stream) {
   if (n_configs < 0 || (n_configs > 0 && (!config_ids || !out_ms || !out_status))) return GEMM_ERR_INVALID_ARG;
   if (warmup < 0 || min_reps < 1 || max_reps < min_reps || refine_ratio < 1.0) return GEMM_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -46,6 +47,8 @@ extern "C" gemm_status_t gemm_benchmark_configs(int32_t n_configs, const int32_t
   // Pass 1: warm-up launches and one timed probe launch per configuration.
   for (int c = 0; c < n_configs && ret == GEMM_OK; ++c) {
     out_ms[c] = 0.0;
+    if (out_probe_ms) out_probe_ms[c] = 0.0;
+    if (out_reps) out_reps[c] = 0;
     bool noop = false;
     gemm_status_t st = make_launch_args(config_ids[c], transA, transB, M, N, K, 1.f, A, lda, B, ldb, 0.f, C, ldc,
                                         batch, &args[c], &noop);
@@ -72,6 +75,8 @@ extern "C" gemm_status_t gemm_benchmark_configs(int32_t n_configs, const int32_t
     out_status[c] = st;
     if (st == GEMM_OK) {
       out_ms[c] = ms;
+      if (out_probe_ms) out_probe_ms[c] = ms;
+      if (out_reps) out_reps[c] = 1;
       best = std::min(best, (double)ms);
     } else if (st == GEMM_ERR_CUDA) {
       ret = GEMM_ERR_CUDA;  // the context may be unusable: stop the sweep
@@ -95,11 +100,13 @@ extern "C" gemm_status_t gemm_benchmark_configs(int32_t n_configs, const int32_t
     }
     if (st != GEMM_OK) {
       out_status[c] = st;
+      out_ms[c] = 0.0;
       continue;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     out_ms[c] = (double)ms / reps;
+    if (out_reps) out_reps[c] = reps;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -6,17 +6,19 @@
 // other layouts, and operands whose rows are not 16-byte aligned, are first
 // rewritten K-contiguous by a tiled transpose pre-pass into scratch.  The x3
 // family splits each FP32 value x into hi = bf16(x) and lo = bf16(x - hi) in
-// the same pre-pass and lays K out as three segments, A' = [hi | hi | lo] and
-// B' = [hi | lo | hi], so one BF16 GEMM over K' = 3 K accumulates
-// hi*hi + hi*lo + lo*hi in FP32.
+// the same pre-pass and stores [hi | lo] per row; the kernel's K' = 3 K loop
+// reads the segment pairs (hi, hi), (hi, lo), (lo, hi), so one BF16 GEMM
+// accumulates hi*hi + hi*lo + lo*hi in FP32 (for K < 64, three parts and six
+// products: see split_plan).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <numeric>
 #include <cstring>
+#include <memory>
+#include <numeric>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -34,18 +36,48 @@ constexpr int kTcStages[3] = {2, 3, 4};
 struct TcConfig {
   int family;  // GEMM_PREC_TF32, GEMM_PREC_BF16, GEMM_PREC_F32X3
   int bn, stages;
-  int pair;    // 1: clusters of two CTAs sharing the B slice by multicast
 };
 
+// Index idx of a family is (BN slot * 3 + stage slot) * 2 + p; the slots with
+// p = 1 are reserved (no kernel), so a family has 9 valid configurations.
 bool decode(int id, TcConfig* c) {
   if (id < kTcBase) return false;
   const int fam = (id - kTcBase) / 100, idx = (id - kTcBase) % 100;
-  if (fam < 0 || fam > 2 || idx >= kTcConfigsPerFamily) return false;
+  if (fam < 0 || fam > 2 || idx >= kTcConfigsPerFamily || idx % 2 != 0) return false;
   c->family = fam + 1;
   c->bn = kTcBn[idx / 6];
   c->stages = kTcStages[(idx / 2) % 3];
-  c->pair = idx % 2;
   return true;
+}
+
+// ---------------------------------------------------------------- split-BF16 products (F32X3 family)
+// Each FP32 operand x is split into BF16 parts x = p0 + p1 (+ p2) + r, each
+// part the rounded remainder of the previous ones, and the K' loop runs one
+// K-segment per product of parts.  BF16 keeps 8 significant bits, so with two
+// parts the three products p0q0 + p0q1 + p1q0 drop terms of up to 3 * 2^-16 of
+// |xy| per product; summed over K products of uniform data these errors
+// average out below 1e-5 of sum |xy| once K reaches a few tens, but not for
+// K of a few.  Below kSplit6MaxK the family therefore uses three parts and
+// the six products whose part indexes sum to at most 2, which drop terms
+// below about 4 * 2^-24 of |xy|: the FP32 level at every K.  Small-K products
+// are bound by memory and launch latency, so the extra products cost little.
+constexpr int64_t kSplit6MaxK = 64;
+constexpr int64_t kSplitSeg = 64;  // K elements per segment are padded to a whole 128-byte slice
+
+struct SplitPlan {
+  int nseg;     // parts per operand (segments stored)
+  int nprod;    // products (segments of the K' loop)
+  int seg_map;  // product g: A part at bits [2g, 2g + 2), B part at bits [16 + 2g, 16 + 2g + 2)
+};
+
+SplitPlan split_plan(int64_t K) {
+  static constexpr int a3[3] = {0, 0, 1}, b3[3] = {0, 1, 0};
+  static constexpr int a6[6] = {0, 0, 1, 0, 1, 2}, b6[6] = {0, 1, 0, 2, 1, 0};
+  const bool six = K < kSplit6MaxK;
+  SplitPlan p{six ? 3 : 2, six ? 6 : 3, 0};
+  for (int g = 0; g < p.nprod; ++g)
+    p.seg_map |= ((six ? a6[g] : a3[g]) << (2 * g)) | ((six ? b6[g] : b3[g]) << (16 + 2 * g));
+  return p;
 }
 
 // ---------------------------------------------------------------- driver entry point for TMA descriptors
@@ -81,13 +113,15 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t K, int64_t ro
 }
 
 // ---------------------------------------------------------------- device status word (sticky)
-int* status_word() {
+// One int per device, made by the device's first tensor-core call; with
+// create = false a device that has none yet gets nullptr (nothing allocated).
+int* status_word_of(bool create) {
   static int* words[64] = {nullptr};
   static std::mutex mu;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> g(mu);
-  if (!words[dev]) {
+  if (!words[dev] && create) {
     int* w = nullptr;
     if (cudaMalloc(&w, sizeof(int)) != cudaSuccess) return nullptr;
     if (cudaMemset(w, 0, sizeof(int)) != cudaSuccess) return nullptr;
@@ -96,18 +130,22 @@ int* status_word() {
   return words[dev];
 }
 
+int* status_word() { return status_word_of(true); }
+int* status_word_if_ready() { return status_word_of(false); }
+
 // ---------------------------------------------------------------- K-contiguous pre-pass
 // One rewrite job: out[b][r][seg * Kp + k] for r < R, k < Kp (zero for k >= K)
 // from the logical R x K operand whose element (r, k) of batch entry b sits at
-// in[b * in_stride + r * rs + k * ks].  Copy (nseg 1, same type) or x3 split
-// (FP32 in, BF16 out, nseg 2: segment 0 holds hi, segment 1 lo, as bit s of
-// `pattern` set = segment s holds lo).
+// in[b * in_stride + r * rs + k * ks].  Copy (nseg 1, same type) or BF16
+// split (FP32 in, BF16 out, nseg 2 or 3): segment 0 holds p0 = bf16(x) and
+// segment s the rounded remainder p_s = bf16(x - p0 - ... - p_{s-1}); every
+// remainder is exact in FP32.
 struct PrepJob {
   const void* in;
   int64_t in_stride, rs, ks;
   void* out;
   int64_t ld_out;
-  int R, K, Kp, nseg, pattern;
+  int R, K, Kp, nseg;
   int tiles_k, tiles_r, block_start;  // 64 x 64 tiles; first block of this job (grouped form)
   int vec2;  // element pairs along the source's contiguous dimension may be read as one access
 };
@@ -177,15 +215,15 @@ __device__ __forceinline__ void prep_tile(const PrepJob& j, int b, int tr, int t
         else o[0] = x0;
       }
     } else {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-      const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-      const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+      float r0 = x0, r1 = x1;  // remainders still to be represented
       __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(dst) + (int64_t)r * j.ld_out + k;
       for (int sg = 0; sg < j.nseg; ++sg) {
-        const bool lo = (j.pattern >> sg) & 1;
+        const __nv_bfloat16 p0 = __float2bfloat16_rn(r0), p1 = __float2bfloat16_rn(r1);
+        r0 -= __bfloat162float(p0);
+        r1 -= __bfloat162float(p1);
         __nv_bfloat16* os = o + (int64_t)sg * j.Kp;
-        if (two) *reinterpret_cast<__nv_bfloat162*>(os) = __halves2bfloat162(lo ? l0 : h0, lo ? l1 : h1);
-        else os[0] = lo ? l0 : h0;
+        if (two) *reinterpret_cast<__nv_bfloat162*>(os) = __halves2bfloat162(p0, p1);
+        else os[0] = p0;
       }
     }
   }
@@ -197,9 +235,12 @@ __global__ void prep_kernel(const PrepJob j) {
   prep_tile<TIn, TOut, SPLIT>(j, blockIdx.z, blockIdx.y, blockIdx.x);
 }
 
-// Grouped form: one block per (job, tile); jobs sorted by block_start.
+// Grouped form: one block per (job, tile); jobs sorted by block_start.  The
+// job table may have been written by the kernel just before (gemm_grouped
+// uploads it), so the programmatic wait comes before reading it.
 template <typename TIn, typename TOut, bool SPLIT>
 __global__ void prep_group_kernel(const PrepJob* jobs, int n_jobs) {
+  pdl_wait();
   const int blk = blockIdx.x;
   int lo = 0, hi = n_jobs - 1;
   while (lo < hi) {
@@ -241,8 +282,6 @@ cudaError_t launch_prep_pair(int family, const PrepJob& ja, const PrepJob& jb, i
 cudaError_t launch_prep_group(int family, const PrepJob* jobs, int n_jobs, int blocks, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
   dim3 block(32, kPrepWarps);
-  // The job table is written once when the plan is made, so reading it before
-  // the programmatic wait in prep_tile is safe.
   if (family == GEMM_PREC_F32X3)
     return launch_pdl(prep_group_kernel<float, __nv_bfloat16, true>, dim3(blocks), block, 0, s, nullptr, 0, jobs, n_jobs);
   if (family == GEMM_PREC_BF16)
@@ -252,30 +291,17 @@ cudaError_t launch_prep_group(int family, const PrepJob* jobs, int n_jobs, int b
 }
 
 // ---------------------------------------------------------------- main kernel launch
-// Persistent grid: one CTA (or CTA pair) per resident slot, at most one per tile unit.
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR>
+// Persistent grid: one CTA per resident slot, at most one per tile.
+template <int BN, int STAGES, bool TF32, bool GROUPED>
 cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc::TcArgs& a, const tc::GroupArgs& g,
                           cudaStream_t s) {
   using Cfg = tc::TcCfg<BN, STAGES, TF32>;
-  auto kern = tc::tc_gemm_kernel<BN, STAGES, TF32, GROUPED, PAIR>;
+  auto kern = tc::tc_gemm_kernel<BN, STAGES, TF32, GROUPED>;
   static unsigned long long done_mask = 0;
   static int slots_cache[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(tc::kThreads, 1, 1);
-  cfg.dynamicSmemBytes = Cfg::SMEM_BYTES;
-  cfg.stream = s;
-  if (PAIR) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-  }
   if (!(__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & bit)) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -294,30 +320,21 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc
     const int regs = (fa.numRegs + 7) / 8 * 8;
     int occ = std::min(smem_sm / (Cfg::SMEM_BYTES + (int)fa.sharedSizeBytes + reserved), regs_sm / (regs * tc::kThreads));
     occ = std::max(1, std::min(occ, 512 / Cfg::TMEM_COLS));  // every resident CTA must fit in TMEM
-    int slots = occ * sms;
-    if (PAIR) {
-      // The cluster query places one pair per two SMs; scale it by the CTAs per SM.
-      int clusters = 0;
-      cfg.gridDim = dim3(2 * sms, 1, 1);
-      e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
-      if (e != cudaSuccess) return e;
-      slots = std::max(1, std::min(clusters * occ, slots / 2));  // in pairs
-    }
-    slots_cache[dev & 63] = slots;
+    slots_cache[dev & 63] = occ * sms;
     __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);
   }
-  const int units = std::min(a.num_tiles, slots_cache[dev & 63]);
-  return launch_pdl(kern, dim3((unsigned)(PAIR ? 2 * units : units), 1, 1), cfg.blockDim, cfg.dynamicSmemBytes, s,
-                    cfg.attrs, (int)cfg.numAttrs, ma, mb, a, g);
+  const int ctas = std::min(a.num_tiles, slots_cache[dev & 63]);
+  return launch_pdl(kern, dim3((unsigned)ctas, 1, 1), dim3(tc::kThreads, 1, 1), Cfg::SMEM_BYTES, s, nullptr, 0, ma,
+                    mb, a, g);
 }
 
 using TcLaunch = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const tc::TcArgs&, const tc::GroupArgs&,
                                  cudaStream_t);
 
-template <bool TF32, bool GROUPED, bool PAIR>
+template <bool TF32, bool GROUPED>
 TcLaunch pick(int bn, int stages) {
 #define KS_TC_CASE(B, S) \
-  if (bn == B && stages == S) return &launch_kernel<B, S, TF32, GROUPED, PAIR>;
+  if (bn == B && stages == S) return &launch_kernel<B, S, TF32, GROUPED>;
   KS_TC_CASE(64, 2) KS_TC_CASE(64, 3) KS_TC_CASE(64, 4)
   KS_TC_CASE(128, 2) KS_TC_CASE(128, 3) KS_TC_CASE(128, 4)
   KS_TC_CASE(256, 2) KS_TC_CASE(256, 3) KS_TC_CASE(256, 4)
@@ -327,19 +344,11 @@ TcLaunch pick(int bn, int stages) {
 
 TcLaunch pick_launch(const TcConfig& c, bool grouped) {
   const bool tf32 = c.family == GEMM_PREC_TF32;
-  if (c.pair) {
-    if (grouped) return tf32 ? pick<true, true, true>(c.bn, c.stages) : pick<false, true, true>(c.bn, c.stages);
-    return tf32 ? pick<true, false, true>(c.bn, c.stages) : pick<false, false, true>(c.bn, c.stages);
-  }
-  if (grouped) return tf32 ? pick<true, true, false>(c.bn, c.stages) : pick<false, true, false>(c.bn, c.stages);
-  return tf32 ? pick<true, false, false>(c.bn, c.stages) : pick<false, false, false>(c.bn, c.stages);
+  if (grouped) return tf32 ? pick<true, true>(c.bn, c.stages) : pick<false, true>(c.bn, c.stages);
+  return tf32 ? pick<true, false>(c.bn, c.stages) : pick<false, false>(c.bn, c.stages);
 }
 
-// Row-tile units: 128-row tiles, or pairs of them.
-int row_units(int64_t M, int pair) {
-  const int t = (int)((M + tc::kBM - 1) / tc::kBM);
-  return pair ? (t + 1) / 2 : t;
-}
+int row_tiles(int64_t M) { return (int)((M + tc::kBM - 1) / tc::kBM); }
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -359,9 +368,9 @@ struct OperandPlan {
 
 // Operand of logical shape R x K (rows of op(A), or columns of op(B) = rows of
 // B^T).  `kcontig` says whether it is stored R x K (K contiguous); `mn_ext` is
-// the extent along R that one CTA loads per slice (128 for A, BN or BN / 2 for B).
+// the extent along R that one CTA loads per slice (128 for A, BN for B).
 OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t stride, bool kcontig, int R, int K,
-                         int batch, int pattern, int mn_ext) {
+                         int batch, int mn_ext) {
   const bool x3 = c.family == GEMM_PREC_F32X3;
   const int64_t in_elem = c.family == GEMM_PREC_BF16 ? 2 : 4;
   const int64_t op_elem = c.family == GEMM_PREC_TF32 ? 4 : 2;
@@ -376,8 +385,8 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   o.mn = !o.direct && c.family == GEMM_PREC_BF16 && !kcontig && mn_ext % tc::kMnBox == 0 &&
          ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0) && (batch == 1 || stride == (int64_t)K * ld);
   if (o.mn) o.direct = true;
-  const int nseg = x3 ? 2 : 1;
-  const int64_t Kp = x3 ? round_up(K, 64) : round_up(K, 16 / op_elem);
+  const int nseg = x3 ? split_plan(K).nseg : 1;
+  const int64_t Kp = x3 ? round_up(K, kSplitSeg) : round_up(K, 16 / op_elem);
   o.ld = o.direct ? ld : nseg * Kp;
   o.bytes = o.direct ? 0 : (int64_t)batch * R * o.ld * op_elem;
   // Element pairs along the contiguous dimension are read as one access when
@@ -385,7 +394,7 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   // strides all even multiples of the element size.
   const int64_t pair_bytes = 2 * in_elem;
   const int vec2 = ((uintptr_t)ptr % pair_bytes == 0) && (ld % 2 == 0) && (stride % 2 == 0);
-  o.job = PrepJob{ptr, stride, kcontig ? ld : 1, kcontig ? 1 : ld, nullptr, o.ld, R, K, (int)Kp, nseg, pattern,
+  o.job = PrepJob{ptr, stride, kcontig ? ld : 1, kcontig ? 1 : ld, nullptr, o.ld, R, K, (int)Kp, nseg,
                   (int)((Kp + 63) / 64), (R + 63) / 64, 0, vec2};
   return o;
 }
@@ -401,7 +410,7 @@ gemm_status_t tc_params(int id, int32_t out[8]) {
   TcConfig c;
   if (!decode(id, &c)) return GEMM_ERR_NO_KERNEL;
   const int bk = (c.family == GEMM_PREC_TF32) ? 32 : 64;
-  int32_t v[8] = {c.family, 128, c.bn, bk, c.stages, c.pair, 0, 0};
+  int32_t v[8] = {c.family, 128, c.bn, bk, c.stages, 0, 0, 0};
   std::memcpy(out, v, sizeof(v));
   return GEMM_OK;
 }
@@ -417,9 +426,9 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
   if (!status) return fail(cudaGetLastError());
 
   // op(A) rows are M, stored M x K when transA = 0; op(B)^T rows are N, stored N x K when transB = 1.
-  const int b_ext = c.pair ? c.bn / 2 : c.bn;
-  OperandPlan pa = plan_operand(c, g.A, g.lda, g.strideA, !g.transA, g.M, g.K, g.batch, /*hi,lo*/ 0b10, tc::kBM);
-  OperandPlan pb = plan_operand(c, g.B, g.ldb, g.strideB, g.transB != 0, g.N, g.K, g.batch, /*hi,lo*/ 0b10, b_ext);
+  const int b_ext = c.bn;
+  OperandPlan pa = plan_operand(c, g.A, g.lda, g.strideA, !g.transA, g.M, g.K, g.batch, tc::kBM);
+  OperandPlan pb = plan_operand(c, g.B, g.ldb, g.strideB, g.transB != 0, g.N, g.K, g.batch, b_ext);
   char* scratch = nullptr;
   if (pa.bytes + pb.bytes > 0) {
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), pa.bytes + pb.bytes + 256, s);
@@ -438,10 +447,12 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
     e = launch_prep(c.family, pb.job, g.batch, s);
   }
   gemm_status_t st = e == cudaSuccess ? GEMM_OK : fail(e);
-  // x3: the K' loop covers 3 segments of round_up(K, 64); the operands hold 2.
+  // Split products: the K' loop covers one segment of round_up(K, 64) per
+  // product; the operands hold one segment per part.
   const bool x3 = c.family == GEMM_PREC_F32X3;
-  const int64_t Kop = x3 ? 3 * round_up(g.K, 64) : g.K;
-  const int64_t Kmap = x3 ? 2 * round_up(g.K, 64) : g.K;
+  const SplitPlan sp = split_plan(g.K);
+  const int64_t Kop = x3 ? sp.nprod * round_up(g.K, kSplitSeg) : g.K;
+  const int64_t Kmap = x3 ? sp.nseg * round_up(g.K, kSplitSeg) : g.K;
   CUtensorMap ma, mb;
   const int bk = op_bf16 ? 64 : 32;
   const bool map_ok = st == GEMM_OK &&
@@ -453,18 +464,19 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
   if (st == GEMM_OK) {
     tc::TcArgs a;
     a.M = g.M; a.N = g.N; a.K = (int)Kop; a.batch = g.batch;
-    a.tiles_m = row_units(g.M, c.pair);
+    a.tiles_m = row_tiles(g.M);
     a.tiles_n = (g.N + c.bn - 1) / c.bn;
     a.num_tiles = a.tiles_m * a.tiles_n * g.batch;
     a.k_blocks = (int)((Kop + (op_bf16 ? 63 : 31)) / (op_bf16 ? 64 : 32));
-    // Grouped raster: 8 tile rows (units) per group bound the operand slices the
+    // Grouped raster: 8 tile rows per group bound the operand slices the
     // SMs' tiles in flight read at once (8 A + ~10 B slices for 152 CTAs).
     a.raster = 2;
     a.group_m = std::max(1, std::min(a.tiles_m, kRasterGroup));
     a.alpha = g.alpha; a.beta = g.beta;
     a.C = g.C; a.ldc = g.ldc; a.strideC = g.strideC; a.vecC = g.vecC;
     a.a_mn = pa.mn; a.b_mn = pb.mn;
-    a.seg_blocks = x3 ? (int)(round_up(g.K, 64) / 64) : 0;
+    a.seg_blocks = x3 ? (int)(round_up(g.K, kSplitSeg) / 64) : 0;
+    a.seg_map = x3 ? sp.seg_map : 0;
     a.status = status;
     tc::GroupArgs none{nullptr, 0};
     e = fn(ma, mb, a, none, s);
@@ -492,7 +504,236 @@ __global__ void wait_selftest_kernel(int* status, uint64_t limit_ns, int* waited
 }
 }  // namespace ks
 
-// ------------------------------------------------------------------ grouped plans
+// ------------------------------------------------------------------ grouped launches
+// A group is laid out on the host (validation, per-operand plans, scratch
+// offsets, problem order), then encoded into per-problem descriptors and
+// pre-pass jobs once its scratch address is known.  A plan keeps these in
+// device buffers of its own; gemm_grouped writes them into the handle's
+// workspace with kernels that carry them as launch parameters, so that a
+// CUDA graph captured around the call holds its own copy of them.
+namespace ks {
+namespace {
+
+struct GroupBuild {
+  TcConfig c;
+  int count = 0, n_jobs = 0;
+  std::vector<OperandPlan> pa, pb;
+  std::vector<int64_t> offA, offB;
+  std::vector<int> order;
+  int64_t scratch_bytes = 0;
+};
+
+// K extent of the kernel's loop for one problem (split products: one segment per product).
+int64_t k_loop(const TcConfig& c, int64_t K) {
+  return c.family == GEMM_PREC_F32X3 ? split_plan(K).nprod * round_up(K, kSplitSeg) : K;
+}
+
+gemm_status_t group_layout(const TcConfig& c, int count, const gemm_problem_t* probs, GroupBuild* b) {
+  if (count < 1 || !probs) return GEMM_ERR_INVALID_ARG;
+  b->c = c;
+  b->count = count;
+  b->pa.resize(count);
+  b->pb.resize(count);
+  b->offA.assign(count, -1);
+  b->offB.assign(count, -1);
+  int64_t tiles = 0;
+  for (int i = 0; i < count; ++i) {
+    const gemm_problem_t& q = probs[i];
+    int ta, tb;
+    auto tr = [](char t, int* o) {
+      if (t == 'N' || t == 'n') { *o = 0; return true; }
+      if (t == 'T' || t == 't') { *o = 1; return true; }
+      return false;
+    };
+    if (!tr(q.transA, &ta) || !tr(q.transB, &tb)) return GEMM_ERR_INVALID_ARG;
+    if (q.M < 0 || q.N < 0 || q.K < 1 || q.M >= (1ll << 31) || q.N >= (1ll << 31) || q.K >= (1ll << 31))
+      return GEMM_ERR_INVALID_ARG;
+    if (!q.A || !q.B || !q.C || q.ldc < q.N) return GEMM_ERR_INVALID_ARG;
+    if (q.lda < (ta ? q.M : q.K) || q.ldb < (tb ? q.K : q.N)) return GEMM_ERR_INVALID_ARG;
+    b->pa[i] = plan_operand(c, q.A, q.lda, 0, !ta, (int)q.M, (int)q.K, 1, tc::kBM);
+    b->pb[i] = plan_operand(c, q.B, q.ldb, 0, tb != 0, (int)q.N, (int)q.K, 1, c.bn);
+    if (!b->pa[i].direct) { b->offA[i] = b->scratch_bytes; b->scratch_bytes += round_up(b->pa[i].bytes, 256); ++b->n_jobs; }
+    if (!b->pb[i].direct) { b->offB[i] = b->scratch_bytes; b->scratch_bytes += round_up(b->pb[i].bytes, 256); ++b->n_jobs; }
+    tiles += (int64_t)row_tiles(q.M) * ((q.N + c.bn - 1) / c.bn);
+    if (tiles >= (1ll << 31)) return GEMM_ERR_UNSUPPORTED;
+  }
+  // Tiles are dealt to the persistent CTAs by static striding over the global
+  // tile index, so the problems are laid out by K-steps per tile, longest
+  // first: each CTA then takes one tile per round of a longest-first list,
+  // which balances uneven groups (results do not depend on the order).
+  b->order.resize(count);
+  std::iota(b->order.begin(), b->order.end(), 0);
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int x, int y) { return k_loop(c, probs[x].K) > k_loop(c, probs[y].K); });
+  return GEMM_OK;
+}
+
+// Descriptors and pre-pass jobs of a laid-out group whose scratch starts at
+// `scratch`; *total_tiles and *prep_blocks receive the two launches' sizes.
+gemm_status_t group_encode(const GroupBuild& b, const gemm_problem_t* probs, char* scratch,
+                           std::vector<tc::GroupDesc>* descs, std::vector<PrepJob>* jobs, int* total_tiles,
+                           int* prep_blocks) {
+  const TcConfig& c = b.c;
+  const bool op_bf16 = c.family != GEMM_PREC_TF32;
+  const bool x3 = c.family == GEMM_PREC_F32X3;
+  const int64_t op_elem = op_bf16 ? 2 : 4;
+  const int bk = op_bf16 ? 64 : 32;
+  descs->assign(b.count, tc::GroupDesc{});
+  jobs->clear();
+  int tile_start = 0, blocks = 0;
+  for (int r = 0; r < b.count; ++r) {
+    const int i = b.order[r];
+    const gemm_problem_t& q = probs[i];
+    const OperandPlan& pa = b.pa[i];
+    const OperandPlan& pb = b.pb[i];
+    const void* Aop = pa.direct ? q.A : scratch + b.offA[i];
+    const void* Bop = pb.direct ? q.B : scratch + b.offB[i];
+    if (!pa.direct) {
+      PrepJob j = pa.job;
+      j.out = const_cast<void*>(Aop);
+      j.block_start = blocks;
+      blocks += j.tiles_k * j.tiles_r;
+      jobs->push_back(j);
+    }
+    if (!pb.direct) {
+      PrepJob j = pb.job;
+      j.out = const_cast<void*>(Bop);
+      j.block_start = blocks;
+      blocks += j.tiles_k * j.tiles_r;
+      jobs->push_back(j);
+    }
+    const SplitPlan sp = split_plan(q.K);
+    const int64_t Kmap = x3 ? sp.nseg * round_up(q.K, kSplitSeg) : q.K;  // the operands hold one segment per part
+    tc::GroupDesc& d = (*descs)[r];
+    std::memset(&d, 0, sizeof(d));
+    const int64_t Mr = q.M > 0 ? q.M : 1, Nr = q.N > 0 ? q.N : 1;
+    const bool ok_a = pa.mn ? make_map(&d.tmA, Aop, op_bf16, Mr, Kmap, pa.ld, 1, bk)
+                            : make_map(&d.tmA, Aop, op_bf16, Kmap, Mr, pa.ld, 1, tc::kBM);
+    const bool ok_b = pb.mn ? make_map(&d.tmB, Bop, op_bf16, Nr, Kmap, pb.ld, 1, bk)
+                            : make_map(&d.tmB, Bop, op_bf16, Kmap, Nr, pb.ld, 1, c.bn);
+    if (!ok_a || !ok_b) return GEMM_ERR_MISALIGNED;
+    d.C = q.C;
+    d.ldc = q.ldc;
+    d.M = (int)q.M;
+    d.N = (int)q.N;
+    d.k_blocks = (int)((k_loop(c, q.K) * op_elem + 127) / 128);
+    d.tiles_m = row_tiles(q.M);
+    d.tiles_n = (int)((q.N + c.bn - 1) / c.bn);
+    d.tile_start = tile_start;
+    d.vecC = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0);
+    d.a_mn = pa.mn;
+    d.b_mn = pb.mn;
+    d.seg_blocks = x3 ? (int)(round_up(q.K, kSplitSeg) / 64) : 0;
+    d.seg_map = x3 ? sp.seg_map : 0;
+    d.alpha = q.alpha;
+    d.beta = q.beta;
+    tile_start += d.tiles_m * d.tiles_n;
+  }
+  *total_tiles = tile_start;
+  *prep_blocks = blocks;
+  return GEMM_OK;
+}
+
+// The pre-pass (when any operand needs one) and the persistent grouped launch.
+cudaError_t launch_group(const TcConfig& c, const tc::GroupDesc* descs_dev, int count, const PrepJob* jobs_dev,
+                         int n_jobs, int prep_blocks, int total_tiles, int* status, cudaStream_t s) {
+  cudaError_t e = launch_prep_group(c.family, jobs_dev, n_jobs, prep_blocks, s);
+  if (e != cudaSuccess) return e;
+  TcLaunch fn = pick_launch(c, true);
+  if (!fn) return cudaErrorInvalidDeviceFunction;
+  tc::TcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.num_tiles = total_tiles;
+  a.raster = 0;
+  a.status = status;
+  tc::GroupArgs g{descs_dev, count};
+  CUtensorMap dummy;
+  std::memset(&dummy, 0, sizeof(dummy));
+  return fn(dummy, dummy, a, g, s);
+}
+
+// Host bytes written to device memory by a kernel that receives them as its
+// launch parameter (at most 32,764 bytes of parameters per launch).  Inside a
+// stream capture the bytes become part of the graph.
+constexpr int kUploadBytes = 32 * 1024 - 512;
+struct UploadChunk {
+  uint8_t* dst;  // 16-byte aligned
+  int n;
+  alignas(16) uint8_t data[kUploadBytes];
+};
+
+__global__ void upload_kernel(const __grid_constant__ UploadChunk c) {
+  const int n16 = c.n / 16;
+  for (int i = threadIdx.x; i < n16; i += blockDim.x)
+    reinterpret_cast<uint4*>(c.dst)[i] = reinterpret_cast<const uint4*>(c.data)[i];
+  for (int i = n16 * 16 + threadIdx.x; i < c.n; i += blockDim.x) c.dst[i] = c.data[i];
+}
+
+cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  std::unique_ptr<UploadChunk> ch(new (std::nothrow) UploadChunk);
+  if (!ch) return cudaErrorMemoryAllocation;
+  for (size_t off = 0; off < bytes; off += kUploadBytes) {
+    ch->dst = static_cast<uint8_t*>(dst) + off;
+    ch->n = (int)std::min<size_t>(kUploadBytes, bytes - off);
+    std::memcpy(ch->data, static_cast<const uint8_t*>(src) + off, ch->n);
+    upload_kernel<<<1, 256, 0, s>>>(*ch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Workspace layout of a laid-out group: [descriptors | jobs | scratch], each
+// part 256-byte aligned from a 256-byte aligned base.
+struct WsLayout {
+  int64_t jobs_off, scratch_off, bytes;
+};
+WsLayout ws_layout(const GroupBuild& b) {
+  WsLayout w;
+  w.jobs_off = round_up((int64_t)sizeof(tc::GroupDesc) * b.count, 256);
+  w.scratch_off = w.jobs_off + round_up((int64_t)sizeof(PrepJob) * b.n_jobs, 256);
+  w.bytes = w.scratch_off + b.scratch_bytes;
+  return w;
+}
+
+// Family a precision class runs grouped: its own, or split-BF16 x3 for the
+// FP32 class (the tensor-core family with FP32-level accuracy).
+int grouped_family(int32_t precision) {
+  if (precision == GEMM_PREC_F32) return GEMM_PREC_F32X3;
+  if (precision >= GEMM_PREC_TF32 && precision <= GEMM_PREC_F32X3) return precision;
+  return -1;
+}
+
+// The group's config from the handle's group selector, checked against the family.
+gemm_status_t grouped_config(gemm_handle_t h, int32_t count, const gemm_problem_t* probs, int32_t precision,
+                             TcConfig* c) {
+  if (!h || count < 1 || !probs) return GEMM_ERR_INVALID_ARG;
+  const int fam = grouped_family(precision);
+  if (fam < 0) return GEMM_ERR_INVALID_ARG;
+  const int32_t id = gemm_grouped_select(h, count, probs);
+  if (id < 0) return (gemm_status_t)id;
+  if (!decode(id, c) || c->family != fam) return GEMM_ERR_NO_KERNEL;
+  return GEMM_OK;
+}
+
+// Makes the handle's workspace on the current device at least `bytes` long.
+// The buffer it replaces is kept (queued work and captured graphs may still
+// use it) and freed with the handle.  Called with h->dev_mu held.
+gemm_status_t ws_reserve(gemm_handle_t h, int dev, int64_t bytes) {
+  if (h->dev_ws_bytes[dev] >= bytes) return GEMM_OK;
+  char* p = nullptr;
+  const int64_t grow = std::max<int64_t>(bytes, 1 << 20);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), grow);
+  if (e != cudaSuccess) return fail(e);
+  if (h->dev_ws[dev]) h->retired_ws.push_back(h->dev_ws[dev]);
+  h->dev_ws[dev] = p;
+  h->dev_ws_bytes[dev] = grow;
+  return GEMM_OK;
+}
+
+}  // namespace
+}  // namespace ks
+
 struct kselect_grouped_plan {
   ks::TcConfig cfg;
   int count = 0, total_tiles = 0, n_jobs = 0, prep_blocks = 0;
@@ -526,106 +767,22 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
   if (!encode_fn()) return GEMM_ERR_UNSUPPORTED;
   if (!status_word()) return fail(cudaGetLastError());  // made now, so that runs never allocate
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool op_bf16 = c.family != GEMM_PREC_TF32;
-  const int64_t op_elem = op_bf16 ? 2 : 4;
-  std::vector<tc::GroupDesc> descs(count);
-  std::vector<PrepJob> jobs;
-  std::vector<OperandPlan> pa(count), pb(count);
-  int64_t scratch_bytes = 0, tiles = 0;
-  std::vector<int64_t> offA(count, -1), offB(count, -1);
-  for (int i = 0; i < count; ++i) {
-    const gemm_problem_t& q = probs[i];
-    int ta, tb;
-    auto tr = [](char t, int* o) {
-      if (t == 'N' || t == 'n') { *o = 0; return true; }
-      if (t == 'T' || t == 't') { *o = 1; return true; }
-      return false;
-    };
-    if (!tr(q.transA, &ta) || !tr(q.transB, &tb)) return GEMM_ERR_INVALID_ARG;
-    if (q.M < 0 || q.N < 0 || q.K < 1 || q.M >= (1ll << 31) || q.N >= (1ll << 31) || q.K >= (1ll << 31))
-      return GEMM_ERR_INVALID_ARG;
-    if (!q.A || !q.B || !q.C || q.ldc < q.N) return GEMM_ERR_INVALID_ARG;
-    if (q.lda < (ta ? q.M : q.K) || q.ldb < (tb ? q.K : q.N)) return GEMM_ERR_INVALID_ARG;
-    pa[i] = plan_operand(c, q.A, q.lda, 0, !ta, (int)q.M, (int)q.K, 1, /*hi,lo*/ 0b10, tc::kBM);
-    pb[i] = plan_operand(c, q.B, q.ldb, 0, tb != 0, (int)q.N, (int)q.K, 1, /*hi,lo*/ 0b10, c.pair ? c.bn / 2 : c.bn);
-    if (!pa[i].direct) { offA[i] = scratch_bytes; scratch_bytes += round_up(pa[i].bytes, 256); }
-    if (!pb[i].direct) { offB[i] = scratch_bytes; scratch_bytes += round_up(pb[i].bytes, 256); }
-    const int tm = row_units(q.M, c.pair), tn = (int)((q.N + c.bn - 1) / c.bn);
-    tiles += (int64_t)tm * tn;
-    if (tiles >= (1ll << 31)) return GEMM_ERR_UNSUPPORTED;
-  }
+  GroupBuild b;
+  gemm_status_t st = group_layout(c, count, probs, &b);
+  if (st != GEMM_OK) return st;
   kselect_grouped_plan* p = new (std::nothrow) kselect_grouped_plan();
   if (!p) return GEMM_ERR_UNSUPPORTED;
   p->cfg = c;
   p->count = count;
   cudaGetDevice(&p->device);
   cudaError_t e = cudaSuccess;
-  if (scratch_bytes > 0) e = cudaMalloc(reinterpret_cast<void**>(&p->scratch), scratch_bytes);
+  if (b.scratch_bytes > 0) e = cudaMalloc(reinterpret_cast<void**>(&p->scratch), b.scratch_bytes);
   if (e != cudaSuccess) { plan_free(p); return fail(e); }
-  // Tiles are dealt to the persistent CTAs by static striding over the global
-  // tile index, so the problems are laid out by K-steps per tile, longest
-  // first: each CTA then takes one tile per round of a longest-first list,
-  // which balances uneven groups (results do not depend on the order).
-  std::vector<int> order(count);
-  std::iota(order.begin(), order.end(), 0);
-  const int64_t kmul = c.family == GEMM_PREC_F32X3 ? 3 : 1;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    const int64_t kx = kmul * (c.family == GEMM_PREC_F32X3 ? round_up(probs[x].K, 64) : probs[x].K);
-    const int64_t ky = kmul * (c.family == GEMM_PREC_F32X3 ? round_up(probs[y].K, 64) : probs[y].K);
-    return kx > ky;
-  });
-  int tile_start = 0, blocks = 0;
-  for (int r = 0; r < count; ++r) {
-    const int i = order[r];
-    const gemm_problem_t& q = probs[i];
-    const void* Aop = pa[i].direct ? q.A : p->scratch + offA[i];
-    const void* Bop = pb[i].direct ? q.B : p->scratch + offB[i];
-    if (!pa[i].direct) {
-      pa[i].job.out = const_cast<void*>(Aop);
-      pa[i].job.block_start = blocks;
-      blocks += pa[i].job.tiles_k * pa[i].job.tiles_r;
-      jobs.push_back(pa[i].job);
-    }
-    if (!pb[i].direct) {
-      pb[i].job.out = const_cast<void*>(Bop);
-      pb[i].job.block_start = blocks;
-      blocks += pb[i].job.tiles_k * pb[i].job.tiles_r;
-      jobs.push_back(pb[i].job);
-    }
-    const bool x3 = c.family == GEMM_PREC_F32X3;
-    const int64_t Kop = x3 ? 3 * round_up(q.K, 64) : q.K;  // K' loop; the operands hold 2 segments
-    const int64_t Kmap = x3 ? 2 * round_up(q.K, 64) : q.K;
-    tc::GroupDesc& d = descs[r];
-    std::memset(&d, 0, sizeof(d));
-    const int64_t Mr = q.M > 0 ? q.M : 1, Nr = q.N > 0 ? q.N : 1;
-    const int bk = op_bf16 ? 64 : 32;
-    const bool ok_a = pa[i].mn ? make_map(&d.tmA, Aop, op_bf16, Mr, Kmap, pa[i].ld, 1, bk)
-                               : make_map(&d.tmA, Aop, op_bf16, Kmap, Mr, pa[i].ld, 1, tc::kBM);
-    const bool ok_b = pb[i].mn ? make_map(&d.tmB, Bop, op_bf16, Nr, Kmap, pb[i].ld, 1, bk)
-                               : make_map(&d.tmB, Bop, op_bf16, Kmap, Nr, pb[i].ld, 1, c.pair ? c.bn / 2 : c.bn);
-    if (!ok_a || !ok_b) {
-      plan_free(p);
-      return GEMM_ERR_MISALIGNED;
-    }
-    d.C = q.C;
-    d.ldc = q.ldc;
-    d.M = (int)q.M;
-    d.N = (int)q.N;
-    d.k_blocks = (int)((Kop * op_elem + 127) / 128);
-    d.tiles_m = row_units(q.M, c.pair);
-    d.tiles_n = (int)((q.N + c.bn - 1) / c.bn);
-    d.tile_start = tile_start;
-    d.vecC = ((uintptr_t)q.C % 16 == 0) && (q.ldc % 4 == 0);
-    d.a_mn = pa[i].mn;
-    d.b_mn = pb[i].mn;
-    d.seg_blocks = x3 ? (int)(round_up(q.K, 64) / 64) : 0;
-    d.alpha = q.alpha;
-    d.beta = q.beta;
-    tile_start += d.tiles_m * d.tiles_n;
-  }
-  p->total_tiles = tile_start;
+  std::vector<tc::GroupDesc> descs;
+  std::vector<PrepJob> jobs;
+  st = group_encode(b, probs, p->scratch, &descs, &jobs, &p->total_tiles, &p->prep_blocks);
+  if (st != GEMM_OK) { plan_free(p); return st; }
   p->n_jobs = (int)jobs.size();
-  p->prep_blocks = blocks;
   e = cudaMalloc(reinterpret_cast<void**>(&p->descs), sizeof(tc::GroupDesc) * count);
   if (e == cudaSuccess && !jobs.empty()) e = cudaMalloc(reinterpret_cast<void**>(&p->jobs), sizeof(PrepJob) * jobs.size());
   if (e == cudaSuccess)
@@ -641,28 +798,16 @@ gemm_status_t gemm_grouped_plan_create(int32_t id, int32_t count, const gemm_pro
 gemm_status_t gemm_grouped_run(gemm_grouped_plan_t p, void* stream) {
   if (!p) return GEMM_ERR_INVALID_ARG;
   if (p->total_tiles == 0) return GEMM_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* status = status_word();
   if (!status) return fail(cudaGetLastError());
-  cudaError_t e = launch_prep_group(p->cfg.family, p->jobs, p->n_jobs, p->prep_blocks, s);
-  if (e != cudaSuccess) return fail(e);
-  TcLaunch fn = pick_launch(p->cfg, true);
-  if (!fn) return GEMM_ERR_NO_KERNEL;
-  tc::TcArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.num_tiles = p->total_tiles;
-  a.raster = 0;
-  a.status = status;
-  tc::GroupArgs g{p->descs, p->count};
-  CUtensorMap dummy;
-  std::memset(&dummy, 0, sizeof(dummy));
-  e = fn(dummy, dummy, a, g, s);
+  cudaError_t e = launch_group(p->cfg, p->descs, p->count, p->jobs, p->n_jobs, p->prep_blocks, p->total_tiles,
+                               status, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GEMM_OK : fail(e);
 }
 
 void gemm_grouped_plan_destroy(gemm_grouped_plan_t p) { plan_free(p); }
 
-gemm_status_t gemm_grouped(int32_t id, int32_t count, const gemm_problem_t* probs, void* stream) {
+gemm_status_t gemm_grouped_with_config(int32_t id, int32_t count, const gemm_problem_t* probs, void* stream) {
   gemm_grouped_plan_t p = nullptr;
   gemm_status_t st = gemm_grouped_plan_create(id, count, probs, stream, &p);
   if (st != GEMM_OK) return st;
@@ -672,6 +817,66 @@ gemm_status_t gemm_grouped(int32_t id, int32_t count, const gemm_problem_t* prob
   plan_free(p);
   if (st == GEMM_OK && e != cudaSuccess) st = fail(e);
   return st;
+}
+
+gemm_status_t gemm_grouped_reserve(gemm_handle_t h, int32_t count, const gemm_problem_t* probs, int32_t precision) {
+  TcConfig c;
+  gemm_status_t st = grouped_config(h, count, probs, precision, &c);
+  if (st != GEMM_OK) return st;
+  GroupBuild b;
+  if ((st = group_layout(c, count, probs, &b)) != GEMM_OK) return st;
+  if (!encode_fn()) return GEMM_ERR_UNSUPPORTED;
+  if (!status_word()) return fail(cudaGetLastError());
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return GEMM_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> g(h->dev_mu);
+  return ws_reserve(h, dev, ws_layout(b).bytes);
+}
+
+gemm_status_t gemm_grouped(gemm_handle_t h, int32_t count, const gemm_problem_t* probs, int32_t precision,
+                           void* stream) {
+  TcConfig c;
+  gemm_status_t st = grouped_config(h, count, probs, precision, &c);
+  if (st != GEMM_OK) return st;
+  GroupBuild b;
+  if ((st = group_layout(c, count, probs, &b)) != GEMM_OK) return st;
+  if (!encode_fn()) return GEMM_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return fail(e);
+  int* status = nullptr;
+  if (cap == cudaStreamCaptureStatusNone) {
+    status = status_word();  // may allocate on the device's first tensor-core call
+    if (!status) return fail(cudaGetLastError());
+  } else {
+    status = status_word_if_ready();
+    if (!status) return GEMM_ERR_UNSUPPORTED;  // first call on this device under capture
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return GEMM_ERR_UNSUPPORTED;
+  const WsLayout w = ws_layout(b);
+  std::lock_guard<std::mutex> g(h->dev_mu);
+  if (h->dev_ws_bytes[dev] < w.bytes) {
+    if (cap != cudaStreamCaptureStatusNone) return GEMM_ERR_UNSUPPORTED;  // never allocate inside a capture
+    if ((st = ws_reserve(h, dev, w.bytes)) != GEMM_OK) return st;
+  }
+  char* base = h->dev_ws[dev];
+  std::vector<tc::GroupDesc> descs;
+  std::vector<PrepJob> jobs;
+  int total_tiles = 0, prep_blocks = 0;
+  if ((st = group_encode(b, probs, base + w.scratch_off, &descs, &jobs, &total_tiles, &prep_blocks)) != GEMM_OK)
+    return st;
+  if (total_tiles == 0) return GEMM_OK;
+  e = upload(base, descs.data(), sizeof(tc::GroupDesc) * descs.size(), s);
+  if (e == cudaSuccess && !jobs.empty()) e = upload(base + w.jobs_off, jobs.data(), sizeof(PrepJob) * jobs.size(), s);
+  if (e == cudaSuccess)
+    e = launch_group(c, reinterpret_cast<const tc::GroupDesc*>(base), count,
+                     reinterpret_cast<const PrepJob*>(base + w.jobs_off), (int)jobs.size(), prep_blocks, total_tiles,
+                     status, s);
+  return e == cudaSuccess ? GEMM_OK : fail(e);
 }
 
 gemm_status_t kselect_wait_selftest(int64_t limit_ns, int32_t* waited_out, void* stream) {

@@ -34,10 +34,11 @@ struct TcArgs {
   int64_t ldc, strideC;
   int vecC;
   int a_mn, b_mn;  // operand staged MN-major (BF16 only)
-  // Split-BF16 x3: the operands hold [hi | lo] segments of seg_blocks K-slices
-  // each and the K' = 3 x segment loop reads A as hi, hi, lo and B as hi, lo,
-  // hi; 0 for the other families.
-  int seg_blocks;
+  // Split-BF16 products: each operand holds nseg segments of seg_blocks
+  // K-slices (its BF16 split parts, largest first) and segment g of the K'
+  // loop multiplies A's part seg_map bits [2g, 2g + 2) by B's part seg_map bits
+  // [16 + 2g, 16 + 2g + 2); seg_blocks is 0 for the other families.
+  int seg_blocks, seg_map;
   int* status;
 };
 
@@ -50,7 +51,7 @@ struct alignas(128) GroupDesc {
   float* C;
   int64_t ldc;
   int M, N, k_blocks, tiles_m, tiles_n, tile_start, vecC;
-  int a_mn, b_mn, seg_blocks;
+  int a_mn, b_mn, seg_blocks, seg_map;
   float alpha, beta;
 };
 
@@ -114,17 +115,13 @@ struct TileLoc {
   const CUtensorMap* mb;
   float* C;
   int64_t ldc, strideC;
-  int M, N, k_blocks, b, tm, tn, vecC, a_mn, b_mn, seg_blocks;
+  int M, N, k_blocks, b, tm, tn, vecC, a_mn, b_mn, seg_blocks, seg_map;
   float alpha, beta;
 };
 
-// With PAIR, tile units count pairs of vertically adjacent 128-row tiles:
-// tiles_m is in pair units and CTA `rank` of the cluster takes row tile
-// 2 * unit + rank (the odd pair's second tile may lie past M: its loads
-// zero-fill and its stores are skipped).
-template <bool GROUPED, bool PAIR = false>
+template <bool GROUPED>
 __device__ __forceinline__ TileLoc locate(const TcArgs& p, const GroupArgs& g, const CUtensorMap* ma,
-                                          const CUtensorMap* mb, int tile, int rank = 0) {
+                                          const CUtensorMap* mb, int tile) {
   TileLoc L;
   if constexpr (GROUPED) {
     int lo = 0, hi = g.count - 1;  // last problem whose tile_start <= tile
@@ -136,16 +133,15 @@ __device__ __forceinline__ TileLoc locate(const TcArgs& p, const GroupArgs& g, c
     const int t = tile - d.tile_start;
     L.ma = &d.tmA; L.mb = &d.tmB; L.C = d.C; L.ldc = d.ldc; L.strideC = 0;
     L.M = d.M; L.N = d.N; L.k_blocks = d.k_blocks; L.b = 0; L.vecC = d.vecC; L.a_mn = d.a_mn; L.b_mn = d.b_mn;
-    L.seg_blocks = d.seg_blocks;
+    L.seg_blocks = d.seg_blocks; L.seg_map = d.seg_map;
     L.alpha = d.alpha; L.beta = d.beta;
     if (p.raster == 0) { L.tm = t % d.tiles_m; L.tn = t / d.tiles_m; } else { L.tn = t % d.tiles_n; L.tm = t / d.tiles_n; }
   } else {
     L.ma = ma; L.mb = mb; L.C = p.C; L.ldc = p.ldc; L.strideC = p.strideC;
     L.M = p.M; L.N = p.N; L.k_blocks = p.k_blocks; L.vecC = p.vecC; L.alpha = p.alpha; L.beta = p.beta;
-    L.a_mn = p.a_mn; L.b_mn = p.b_mn; L.seg_blocks = p.seg_blocks;
+    L.a_mn = p.a_mn; L.b_mn = p.b_mn; L.seg_blocks = p.seg_blocks; L.seg_map = p.seg_map;
     tile_coords(p, tile, L.b, L.tm, L.tn);
   }
-  if (PAIR) L.tm = 2 * L.tm + rank;
   return L;
 }
 
@@ -200,13 +196,7 @@ __device__ __forceinline__ void store_chunk32(const TileLoc& p, float* cbase, in
   }
 }
 
-// PAIR: the kernel runs in clusters of two CTAs that compute vertically
-// adjacent tiles with the same B slice.  Each CTA loads its own A rows and
-// one half of the B slice, multicasting that half into both CTAs' rings, so a
-// CTA reads 16 KB + BN x 64 B per slice from L2 instead of 16 KB + BN x 128 B.
-// A ring slot is refilled only after both CTAs' MMAs released it: every MMA
-// commit arrives on the slot's empty barrier in both CTAs (2 arrivals).
-template <int BN, int STAGES, bool TF32, bool GROUPED, bool PAIR>
+template <int BN, int STAGES, bool TF32, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs p,
                    const GroupArgs g) {
@@ -216,14 +206,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_base_sh;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rank = PAIR ? (int)cluster_ctarank() : 0;
-  const int unit0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-  const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int unit0 = (int)blockIdx.x;
+  const int units = (int)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], PAIR ? 2 : 1);
+      mbar_init(&empty_bar[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&accf_bar[a], 1);
@@ -238,7 +227,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 5) tmem_alloc<Cfg::TMEM_COLS>(&tmem_base_sh);
   tc_fence_before();
   __syncthreads();
-  if (PAIR) cluster_sync();  // the peer's multicasts target barriers initialised above
   tc_fence_after();
   const uint32_t tmem_base = tmem_base_sh;
   // The prologue above (barriers, TMEM, tensor-map prefetch) touches no global
@@ -253,17 +241,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       bool ok = true;
       for (int tile = unit0; tile < p.num_tiles && ok; tile += units) {
-        const TileLoc L = locate<GROUPED, PAIR>(p, g, &tmA, &tmB, tile, rank);
+        const TileLoc L = locate<GROUPED>(p, g, &tmA, &tmB, tile);
         for (int kb = 0; kb < L.k_blocks; ++kb) {
           if (!(ok = mbar_wait(&empty_bar[stage], phase ^ 1, p.status, kStatusTimeoutEmpty))) break;
           uint8_t* sa = smem + stage * Cfg::STAGE_BYTES;
-          // K coordinates of this slice in A and B (x3: segment g of the K'
-          // loop reads A's hi, hi, lo and B's hi, lo, hi segment).
+          // K coordinates of this slice in A and B (split products: segment g
+          // of the K' loop reads the parts of A and B that seg_map names).
           int xa = kb * Cfg::BK, xb = kb * Cfg::BK;
           if (!TF32 && L.seg_blocks > 0) {
             const int g = kb / L.seg_blocks, kk = kb - g * L.seg_blocks;
-            xa = ((g == 2 ? L.seg_blocks : 0) + kk) * Cfg::BK;
-            xb = ((g == 1 ? L.seg_blocks : 0) + kk) * Cfg::BK;
+            xa = (((L.seg_map >> (2 * g)) & 3) * L.seg_blocks + kk) * Cfg::BK;
+            xb = (((L.seg_map >> (16 + 2 * g)) & 3) * L.seg_blocks + kk) * Cfg::BK;
           }
           mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
           if (!TF32 && L.a_mn) {
@@ -275,20 +263,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_3d(sa, L.ma, &full_bar[stage], xa, L.tm * kBM, L.b);
           }
           if (!TF32 && L.b_mn) {
-            // This CTA's boxes of the slice: all BN / 64, or its half of them in a pair.
-            constexpr int NB = (PAIR ? BN / 2 : BN) / Cfg::MN_BOX;
 #pragma unroll
-            for (int jj = 0; jj < NB; ++jj) {
-              const int j = (PAIR ? rank * NB : 0) + jj;
-              uint8_t* dst = sa + Cfg::A_BYTES + j * Cfg::MN_BOX_BYTES;
-              if constexpr (PAIR)
-                tma_load_3d_mcast(dst, L.mb, &full_bar[stage], L.tn * BN + j * Cfg::MN_BOX, xb, L.b, (uint16_t)0x3);
-              else
-                tma_load_3d(dst, L.mb, &full_bar[stage], L.tn * BN + j * Cfg::MN_BOX, xb, L.b);
-            }
-          } else if constexpr (PAIR) {
-            tma_load_3d_mcast(sa + Cfg::A_BYTES + rank * (Cfg::B_BYTES / 2), L.mb, &full_bar[stage], xb,
-                              L.tn * BN + rank * (BN / 2), L.b, (uint16_t)0x3);
+            for (int j = 0; j < BN / Cfg::MN_BOX; ++j)
+              tma_load_3d(sa + Cfg::A_BYTES + j * Cfg::MN_BOX_BYTES, L.mb, &full_bar[stage],
+                          L.tn * BN + j * Cfg::MN_BOX, xb, L.b);
           } else {
             tma_load_3d(sa + Cfg::A_BYTES, L.mb, &full_bar[stage], xb, L.tn * BN, L.b);
           }
@@ -320,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = unit0; tile < p.num_tiles && ok; tile += units) {
         int k_blocks = p.k_blocks, a_mn = p.a_mn, b_mn = p.b_mn;
         if constexpr (GROUPED) {
-          const TileLoc L = locate<true, PAIR>(p, g, &tmA, &tmB, tile, rank);
+          const TileLoc L = locate<true>(p, g, &tmA, &tmB, tile);
           k_blocks = L.k_blocks;
           a_mn = L.a_mn;
           b_mn = L.b_mn;
@@ -347,9 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t bd = smem_desc_sw128(b_addr + (uint32_t)k * b_step, b_lbo, 1024);
             mma<TF32>(d_tmem, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
           }
-          // frees the slot (in both CTAs of a pair) once these MMAs have read it
-          if constexpr (PAIR) mma_commit_mcast(&empty_bar[stage], (uint16_t)0x3);
-          else mma_commit(&empty_bar[stage]);
+          mma_commit(&empty_bar[stage]);  // frees the slot once these MMAs have read it
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1;
@@ -370,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = unit0; tile < p.num_tiles; tile += units) {
       if (!mbar_wait(&accf_bar[acc], acc_phase, p.status, kStatusTimeoutAcc)) break;
       tc_fence_after();
-      const TileLoc L = locate<GROUPED, PAIR>(p, g, &tmA, &tmB, tile, rank);
+      const TileLoc L = locate<GROUPED>(p, g, &tmA, &tmB, tile);
       const int row0 = L.tm * kBM + warp * 32;
       float* cbase = L.C + (int64_t)L.b * L.strideC;
       float* stage = reinterpret_cast<float*>(smem + STAGES * Cfg::STAGE_BYTES) + warp * 32 * 16;
@@ -396,9 +372,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     tmem_dealloc<Cfg::TMEM_COLS>(tmem_base);
   }
-  // Neither CTA of a pair leaves while the other may still multicast into its
-  // ring or commit to its barriers.
-  if (PAIR) cluster_sync();
 }
 
 }  // namespace tc

@@ -30,6 +30,7 @@ GEMM_OK = 0
 PREC_F32, PREC_TF32, PREC_BF16, PREC_F32X3 = 0, 1, 2, 3
 PRECISIONS = {"f32": PREC_F32, "tf32": PREC_TF32, "bf16": PREC_BF16, "f32x3": PREC_F32X3}
 MLP_PARAMS = 5192
+TREE_FEATURES = 5  # M, N, K, batch, M * N * batch
 MAX_DEPLOYED = 16
 
 
@@ -83,7 +84,7 @@ _sig("gemm_strided_batched_with_config", i32, [i32] + _STRIDED_ARGS)
 _sig("gemm_host", i32, [vp, ch, ch, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i64, vp, vp, vp, vp])
 _sig("gemm_host_pipeline", i32, [vp, i32, ctypes.POINTER(HostProblem), vp])
 _sig("gemm_benchmark", i32, [i32, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64, i64, i32, i32, i32, f64,
-                             ctypes.POINTER(f64), vp])
+                             ctypes.POINTER(f64), ctypes.POINTER(i32), vp])
 _sig("gemm_error_check", i32, [i64, i64, i64, vp, i64, i64, i64, vp, vp, vp, ctypes.POINTER(f64), vp])
 _sig("kselect_fill_uniform", i32, [vp, i64, i64, i64, i64, u64, f32, f32, f32, vp])
 _sig("gemm_device_status", i32, [ctypes.POINTER(i32), i32])
@@ -91,7 +92,9 @@ _sig("kselect_wait_selftest", i32, [i64, ctypes.POINTER(i32), vp])
 _sig("gemm_grouped_plan_create", i32, [i32, i32, ctypes.POINTER(Problem), vp, ctypes.POINTER(vp)])
 _sig("gemm_grouped_run", i32, [vp, vp])
 _sig("gemm_grouped_plan_destroy", None, [vp])
-_sig("gemm_grouped", i32, [i32, i32, ctypes.POINTER(Problem), vp])
+_sig("gemm_grouped_with_config", i32, [i32, i32, ctypes.POINTER(Problem), vp])
+_sig("gemm_grouped", i32, [vp, i32, ctypes.POINTER(Problem), i32, vp])
+_sig("gemm_grouped_reserve", i32, [vp, i32, ctypes.POINTER(Problem), i32])
 _sig("gemm_grouped_select", i32, [vp, i32, ctypes.POINTER(Problem)])
 _sig("mlp_features", i32, [i32, vp, vp, vp])
 _sig("mlp_forward", i32, [i32, vp, vp, vp, vp])
@@ -101,7 +104,8 @@ _sig("mlp_loss_grad_noalloc", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
 _sig("mlp_train", i32, [i32, vp, vp, vp, vp, vp, vp, i32, i32, f32, f32, f32, f32, vp, vp])
 _sig("select_kernels_batched", i32, [vp, i32, vp, vp, vp, vp])
 _sig("gemm_benchmark_configs", i32, [i32, ctypes.POINTER(i32), ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, i64,
-                                     i64, i32, i32, i32, f64, f64, ctypes.POINTER(f64), ctypes.POINTER(i32), vp])
+                                     i64, i32, i32, i32, f64, f64, ctypes.POINTER(f64), ctypes.POINTER(i32),
+                                     ctypes.POINTER(f64), ctypes.POINTER(i32), vp])
 _sig("kselect_normalise", i32, [i64, i32, vp, vp, i32, vp])
 _sig("kselect_kmeans", i32, [i32, i32, i32, i32, vp, ctypes.POINTER(ctypes.c_uint32), i32, f32, vp, vp,
                              ctypes.POINTER(f64), ctypes.POINTER(i32), vp])
@@ -123,6 +127,8 @@ _sig("kselect_tree_regress", i32, [i32, i32, ctypes.POINTER(f64), ctypes.POINTER
                                    ctypes.POINTER(f32), ctypes.POINTER(i32)])
 _sig("kselect_tree_train_rf", i32, [i32, ctypes.POINTER(f64), ctypes.POINTER(i32), i32, i32, i32, i32,
                                     ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(TreeNode), i32, ctypes.POINTER(i32)])
+_sig("kselect_selector_features", i32, [i32, ctypes.POINTER(i64), ctypes.POINTER(f64)])
+_sig("kselect_best_labels", i32, [i32, i32, ctypes.POINTER(f64), i32, ctypes.POINTER(i32), ctypes.POINTER(i32)])
 _sig("kselect_tree_train", i32, [i32, ctypes.POINTER(f64), ctypes.POINTER(i32), i32, i32, i32,
                                  ctypes.POINTER(TreeNode), i32, ctypes.POINTER(i32)])
 
@@ -332,13 +338,15 @@ def gemm_status(cid: int, transA: str, transB: str, M, N, K, alpha, A, lda, B, l
 
 
 def gemm_benchmark(cid: int, transA: str, transB: str, M, N, K, A, lda, B, ldb, C, ldc, batch=1, warmup=2,
-                   min_reps=3, max_reps=50, min_total_ms=2.0, stream=None) -> tuple[int, float]:
-    """(status, mean ms per launch); a non-OK status is returned, not raised, so
-    that a sweep can record configs that cannot run as failed."""
-    out = f64()
+                   min_reps=3, max_reps=50, min_total_ms=2.0, stream=None, with_reps=False):
+    """(status, mean ms per launch[, launches timed]); a non-OK status is
+    returned, not raised, so that a sweep can record configs that cannot run
+    as failed."""
+    out, reps = f64(), i32()
     st = _lib.gemm_benchmark(cid, _c(transA), _c(transB), M, N, K, ptr(A), lda, ptr(B), ldb, ptr(C), ldc, batch,
-                             warmup, min_reps, max_reps, min_total_ms, ctypes.byref(out), stream_handle(stream))
-    return st, out.value
+                             warmup, min_reps, max_reps, min_total_ms, ctypes.byref(out), ctypes.byref(reps),
+                             stream_handle(stream))
+    return (st, out.value, reps.value) if with_reps else (st, out.value)
 
 
 def error_check(C, Cref, den, rows=0, cols=0, batch=0, ldc=0, strideC=0, pos=None, stream=None) -> float:
@@ -377,16 +385,21 @@ def _arr(a, dtype, ctype):
 
 
 def benchmark_configs(cids, transA, transB, M, N, K, A, lda, B, ldb, C, ldc, batch=1, warmup=1, min_reps=2,
-                      max_reps=50, min_total_ms=2.0, refine_ratio=2.0, stream=None):
-    """Section 3.1 over a config list: (ms per launch, status) arrays."""
+                      max_reps=50, min_total_ms=2.0, refine_ratio=2.0, stream=None, details=False):
+    """Section 3.1 over a config list: (ms per launch, status) arrays, plus
+    (pass-1 probe ms, launches averaged) with details=True."""
     ids, pids = _arr(cids, np.int32, i32)
     ms = np.zeros(len(ids), np.float64)
     st = np.zeros(len(ids), np.int32)
+    probe = np.zeros(len(ids), np.float64)
+    reps = np.zeros(len(ids), np.int32)
     check(_lib.gemm_benchmark_configs(len(ids), pids, _c(transA), _c(transB), M, N, K, ptr(A), lda, ptr(B), ldb,
                                       ptr(C), ldc, batch, warmup, min_reps, max_reps, min_total_ms, refine_ratio,
                                       ms.ctypes.data_as(ctypes.POINTER(f64)), st.ctypes.data_as(ctypes.POINTER(i32)),
-                                      stream_handle(stream)), "gemm_benchmark_configs")
-    return ms, st
+                                      probe.ctypes.data_as(ctypes.POINTER(f64)),
+                                      reps.ctypes.data_as(ctypes.POINTER(i32)), stream_handle(stream)),
+          "gemm_benchmark_configs")
+    return (ms, st, probe, reps) if details else (ms, st)
 
 
 NORM_MODES = {"standard": 0, "raw_cutoff": 1, "standard_cutoff": 2, "sigmoid": 3}
@@ -483,6 +496,7 @@ def tree_regress(features: np.ndarray, Y: np.ndarray, max_leaves: int) -> tuple[
     """Regression-tree partition of the sizes (host): (labels, leaf-mean centres)."""
     n, d = Y.shape
     F, pf = _arr(features, np.float64, f64)
+    assert F.shape == (n, TREE_FEATURES)
     Yc, py = _arr(Y, np.float32, f32)
     labels = np.zeros(n, np.int32)
     centres = np.zeros((max_leaves, d), np.float32)
@@ -511,10 +525,29 @@ def top_n(perf: np.ndarray, n: int) -> np.ndarray:
     return out
 
 
+def selector_features(sizes) -> np.ndarray:
+    """(n, TREE_FEATURES) feature rows of (M, N, K, batch) sizes, as the tree reads them."""
+    s = np.ascontiguousarray(np.asarray(sizes, np.int64).reshape(-1, 4))
+    out = np.zeros((s.shape[0], TREE_FEATURES), np.float64)
+    check(_lib.kselect_selector_features(s.shape[0], s.ctypes.data_as(ctypes.POINTER(i64)),
+                                         out.ctypes.data_as(ctypes.POINTER(f64))), "kselect_selector_features")
+    return out
+
+
+def best_labels(perf: np.ndarray, cols) -> np.ndarray:
+    """Per row of perf, the index into cols of its best column (lowest on ties)."""
+    P, pP = _arr(perf, np.float64, f64)
+    c, pc = _arr(cols, np.int32, i32)
+    out = np.zeros(P.shape[0], np.int32)
+    check(_lib.kselect_best_labels(P.shape[0], P.shape[1], pP, len(c), pc, out.ctypes.data_as(ctypes.POINTER(i32))),
+          "kselect_best_labels")
+    return out
+
+
 def tree_train(features: np.ndarray, labels: np.ndarray, n_classes: int, max_depth=None, min_leaf=1,
                max_nodes=8192) -> list[dict]:
     F, pF = _arr(features, np.float64, f64)
-    assert F.ndim == 2 and F.shape[1] == 4
+    assert F.ndim == 2 and F.shape[1] == TREE_FEATURES
     y, py = _arr(labels, np.int32, i32)
     nodes = (TreeNode * max_nodes)()
     cnt = i32()
@@ -526,12 +559,12 @@ def tree_train(features: np.ndarray, labels: np.ndarray, n_classes: int, max_dep
 
 def tree_train_rf(features: np.ndarray, labels: np.ndarray, n_classes: int, max_features: int, draws: np.ndarray,
                   max_depth=None, min_leaf=1, max_nodes=8192) -> list[dict]:
-    """One random-forest tree; draws: (>= max_nodes, 4) uint32, row j for node j."""
+    """One random-forest tree; draws: (>= max_nodes, TREE_FEATURES) uint32, row j for node j."""
     F, pF = _arr(features, np.float64, f64)
-    assert F.ndim == 2 and F.shape[1] == 4
+    assert F.ndim == 2 and F.shape[1] == TREE_FEATURES
     y, py = _arr(labels, np.int32, i32)
     d = np.ascontiguousarray(draws, np.uint32)
-    assert d.ndim == 2 and d.shape[1] == 4 and d.shape[0] >= max_nodes
+    assert d.ndim == 2 and d.shape[1] == TREE_FEATURES and d.shape[0] >= max_nodes
     nodes = (TreeNode * max_nodes)()
     cnt = i32()
     check(_lib.kselect_tree_train_rf(F.shape[0], pF, py, n_classes, -1 if max_depth is None else max_depth, min_leaf,
@@ -586,9 +619,22 @@ class GroupedPlan:
             pass
 
 
-def gemm_grouped(cid: int, problems, stream=None) -> None:
+def gemm_grouped_with_config(cid: int, problems, stream=None) -> None:
+    """One-shot grouped launch with an explicit config (plans, runs, synchronises)."""
     arr = _problems(problems)
-    check(_lib.gemm_grouped(cid, len(problems), arr, stream_handle(stream)), "gemm_grouped")
+    check(_lib.gemm_grouped_with_config(cid, len(problems), arr, stream_handle(stream)), "gemm_grouped_with_config")
+
+
+def gemm_grouped(handle: Handle, problems, precision: int, stream=None) -> None:
+    """The group's tile config picked by the handle's group selector, launched
+    asynchronously on `stream` (capturable once the handle's workspace fits)."""
+    arr = _problems(problems)
+    check(_lib.gemm_grouped(handle.value, len(problems), arr, precision, stream_handle(stream)), "gemm_grouped")
+
+
+def gemm_grouped_reserve(handle: Handle, problems, precision: int) -> None:
+    arr = _problems(problems)
+    check(_lib.gemm_grouped_reserve(handle.value, len(problems), arr, precision), "gemm_grouped_reserve")
 
 
 # ---------------------------------------------------------------- learned selector
@@ -600,14 +646,36 @@ def mlp_forward(params, X, Y, stream=None) -> None:
     check(_lib.mlp_forward(X.shape[0], ptr(params), ptr(X), ptr(Y), stream_handle(stream)), "mlp_forward")
 
 
+def _check_mlp_loss_args(where, params, X, T, mask, grad, loss) -> int:
+    """The C entry points take raw pointers and n: a tensor of the wrong shape,
+    type, layout or device would be read out of bounds on the GPU, so every
+    argument is checked here first (GEMM_ERR_INVALID_ARG).  Returns n."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None
+
+    def ok(t, shape):
+        return (isinstance(t, torch.Tensor) and t.dtype == torch.float32 and t.is_contiguous()
+                and t.device == dev and tuple(t.shape) == shape)
+
+    n = X.shape[0] if isinstance(X, torch.Tensor) and X.dim() == 2 else -1
+    good = (n >= 1 and ok(params, (MLP_PARAMS,)) and ok(X, (n, 7)) and ok(T, (n, 8))
+            and (mask is None or ok(mask, (n, 8))) and ok(grad, (MLP_PARAMS,)) and ok(loss, (1,)))
+    if not good:
+        raise KSelectError(-1, f"{where}: params and grad must be ({MLP_PARAMS},), X (n, 7), T and mask (n, 8), "
+                               f"loss (1,): float32, contiguous, on the current CUDA device")
+    return n
+
+
 def mlp_loss_grad(params, X, T, mask, grad, loss, stream=None) -> None:
-    check(_lib.mlp_loss_grad(X.shape[0], ptr(params), ptr(X), ptr(T), ptr(mask), ptr(grad), ptr(loss),
+    n = _check_mlp_loss_args("mlp_loss_grad", params, X, T, mask, grad, loss)
+    check(_lib.mlp_loss_grad(n, ptr(params), ptr(X), ptr(T), ptr(mask), ptr(grad), ptr(loss),
                              stream_handle(stream)), "mlp_loss_grad")
 
 
 def mlp_loss_grad_noalloc(params, X, T, mask, grad, loss, stream=None) -> None:
     """mlp_loss_grad without device allocation (fixed in-library scratch, n <= 8192)."""
-    check(_lib.mlp_loss_grad_noalloc(X.shape[0], ptr(params), ptr(X), ptr(T), ptr(mask), ptr(grad), ptr(loss),
+    n = _check_mlp_loss_args("mlp_loss_grad_noalloc", params, X, T, mask, grad, loss)
+    check(_lib.mlp_loss_grad_noalloc(n, ptr(params), ptr(X), ptr(T), ptr(mask), ptr(grad), ptr(loss),
                                      stream_handle(stream)), "mlp_loss_grad_noalloc")
 
 
@@ -637,4 +705,5 @@ def exported_symbols() -> list[str]:
             "gemm_benchmark_configs", "gemm_device_status", "kselect_wait_selftest", "kselect_normalise", "kselect_kmeans", "kselect_score",
             "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_im2col3x3_nchw", "kselect_bias_act_nchw", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_regress", "kselect_tree_train", "kselect_tree_train_rf", "kselect_spectral_embedding", "kselect_cluster_geomean", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
-            "gemm_grouped_plan_destroy", "gemm_grouped", "gemm_grouped_select"]
+            "gemm_grouped_plan_destroy", "gemm_grouped", "gemm_grouped_with_config", "gemm_grouped_reserve",
+            "gemm_grouped_select", "kselect_selector_features", "kselect_best_labels"]

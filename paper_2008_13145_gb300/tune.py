@@ -61,7 +61,9 @@ def sweep(shapes: list[wl.Shape], precision: int, out_path: str, seed: int = 0, 
           min_total_ms: float = 2.0, config_ids: list[int] | None = None, log=sys.stderr,
           shard: tuple[int, int] = (0, 1)) -> np.ndarray | None:
     """Benchmark every config on every shape; append one JSON line per shape
-    to out_path and skip shapes already there (resume).  Returns GFLOP/s (n x c).
+    to out_path and skip shapes already there (resume; a partial last line, as a
+    sweep killed while writing leaves it, is dropped and its shape re-run).
+    Returns GFLOP/s (n x c).
     With shard = (k, n) only the shapes with index % n == k are run (one box's
     part of a sweep split over several; `merge_sweeps` joins the files) and
     None is returned."""
@@ -70,11 +72,23 @@ def sweep(shapes: list[wl.Shape], precision: int, out_path: str, seed: int = 0, 
     ids = list(config_ids) if config_ids is not None else ks.config_ids(precision)
     done = {}
     if os.path.exists(out_path):
-        for line in open(out_path):
-            if line.strip():
+        with open(out_path) as f:
+            text = f.read()
+        lines = text.split("\n")
+        keep = []
+        for line in lines:
+            if not line.strip():
+                continue
+            try:
                 r = json.loads(line)
-                if r["config_ids"] == ids:
-                    done[r["i"]] = r
+            except json.JSONDecodeError:
+                break  # only the last line can be partial; everything after it is dropped
+            keep.append(line)
+            if r["config_ids"] == ids:
+                done[r["i"]] = r
+        if len(keep) != sum(1 for x in lines if x.strip()) or (text and not text.endswith("\n")):
+            with open(out_path, "w") as f:
+                f.write("".join(x + "\n" for x in keep))
     t0 = time.time()
     with open(out_path, "a") as f:
         for i, sh in enumerate(shapes):
@@ -267,13 +281,14 @@ def prune_by(method: str, perf_train: np.ndarray, shapes_train, k: int, seed: in
 
 
 def features(shapes) -> np.ndarray:
-    return np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
+    """The selector's feature rows of the sizes (computed by the library)."""
+    return _ks().selector_features([[s.M, s.N, s.K, s.batch] for s in shapes])
 
 
 def train_tree(perf_train: np.ndarray, shapes_train, cols: list[int], tree: str = "B") -> list[dict]:
     """Section 5.1: label each training size with its best deployed kernel and fit the tree."""
     ks = _ks()
-    y = np.argmax(perf_train[:, cols], axis=1).astype(np.int32)
+    y = ks.best_labels(perf_train, cols)
     depth, leaf = TREES[tree]
     return ks.tree_train(features(shapes_train), y, len(cols), depth, leaf)
 
@@ -297,13 +312,13 @@ def train_forest(perf_train: np.ndarray, shapes_train, cols: list[int], n_trees:
                  seed: int = 0) -> list[list[dict]]:
     """Random-forest selector (Tables 1-2's RandomForest as a runtime classifier):
     n_trees type-A trees, each on a bootstrap of the training sizes with
-    max_features of the 4 size features per node, all draws seeded inputs."""
+    max_features of the selector's features per node, all draws seeded inputs."""
     ks = _ks()
-    y = np.argmax(perf_train[:, cols], axis=1).astype(np.int32)
+    y = ks.best_labels(perf_train, cols)
     F = features(shapes_train)
     rng = wl.rng_for(seed, 91)
     boot = rng.integers(0, len(y), (n_trees, len(y)))
-    draws = rng.integers(0, 2 ** 32, (n_trees, 8192, 4), dtype=np.uint64).astype(np.uint32)
+    draws = rng.integers(0, 2 ** 32, (n_trees, 8192, ks.TREE_FEATURES), dtype=np.uint64).astype(np.uint32)
     return [ks.tree_train_rf(F[boot[b]], y[boot[b]], len(cols), max_features, draws[b], None, 1)
             for b in range(n_trees)]
 
@@ -334,9 +349,9 @@ def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard"
     dep = {"precision": precision, "config_ids": [ids[c] for c in pr["cols"]], "nodes": nodes}
     ev = evaluate(perf[te], [shapes[i] for i in te], dep, ids)
     # Benchmarked (training) sizes keep their exhaustive-best kernel at run time.
-    dep["known"] = [[shapes[i].M, shapes[i].N, shapes[i].K, shapes[i].batch, ids[int(np.argmax(perf[i]))]]
-                    for i in tr]
     ks = _ks()
+    best = ks.best_labels(perf[tr], list(range(len(ids))))
+    dep["known"] = [[shapes[i].M, shapes[i].N, shapes[i].K, shapes[i].batch, ids[int(b)]] for i, b in zip(tr, best)]
     topn = [int(c) for c in ks.top_n(perf[tr].astype(np.float32), len(pr["cols"]))]
     import torch
     ev["top_n"] = ks.score(torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda(), topn)
@@ -469,7 +484,7 @@ def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, spl
     decision trees A/B/C, 1/3/7 nearest neighbours on the performance model's
     features, bagged trees (n_bag bootstrap trees of type A, majority vote, from
     seeded draws), a random forest (the same bootstraps, each node limited to 2
-    of the 4 features) and, for k <= 8, the MLP performance model."""
+    of the selector's features) and, for k <= 8, the MLP performance model."""
     import torch
     ks = _ks()
     shapes, perf, ids, prec = load_table(table_path)
@@ -480,7 +495,8 @@ def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, spl
     F_tr, F_te = features(s_tr), features(s_te)
     rng = wl.rng_for(seed, 61)
     boot = rng.integers(0, len(tr), (n_bag, len(tr)))
-    rf_draws = wl.rng_for(seed, 81).integers(0, 2 ** 32, (n_bag, 8192, 4), dtype=np.uint64).astype(np.uint32)
+    rf_draws = wl.rng_for(seed, 81).integers(0, 2 ** 32, (n_bag, 8192, ks.TREE_FEATURES),
+                                             dtype=np.uint64).astype(np.uint32)
     out = {"k": list(k_values), "deployed_max": [], "classifiers": {}}
 
     def add(name, cols_chosen):
@@ -495,7 +511,7 @@ def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, spl
     for k in k_values:
         cols = prune_pca(perf[tr], k, seed)["cols"]
         cfg_ids = [ids[c] for c in cols]
-        y = np.argmax(perf[tr][:, cols], axis=1).astype(np.int32)
+        y = ks.best_labels(perf[tr], cols)
         out["deployed_max"].append(ks.score(P, cols)["geomean"])
         for name, (depth, leaf) in TREES.items():
             add(f"DecisionTree{name}", [cols[j] for j in tree_predict(ks.tree_train(F_tr, y, k, depth, leaf), F_te)])
@@ -646,9 +662,9 @@ def grouped_study(family: str, sweep_path: str, n_groups: int = 100, k: int = 4,
     ids = ks.config_ids(ks.PRECISIONS[family])
     tr, te = wl.train_test_split(n_groups, split_seed)
     pr = prune(perf[tr], k, seed)
-    y = np.argmax(perf[tr][:, pr["cols"]], axis=1).astype(np.int32)
+    y = ks.best_labels(perf[tr], pr["cols"])
     depth, leaf = TREES[tree]
-    nodes = ks.tree_train(F[tr], y, len(pr["cols"]), depth, leaf)
+    nodes = ks.tree_train(ks.selector_features(F[tr]), y, len(pr["cols"]), depth, leaf)
     dep = {"precision": ks.PRECISIONS[family], "config_ids": [ids[c] for c in pr["cols"]], "nodes": nodes}
     h = ks.Handle(dep)
     col = {c: j for j, c in enumerate(ids)}

@@ -225,3 +225,20 @@ def sample_positions(shape: Shape, n_rows: int, n_cols: int, seed: int) -> np.nd
             pos.append(np.stack([np.full(shape.M, b), np.arange(shape.M), np.full(shape.M, j)], 1))
     p = np.unique(np.concatenate(pos, 0).astype(np.int64), axis=0)
     return p
+
+
+def band_positions(shape: Shape, band_m: int, band_n: int, seed: int) -> np.ndarray:
+    """Sampled output entries (b, i, j) that meet every band_m x band_n output
+    tile: per batch entry, one seeded row inside each band of band_m rows x all
+    columns, plus one seeded column inside each band of band_n columns x all
+    rows (duplicates removed)."""
+    rng = rng_for(seed, 13)
+    pos = []
+    for b in range(shape.batch):
+        for r0 in range(0, shape.M, band_m):
+            i = r0 + int(rng.integers(0, min(band_m, shape.M - r0)))
+            pos.append(np.stack([np.full(shape.N, b), np.full(shape.N, i), np.arange(shape.N)], 1))
+        for c0 in range(0, shape.N, band_n):
+            j = c0 + int(rng.integers(0, min(band_n, shape.N - c0)))
+            pos.append(np.stack([np.full(shape.M, b), np.arange(shape.M), np.full(shape.M, j)], 1))
+    return np.unique(np.concatenate(pos, 0).astype(np.int64), axis=0)

@@ -105,13 +105,18 @@ def test_split_choice_invariants(ks):
 def test_tc_config_space(ks):
     for prec in (ks.PREC_TF32, ks.PREC_BF16, ks.PREC_F32X3):
         ids = ks.config_ids(prec)
-        assert len(ids) == 18 and len(set(ids)) == 18
+        assert len(ids) == 9 and len(set(ids)) == 9
+        assert ids == [1000 + 100 * (prec - 1) + 2 * i for i in range(9)]
         combos = {tuple(ks.config_params(c)[1:6]) for c in ids}
-        assert len(combos) == 18
+        assert len(combos) == 9
         for c in ids:
             p = ks.config_params(c)
             assert p[0] == prec and p[1] == 128 and p[2] in (64, 128, 256) and p[4] in (2, 3, 4)
-            assert p[3] == (32 if prec == ks.PREC_TF32 else 64) and p[5] in (0, 1)
+            assert p[3] == (32 if prec == ks.PREC_TF32 else 64) and p[5] == 0
+            # the odd slot after each id is reserved: no kernel
+            with pytest.raises(ks.KSelectError) as e:
+                ks.config_params(c + 1)
+            assert e.value.status == -6
     with pytest.raises(ks.KSelectError):
         ks.config_params(999)
 
@@ -123,17 +128,20 @@ def nodes_to_dicts(nodes):
 
 def test_select_kernel_walks_the_tree_like_the_oracle(ks):
     rng = np.random.default_rng(0)
-    F = np.exp(rng.uniform(np.log(16), np.log(4096), (300, 4))).round()
-    F[:, 3] = rng.choice([1, 2, 4, 8, 16], 300)
-    y = rng.integers(0, 5, 300)
+    S = np.exp(rng.uniform(np.log(16), np.log(4096), (300, 4))).round()
+    S[:, 3] = rng.choice([1, 2, 4, 8, 16], 300)
+    F = osel.selector_features(S)
+    # labels that depend on the output count, so the trees split on it
+    y = (rng.integers(0, 3, 300) + (F[:, 4] > np.median(F[:, 4])) * 2).astype(np.int64)
     for depth, leaf in osel.TREES.values():
         nodes = osel.tree_train(F, y, 5, depth, leaf)
+        assert any(n["feature"] == 4 for n in nodes)
         ids = [3, 77, 150, 301, 575]
         h = ks.Handle({"precision": ks.PREC_F32, "config_ids": ids, "nodes": nodes_to_dicts(nodes)})
-        Ft = np.exp(rng.uniform(np.log(16), np.log(4096), (500, 4))).round()
-        Ft[:, 3] = rng.choice([1, 2, 4, 8, 16], 500)
-        want = osel.tree_predict(nodes, Ft)
-        got = [ks.select_kernel(h, *map(int, f)) for f in Ft]
+        St = np.exp(rng.uniform(np.log(16), np.log(4096), (500, 4))).round()
+        St[:, 3] = rng.choice([1, 2, 4, 8, 16], 500)
+        want = osel.tree_predict(nodes, osel.selector_features(St))
+        got = [ks.select_kernel(h, *map(int, s)) for s in St]
         assert got == [ids[w] for w in want]
 
 
@@ -152,21 +160,21 @@ def test_deployment_validation(ks):
             ks.Handle(bad)
         assert e.value.status == code
     with pytest.raises(ks.KSelectError) as e:
-        ks.Handle({"precision": 0, "config_ids": [1, 1001], "nodes": []})
+        ks.Handle({"precision": 0, "config_ids": [1, 1002], "nodes": []})
     assert e.value.status == -6
     with pytest.raises(ks.KSelectError) as e:
         ks.Handle({"precision": 0, "config_ids": [], "nodes": []})
     assert e.value.status == -6
     # an FP32-input handle may mix the SIMT and split-BF16 x3 families, not TF32 or BF16
-    assert ks.Handle({"precision": 0, "config_ids": [5, 1201], "nodes": []}).ids == [5, 1201]
+    assert ks.Handle({"precision": 0, "config_ids": [5, 1202], "nodes": []}).ids == [5, 1202]
     with pytest.raises(ks.KSelectError):
-        ks.Handle({"precision": 3, "config_ids": [1101], "nodes": []})
+        ks.Handle({"precision": 3, "config_ids": [1102], "nodes": []})
     # benchmarked sizes take their measured best kernel, the rest the tree's choice
-    hk = ks.Handle({**ok, "known": [[100, 5, 5, 1, 77], [7, 8, 9, 2, 1201], [100, 5, 5, 1, 3]]})
-    assert ks.select_kernel(hk, 100, 5, 5, 1) == 77 and ks.select_kernel(hk, 7, 8, 9, 2) == 1201
+    hk = ks.Handle({**ok, "known": [[100, 5, 5, 1, 77], [7, 8, 9, 2, 1202], [100, 5, 5, 1, 3]]})
+    assert ks.select_kernel(hk, 100, 5, 5, 1) == 77 and ks.select_kernel(hk, 7, 8, 9, 2) == 1202
     assert ks.select_kernel(hk, 100, 5, 5, 2) == 1 and ks.select_kernel(hk, 101, 5, 5, 1) == 2
     with pytest.raises(ks.KSelectError):
-        ks.Handle({**ok, "known": [[1, 1, 1, 1, 1001]]})
+        ks.Handle({**ok, "known": [[1, 1, 1, 1, 1002]]})
     h0 = ks.Handle({"precision": 0, "config_ids": [42], "nodes": []})
     assert ks.select_kernel(h0, 1, 1, 1, 1) == 42
 
@@ -211,3 +219,21 @@ def test_argument_validation_needs_no_device(ks):
         assert ks._lib.gemm_host_pipeline(h.value, 2, arr, None) == -1, bad
     assert ks._lib.gemm_host_pipeline(h.value, -1, None, None) == -1
     assert ks._lib.gemm_host_pipeline(None, 0, None, None) == -1
+
+
+def test_mlp_wrappers_reject_bad_arguments_before_any_launch(ks):
+    """The loss/gradient wrappers check shapes, type, layout and device before
+    passing raw pointers on (GEMM_ERR_INVALID_ARG, nothing launched).  Host
+    tensors are never on the current CUDA device, so even the well-shaped set
+    is refused here."""
+    import torch
+    good = dict(params=torch.zeros(5192), X=torch.zeros(4, 7), T=torch.zeros(4, 8), mask=None,
+                grad=torch.zeros(5192), loss=torch.zeros(1))
+    bad = [dict(good, params=torch.zeros(5191)), dict(good, X=torch.zeros(4, 6)), dict(good, T=torch.zeros(5, 8)),
+           dict(good, mask=torch.zeros(4, 7)), dict(good, X=torch.zeros(4, 7, dtype=torch.float64)),
+           dict(good, X=torch.zeros(7, 4).t()), dict(good, loss=torch.zeros(2)), dict(good, X=torch.zeros(0, 7))]
+    for fn in (ks.mlp_loss_grad, ks.mlp_loss_grad_noalloc):
+        for args in bad + [good]:
+            with pytest.raises(ks.KSelectError) as e:
+                fn(**args)
+            assert e.value.status == -1

@@ -4,8 +4,9 @@ The 200 held-out shapes of the 1,000-shape grid (M, N, K up to 4096, batch up to
 16, every transpose), each GEMM selected by the committed deployment through the
 handle exactly as the bench's timed step does (plain FP32 kernels and the split-K
 kind included).  Inputs are drawn on the host (seeded) and uploaded; the oracle
-evaluates sampled outputs one by one: per batch entry 2 seeded rows x all columns
-plus 2 seeded columns x all rows."""
+evaluates sampled outputs one by one: per batch entry one seeded row in every
+band of 64 rows x all columns plus one seeded column in every band of 64
+columns x all rows, so every output tile of 64 x 64 or more is met."""
 import json
 import os
 
@@ -32,8 +33,9 @@ def test_bench_workload_sampled(lib):
     for n, i in enumerate(te):
         sh = g[i]
         A, B, _ = wl.gemm_inputs(sh, seed=5000 + n, ld_multiple=8)
-        pos = wl.sample_positions(sh, 2, 2, seed=n)
+        pos = wl.band_positions(sh, 64, 64, seed=n)
         ldc = wl.round_up(sh.N, 4)
+        refs = {}  # the oracle's entries, once per input type
         for name, tol, bf16, h in handles:
             tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
             Ah, Bh = A, B
@@ -45,8 +47,10 @@ def test_bench_workload_sampled(lib):
             ks.gemm(h, sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, tA, A.shape[2], tB, B.shape[2], 0.0, C, ldc,
                     sh.batch)
             got = C.cpu().numpy()[pos[:, 0], pos[:, 1], pos[:, 2]]
-            ref, den = og.gemm_entries(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, Ah, Bh, 0.0, None, pos,
-                                       nthreads=nthreads)
+            if bf16 not in refs:
+                refs[bf16] = og.gemm_entries(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.0, Ah, Bh, 0.0, None, pos,
+                                             nthreads=nthreads)
+            ref, den = refs[bf16]
             err = og.error_ratio(got, ref, den)
             assert err <= tol, (name, sh, ks.select_kernel(h, sh.M, sh.N, sh.K, sh.batch), err)
             worst[name] = max(worst[name], err)

@@ -17,8 +17,9 @@ pytestmark = pytest.mark.gpu
 
 M, N = 64, 1536  # X is M x N; every P is N x N
 # (config, transB): SIMT staged / direct, split-K kind, TF32 (B through the
-# pre-pass when stored K x N), TF32 CTA pair, x3 single CTA and pair.
-CHAIN = [(533, "N"), (2533, "T"), (1017, "N"), (369, "T"), (1216, "N"), (2533, "N"), (1016, "T"), (1217, "T"),
+# pre-pass when stored K x N) in BN 128 and 256 tiles, x3 in BN 256 tiles
+# with 4 and 3 stages.
+CHAIN = [(533, "N"), (2533, "T"), (1010, "N"), (369, "T"), (1216, "N"), (2533, "N"), (1016, "T"), (1214, "T"),
          (368, "N")]
 
 

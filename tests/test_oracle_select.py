@@ -318,6 +318,22 @@ def test_cluster_geomean_centres():
 
 
 # ---------------------------------------------------------------- random-forest trees (Section 5.1 classifiers)
+def test_selector_features_by_hand():
+    """The sizes pass through; the fifth column is the number of outputs."""
+    F = osel.selector_features([[3, 5, 7, 2], [4096, 4096, 16, 16]])
+    assert F.shape == (2, 5)
+    assert F[0].tolist() == [3, 5, 7, 2, 30]
+    assert F[1].tolist() == [4096, 4096, 16, 16, 4096 * 4096 * 16]  # 2^28: exact in FP64
+
+
+def test_best_labels_by_hand():
+    """Position in the deployed list of the fastest deployed column, first on ties."""
+    perf = np.array([[1.0, 5.0, 5.0, 0.0], [9.0, 2.0, 3.0, 0.0], [0.0, 0.0, 0.0, 0.0]])
+    assert osel.best_labels(perf, [2, 1]).tolist() == [0, 0, 0]  # 5 vs 5: first; 3 vs 2; all zero: first
+    assert osel.best_labels(perf, [1, 0]).tolist() == [0, 1, 0]
+    assert osel.best_labels(perf, [3, 0, 2]).tolist() == [2, 1, 0]
+
+
 def test_feature_subset_by_hand():
     # step 0 swaps entries 0 and 0 + 5 % 4 = 1 -> [1, 0, 2, 3]; step 1 swaps 1 and 1 + 7 % 3 = 2 -> [1, 2, 0, 3]
     assert osel.feature_subset(np.array([5, 7, 0, 0]), 4, 2) == [1, 2]

@@ -29,7 +29,7 @@ def same_tree(a, b):
 def test_tree_matches_oracle_with_many_ties(ks, seed, tree):
     rng = np.random.default_rng(seed)
     n = 150
-    F = rng.integers(1, 7, (n, 4)).astype(np.float64)  # few distinct values: many tied splits
+    F = rng.integers(1, 7, (n, 5)).astype(np.float64)  # few distinct values: many tied splits
     y = rng.integers(0, 5, n)
     depth, leaf = osel.TREES[tree]
     same_tree(ks.tree_train(F, y, 5, depth, leaf), osel.tree_train(F, y, 5, depth, leaf))
@@ -39,29 +39,45 @@ def test_tree_matches_oracle_with_many_ties(ks, seed, tree):
 def test_tree_matches_oracle_on_grid_sizes(ks, tree):
     from paper_2008_13145_gb300 import workloads as wl
     g = wl.shape_grid(400, 21)
-    F = np.array([[s.M, s.N, s.K, s.batch] for s in g], np.float64)
+    F = osel.selector_features([[s.M, s.N, s.K, s.batch] for s in g])
     y = ((F[:, 0] * F[:, 1] > 1e5).astype(int) + (F[:, 2] > 700).astype(int) * 2
          + (np.random.default_rng(2).random(400) < 0.15))
     depth, leaf = osel.TREES[tree]
     same_tree(ks.tree_train(F, y, 5, depth, leaf), osel.tree_train(F, y, 5, depth, leaf))
 
 
+def test_selector_features_and_labels_match_oracle(ks):
+    """The feature rows and the best-deployed-kernel labels the tuner trains on
+    are the library's, bit for bit the oracle's (ties included)."""
+    from paper_2008_13145_gb300 import workloads as wl
+    sizes = [[s.M, s.N, s.K, s.batch] for s in wl.shape_grid(500, 3)] + [[0, 7, 1, 1], [4096, 4096, 4096, 65535]]
+    assert np.array_equal(ks.selector_features(sizes), osel.selector_features(sizes))
+    rng = np.random.default_rng(4)
+    perf = rng.integers(0, 6, (300, 40)).astype(np.float64)  # many ties
+    for cols in ([0], [5, 3, 9, 1], list(range(40)), [39, 0, 17, 17]):
+        assert list(ks.best_labels(perf, cols)) == list(osel.best_labels(perf, cols))
+    with pytest.raises(ks.KSelectError):
+        ks.best_labels(perf, [40])
+    with pytest.raises(ks.KSelectError):
+        ks.selector_features([[1, -2, 3, 4]])
+
+
 def test_tree_pure_and_single_sample(ks):
-    F = np.array([[1.0, 2, 3, 4]])
+    F = np.array([[1.0, 2, 3, 4, 5]])
     assert ks.tree_train(F, np.array([2]), 3) == [{"feature": -1, "threshold": 0.0, "left": -1, "right": -1,
                                                     "label": 2}]
-    F = np.tile(np.array([[5.0, 5, 5, 5]]), (6, 1))
+    F = np.tile(np.array([[5.0, 5, 5, 5, 5]]), (6, 1))
     nodes = ks.tree_train(F, np.array([0, 1, 1, 0, 1, 0]), 2)
     assert len(nodes) == 1 and nodes[0]["label"] == 0  # identical features: no split, tie -> lowest class
 
 
 def test_tree_rejects_bad_input(ks):
     with pytest.raises(ks.KSelectError):
-        ks.tree_train(np.ones((3, 4)), np.array([0, 5, 1]), 2)
+        ks.tree_train(np.ones((3, 5)), np.array([0, 5, 1]), 2)
     with pytest.raises(ks.KSelectError):
-        ks.tree_train(np.full((3, 4), np.nan), np.array([0, 1, 1]), 2)
+        ks.tree_train(np.full((3, 5), np.nan), np.array([0, 1, 1]), 2)
     with pytest.raises(ks.KSelectError) as e:  # too many nodes for the output buffer
-        ks.tree_train(np.arange(400, dtype=float).reshape(100, 4), np.arange(100) % 2, 2, max_nodes=5)
+        ks.tree_train(np.arange(500, dtype=float).reshape(100, 5), np.arange(100) % 2, 2, max_nodes=5)
     assert e.value.status == -2
 
 
@@ -98,7 +114,7 @@ def test_tree_regress_matches_oracle(ks, seed, k):
     """Tie-free sizes, float32 performance vectors: the same leaves in the same
     order (exact labels) and leaf means within float rounding."""
     rng = np.random.default_rng(100 + seed)
-    F = rng.permutation(4096)[:4 * 90].reshape(90, 4).astype(np.float64) + 16
+    F = rng.permutation(4096)[:5 * 90].reshape(90, 5).astype(np.float64) + 16
     Y = (rng.random((90, 12)) ** 3).astype(np.float32)
     labels, centres = ks.tree_regress(F, Y, k)
     ref_labels, ref_centres = osel.tree_regression_partition(F, Y.astype(np.float64), k)
@@ -111,7 +127,7 @@ def test_tree_regress_on_grid_sizes_with_ties(ks):
     same partition as the oracle."""
     from paper_2008_13145_gb300 import workloads as wl
     shapes = wl.shape_grid(300, 9)
-    F = np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
+    F = osel.selector_features([[s.M, s.N, s.K, s.batch] for s in shapes])
     rng = np.random.default_rng(9)
     perf = rng.random((300, 20)) * np.log(F[:, :1]) * np.sqrt(F[:, 3:4])
     Y = osel.normalise(perf, "standard").astype(np.float32)
@@ -122,7 +138,7 @@ def test_tree_regress_on_grid_sizes_with_ties(ks):
 
 
 def test_tree_regress_constant_leaves_stop(ks):
-    F = np.array([[16, 16, 16, 1], [32, 16, 16, 1], [64, 16, 16, 1], [128, 16, 16, 1]], np.float64)
+    F = osel.selector_features([[16, 16, 16, 1], [32, 16, 16, 1], [64, 16, 16, 1], [128, 16, 16, 1]])
     Y = np.array([[1, 0], [1, 0], [0, 1], [0, 1]], np.float32)
     labels, centres = ks.tree_regress(F, Y, 4)
     assert labels.tolist() == [0, 0, 1, 1] and np.array_equal(centres, [[1, 0], [0, 1]])
@@ -134,21 +150,21 @@ def test_tree_regress_constant_leaves_stop(ks):
 
 # ---------------------------------------------------------------- random-forest trees (Section 5.1 classifiers)
 @pytest.mark.parametrize("seed", range(4))
-@pytest.mark.parametrize("m", [1, 2, 3, 4])
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
 def test_random_forest_tree_matches_oracle(ks, seed, m):
     """Node for node, with bootstrap-like repeated rows and the same per-node draws."""
     from paper_2008_13145_gb300 import workloads as wl
     rng = np.random.default_rng(200 + seed)
     shapes = wl.shape_grid(400, 10 + seed)
-    F = np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
+    F = osel.selector_features([[s.M, s.N, s.K, s.batch] for s in shapes])
     y = (np.log(F[:, 0]) + np.log(F[:, 1]) > 12).astype(np.int32) + (F[:, 3] > 4).astype(np.int32)
     boot = rng.integers(0, 400, 400)
-    draws = rng.integers(0, 2 ** 32, (8192, 4), dtype=np.uint64).astype(np.uint32)
+    draws = rng.integers(0, 2 ** 32, (8192, 5), dtype=np.uint64).astype(np.uint32)
     for depth, leaf in ((None, 1), (6, 3)):
         got = ks.tree_train_rf(F[boot], y[boot], 3, m, draws, depth, leaf)
         want = osel.tree_train(F[boot], y[boot], 3, depth, leaf, max_features=m, draws=draws)
         same_tree(got, want)
-        if m == 4:
+        if m == 5:
             same_tree(got, ks.tree_train(F[boot], y[boot], 3, depth, leaf))
 
 
@@ -158,22 +174,22 @@ def test_forest_selector_votes_like_the_oracle(ks):
     from paper_2008_13145_gb300 import workloads as wl
     rng = np.random.default_rng(77)
     shapes = wl.shape_grid(300, 21)
-    F = np.array([[s.M, s.N, s.K, s.batch] for s in shapes], np.float64)
+    F = osel.selector_features([[s.M, s.N, s.K, s.batch] for s in shapes])
     y = ((np.log(F[:, 0]) > 6).astype(np.int32) + (np.log(F[:, 2]) > 6.5) * 2 + (F[:, 3] > 4)) % 4
     y = y.astype(np.int32)
     trees = []
     for b in range(9):
         boot = rng.integers(0, 300, 300)
-        draws = rng.integers(0, 2 ** 32, (8192, 4), dtype=np.uint64).astype(np.uint32)
+        draws = rng.integers(0, 2 ** 32, (8192, 5), dtype=np.uint64).astype(np.uint32)
         trees.append(ks.tree_train_rf(F[boot], y[boot], 4, 2, draws))
     ids = [11, 22, 33, 44]
     h = ks.Handle({"precision": 0, "config_ids": ids, "nodes": [], "forest": trees})
-    Q = np.array([[s.M, s.N, s.K, s.batch] for s in wl.shape_grid(500, 22)], np.float64)
+    Q = osel.selector_features([[s.M, s.N, s.K, s.batch] for s in wl.shape_grid(500, 22)])
     votes = np.zeros((len(Q), 4), np.int64)
     for t in trees:
         votes[np.arange(len(Q)), osel.tree_predict(t, Q)] += 1
     want = [ids[int(np.argmax(v))] for v in votes]  # argmax: lowest label among the tied maxima
-    got = [ks.select_kernel(h, *map(int, q)) for q in Q]
+    got = [ks.select_kernel(h, *map(int, q[:4])) for q in Q]
     assert got == want
 
 
@@ -209,7 +225,7 @@ def test_grouped_select_reads_group_medians(ks):
     leaf = lambda c: {"feature": -1, "threshold": 0.0, "left": -1, "right": -1, "label": c}
     nodes = [{"feature": 2, "threshold": 500.0, "left": 1, "right": 2, "label": 0}, leaf(0),
              {"feature": 3, "threshold": 40.0, "left": 3, "right": 4, "label": 0}, leaf(1), leaf(2)]
-    h = ks.Handle({"precision": 2, "config_ids": [1100, 1117, 1105], "nodes": nodes})
+    h = ks.Handle({"precision": 2, "config_ids": [1100, 1116, 1104], "nodes": nodes})
     rng = np.random.default_rng(5)
     for count in (1, 2, 7, 33, 64):
         for _ in range(5):

@@ -4,8 +4,8 @@ One A shared by every batch entry (stride 0), B entries separated by NaN-filled
 gaps (one gap a multiple of 16 bytes, one not, so the unvectorised loads run
 too) and C entries separated by sentinel gaps that must survive.  Every kernel
 family: FP32 SIMT (staged and direct), the split-K kind, TF32, BF16 and
-split-BF16 x3, single CTA and CTA pair (whose kernels pack non-contiguous
-batches in their pre-pass).
+split-BF16 x3 in two tile shapes (whose kernels pack non-contiguous batches in
+their pre-pass).
 Tolerances as in the per-family parity tests."""
 import numpy as np
 import pytest
@@ -16,7 +16,7 @@ from tests.gpu_helpers import SENTINEL
 
 pytestmark = pytest.mark.gpu
 CASES = [("f32 staged", 369, 1e-5), ("f32 direct", 368, 1e-5), ("split-K", 2533, 1e-5),
-         ("tf32", 1008, 5e-3), ("bf16", 1108, 2e-2), ("f32x3", 1208, 1e-5), ("f32x3 pair", 1209, 1e-5)]
+         ("tf32", 1008, 5e-3), ("bf16", 1108, 2e-2), ("f32x3", 1208, 1e-5), ("f32x3 BN 256", 1216, 1e-5)]
 
 
 @pytest.fixture(scope="module")

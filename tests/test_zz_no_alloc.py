@@ -22,10 +22,12 @@ def inputs(n, seed):
 
 def test_noalloc_matches_allocating_entry_point_twice(lib):
     import torch
+    from oracle import mlp as om
     # Two calls in a row: the second uses fewer samples, so stale partials of the
     # first call's extra blocks are still in the shared array and must not leak.
     for n, seed in ((2003, 1), (517, 2)):
-        P, X, T, mask = (torch.from_numpy(a).cuda() for a in inputs(n, seed))
+        host = inputs(n, seed)
+        P, X, T, mask = (torch.from_numpy(a).cuda() for a in host)
         g_ref = torch.empty(5192, device="cuda")
         l_ref = torch.empty(1, device="cuda")
         lib.mlp_loss_grad(P, X, T, mask, g_ref, l_ref)
@@ -37,6 +39,10 @@ def test_noalloc_matches_allocating_entry_point_twice(lib):
         assert np.all(np.isfinite(gn))
         assert np.max(np.abs(gn - gr)) <= 1e-4 * np.max(np.abs(gr))
         assert loss.item() == pytest.approx(l_ref.item(), rel=1e-5)
+        # and against the FP64 oracle of the loss and its analytic gradient
+        o_loss, o_grad = om.loss_and_grad(*(a.astype(np.float64) for a in host))
+        assert np.max(np.abs(gn - o_grad)) <= 1e-4 * np.max(np.abs(o_grad))
+        assert loss.item() == pytest.approx(o_loss, rel=1e-5)
 
 
 def test_noalloc_rejects_more_samples_than_its_scratch(lib):
