@@ -542,6 +542,15 @@ gemm_status_t kselect_tree_train(int32_t n, const double* features, const int32_
  * M, N, K, batch, transA, transB, dtype), as select_kernels_batched computes them. */
 gemm_status_t mlp_features(int32_t n, const int64_t* shapes_dev, float* X_dev, void* stream);
 
+/* Training targets from measured throughputs (perf_dev: n x d GFLOP/s, row =
+ * size, column = deployed kernel, 0 = not measured): T_dev = log(perf / row
+ * max), the natural log of Section 3.4's standard-normalised performance, and
+ * mask_dev = 1 where perf > 0, else T = 0 and mask = 0.  The model thus
+ * predicts each kernel's throughput relative to the fastest deployed kernel
+ * for the size; selection (the largest output) is unaffected by the per-size
+ * offset that absolute log-throughput would add.  All arrays device. */
+gemm_status_t mlp_targets(int32_t n, int32_t d, const float* perf_dev, float* T_dev, float* mask_dev, void* stream);
+
 /* Y_dev (n x 8) = network(X_dev). */
 gemm_status_t mlp_forward(int32_t n, const float* params_dev, const float* X_dev, float* Y_dev, void* stream);
 

@@ -1,8 +1,10 @@
 """FP64 oracle of the MLP performance model -- TEST INFRASTRUCTURE ONLY.
 
 The learned selector predicts, from a GEMM's sizes, the log-throughput of each
-deployed kernel and picks the best.  It replaces the paper's MLP classifier
-(Section 5.1, Tables 1-2) by a regressor over the deployed set.
+deployed kernel relative to the fastest deployed kernel for those sizes (the
+log of Section 3.4's standard-normalised performance) and picks the best.  It
+replaces the paper's MLP classifier (Section 5.1, Tables 1-2) by a regressor
+over the deployed set.
 
 Network: 7 inputs -> 64 ReLU -> 64 ReLU -> 8 linear outputs.  Parameters are
 one flat vector in the order W1 (7x64, row = input), b1 (64), W2 (64x64),
@@ -40,6 +42,21 @@ def features(M, N, K, batch, transA, transB, dtype) -> np.ndarray:
     return np.stack([np.log2(M) / 12.0, np.log2(N) / 12.0, np.log2(K) / 12.0, np.log2(batch) / 4.0,
                      np.asarray(transA, np.float64), np.asarray(transB, np.float64),
                      np.asarray(dtype, np.float64) / 3.0], axis=-1)
+
+
+def targets(perf):
+    """Training targets and mask of a throughput table (rows = sizes, columns =
+    deployed kernels, 0 = not measured): log(perf / row max) where measured,
+    else 0 with mask 0 -- Section 3.4's standard normalisation, in log space."""
+    perf = np.asarray(perf, np.float64)
+    mask = (perf > 0).astype(np.float64)
+    T = np.zeros_like(perf)
+    for i in range(perf.shape[0]):
+        mx = perf[i].max()
+        for j in range(perf.shape[1]):
+            if perf[i, j] > 0:
+                T[i, j] = np.log(perf[i, j] / mx)
+    return T, mask
 
 
 def forward(theta, X):

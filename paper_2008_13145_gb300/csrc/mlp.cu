@@ -194,6 +194,22 @@ __device__ __forceinline__ float feature(int q, const int64_t* sh) {
   }
 }
 
+// Training targets: per row of an n x d throughput table, log(perf / row max)
+// over the measured (perf > 0) entries, 0 elsewhere, and the mask of measured
+// entries (a row with none measured is all masked).
+__global__ void mlp_targets_kernel(int n, int d, const float* perf, float* T, float* mask) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const float* p = perf + (int64_t)r * d;
+  float mx = 0.f;
+  for (int j = 0; j < d; ++j) mx = fmaxf(mx, p[j]);
+  for (int j = 0; j < d; ++j) {
+    const bool ok = p[j] > 0.f;
+    T[(int64_t)r * d + j] = ok ? logf(p[j] / mx) : 0.f;
+    mask[(int64_t)r * d + j] = ok ? 1.f : 0.f;
+  }
+}
+
 __global__ void mlp_features_kernel(int n, const int64_t* shapes, float* X) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -342,6 +358,14 @@ gemm_status_t mlp_features(int32_t n, const int64_t* shapes, float* X, void* str
   if (n < 0 || (n > 0 && (!shapes || !X))) return GEMM_ERR_INVALID_ARG;
   if (n == 0) return GEMM_OK;
   mlp_features_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(n, shapes, X);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GEMM_OK : fail(e);
+}
+
+gemm_status_t mlp_targets(int32_t n, int32_t d, const float* perf, float* T, float* mask, void* stream) {
+  if (n < 0 || d < 1 || (n > 0 && (!perf || !T || !mask))) return GEMM_ERR_INVALID_ARG;
+  if (n == 0) return GEMM_OK;
+  mlp_targets_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(n, d, perf, T, mask);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GEMM_OK : fail(e);
 }

@@ -98,6 +98,7 @@ _sig("gemm_grouped_reserve", i32, [vp, i32, ctypes.POINTER(Problem), i32])
 _sig("gemm_grouped_select", i32, [vp, i32, ctypes.POINTER(Problem)])
 _sig("mlp_features", i32, [i32, vp, vp, vp])
 _sig("mlp_forward", i32, [i32, vp, vp, vp, vp])
+_sig("mlp_targets", i32, [i32, i32, vp, vp, vp, vp])
 _sig("mlp_loss_grad", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
 _sig("mlp_adam_step", i32, [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp])
 _sig("mlp_loss_grad_noalloc", i32, [i32, vp, vp, vp, vp, vp, vp, vp])
@@ -642,6 +643,12 @@ def mlp_features(shapes, X, stream=None) -> None:
     check(_lib.mlp_features(shapes.shape[0], ptr(shapes), ptr(X), stream_handle(stream)), "mlp_features")
 
 
+def mlp_targets(perf, T, mask, stream=None) -> None:
+    """Targets and mask (n x d, device) from a device throughput table."""
+    check(_lib.mlp_targets(perf.shape[0], perf.shape[1], ptr(perf), ptr(T), ptr(mask), stream_handle(stream)),
+          "mlp_targets")
+
+
 def mlp_forward(params, X, Y, stream=None) -> None:
     check(_lib.mlp_forward(X.shape[0], ptr(params), ptr(X), ptr(Y), stream_handle(stream)), "mlp_forward")
 
@@ -706,4 +713,4 @@ def exported_symbols() -> list[str]:
             "kselect_im2col3x3", "kselect_bias_act", "kselect_maxpool2x2", "kselect_im2col3x3_nchw", "kselect_bias_act_nchw", "kselect_knn", "kselect_representatives", "kselect_top_n", "kselect_tree_regress", "kselect_tree_train", "kselect_tree_train_rf", "kselect_spectral_embedding", "kselect_cluster_geomean", "kselect_pca", "kselect_pca_backproject", "mlp_features", "mlp_forward", "mlp_loss_grad",
             "mlp_adam_step", "mlp_loss_grad_noalloc", "mlp_train", "select_kernels_batched", "gemm_grouped_plan_create", "gemm_grouped_run",
             "gemm_grouped_plan_destroy", "gemm_grouped", "gemm_grouped_with_config", "gemm_grouped_reserve",
-            "gemm_grouped_select", "kselect_selector_features", "kselect_best_labels"]
+            "gemm_grouped_select", "kselect_selector_features", "kselect_best_labels", "mlp_targets"]

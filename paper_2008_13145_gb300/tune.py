@@ -340,6 +340,31 @@ def forest_deploy(deploy_path: str, table_path: str, n_trees: int = 16, seed: in
     return out
 
 
+def retree(deploy_path: str, table_path: str, split_seed: int = 1) -> dict:
+    """The deployment at deploy_path with its tree retrained (same deployed
+    kernels, known table, MLP and tree type) on the table's training sizes,
+    and its held-out scores recomputed."""
+    ks = _ks()
+    shapes, perf, ids, _ = load_table(table_path)
+    dep = json.load(open(deploy_path))
+    tr, te = wl.train_test_split(len(shapes), split_seed)
+    col_of = {cid: j for j, cid in enumerate(ids)}
+    cols = [col_of[c] for c in dep["config_ids"]]
+    tree = dep.get("meta", {}).get("tree", "B")
+    out = {k: v for k, v in dep.items() if k != "meta"}
+    out["nodes"] = train_tree(perf[tr], [shapes[i] for i in tr], cols, tree)
+    out.pop("forest", None)
+    ev = evaluate(perf[te], [shapes[i] for i in te], {k: v for k, v in out.items() if k != "known"}, ids)
+    meta = dict(dep.get("meta", {}))
+    import torch
+    topn = [int(c) for c in ks.top_n(perf[tr].astype(np.float32), len(cols))]
+    ev["top_n"] = ks.score(torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda(), topn)
+    meta["scores"] = {key: v for key, v in ev.items() if key != "chosen_cols"}
+    meta["features"] = "M, N, K, batch, M*N*batch"
+    out["meta"] = meta
+    return out
+
+
 def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard", split_seed: int = 1,
            method: str = "kmeans") -> dict:
     shapes, perf, ids, precision = load_table(table_path)
@@ -357,6 +382,7 @@ def deploy(table_path: str, k: int, tree: str, seed: int, norm: str = "standard"
     ev["top_n"] = ks.score(torch.from_numpy(np.ascontiguousarray(perf[te], np.float32)).cuda(), topn)
     dep["meta"] = {"k": k, "tree": tree, "norm": norm, "method": method, "kmeans_seed": seed, "split_seed": split_seed,
                    "n_train": len(tr), "n_test": len(te), "inertia": pr["inertia"],
+                   "features": "M, N, K, batch, M*N*batch",
                    "scores": {key: v for key, v in ev.items() if key != "chosen_cols"}}
     return dep
 
@@ -377,10 +403,15 @@ def mlp_features(shapes, dtype: int = 0):
 
 
 def mlp_targets(perf: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
-    """Natural-log GFLOP/s per deployed kernel and the mask of measured entries."""
-    mask = (perf > 0).astype(np.float32)
-    t = np.where(perf > 0, np.log(np.maximum(perf, 1e-30)), 0.0).astype(np.float32)
-    return t, mask
+    """Per deployed kernel, the log of its throughput relative to the fastest
+    deployed kernel for the size, and the mask of measured entries (computed
+    by the library's targets kernel)."""
+    import torch
+    ks = _ks()
+    P = torch.from_numpy(np.ascontiguousarray(perf, np.float32)).cuda()
+    T, M = torch.empty_like(P), torch.empty_like(P)
+    ks.mlp_targets(P, T, M)
+    return T.cpu().numpy(), M.cpu().numpy()
 
 
 def mlp_init(seed: int) -> np.ndarray:
@@ -396,7 +427,7 @@ def mlp_init(seed: int) -> np.ndarray:
     return np.concatenate(out).astype(np.float32)
 
 
-def mlp_train_params(X, T, mask, steps=3000, lr=3e-3, seed=0, log=None) -> tuple[np.ndarray, list]:
+def mlp_train_params(X, T, mask, steps=10000, lr=3e-3, seed=0, log=None) -> tuple[np.ndarray, list]:
     """Full-batch Adam training by the library's kernels; returns (params, loss history)."""
     import torch
     ks = _ks()
@@ -424,7 +455,7 @@ def mlp_choose(params: np.ndarray, shapes, config_ids) -> np.ndarray:
     return out.cpu().numpy()
 
 
-def mlp_study(deploy_path: str, sweep_path: str, n: int = 2500, seed: int = 4, steps: int = 3000) -> dict:
+def mlp_study(deploy_path: str, sweep_path: str, n: int = 2500, seed: int = 4, steps: int = 10000) -> dict:
     """Learned selector over the deployed set: sweep n seed-`seed` shapes over
     the deployed kernels, train on 80 %, compare MLP, tree and exhaustive on
     the held-out 20 % (fractions of the best deployed kernel)."""
@@ -433,7 +464,11 @@ def mlp_study(deploy_path: str, sweep_path: str, n: int = 2500, seed: int = 4, s
     dep = json.load(open(deploy_path))
     ids = dep["config_ids"]
     shapes = wl.shape_grid(n, seed)
-    perf = sweep(shapes, dep["precision"], sweep_path, config_ids=ids)
+    if sweep_path.endswith(".npz"):  # a table of this sweep saved earlier
+        t_shapes, perf, t_ids, _ = load_table(sweep_path)
+        assert t_ids == ids and t_shapes == shapes, "the table belongs to another deployment or grid"
+    else:
+        perf = sweep(shapes, dep["precision"], sweep_path, config_ids=ids)
     tr, te = wl.train_test_split(n, seed)
     X = mlp_features([shapes[i] for i in tr])
     T, M = mlp_targets(perf)
@@ -478,7 +513,7 @@ def pruning_study(table_path: str, k_values=range(4, 16), seed: int = 0, split_s
 
 # ---------------------------------------------------------------- classifiers (Tables 1-2 analogue)
 def classifier_study(table_path: str, k_values=(5, 6, 8, 15), seed: int = 0, split_seed: int = 1,
-                     n_bag: int = 16, mlp_steps: int = 3000) -> dict:
+                     n_bag: int = 16, mlp_steps: int = 10000) -> dict:
     """For each deployed-set size k (PCA + k-means selection, as in Section 5),
     the held-out geometric-mean fraction of the per-shape optimum reached by:
     decision trees A/B/C, 1/3/7 nearest neighbours on the performance model's
@@ -774,7 +809,7 @@ def main(argv=None):
     ml.add_argument("--deploy", required=True)
     ml.add_argument("--sweep", required=True)
     ml.add_argument("--n", type=int, default=2500)
-    ml.add_argument("--steps", type=int, default=3000)
+    ml.add_argument("--steps", type=int, default=10000)
     ml.add_argument("--out", required=True)
     cb = sub.add_parser("combine")
     cb.add_argument("--tables", nargs="+", required=True)
@@ -813,6 +848,10 @@ def main(argv=None):
     nw.add_argument("--deploy", required=True)
     nw.add_argument("--sweep", required=True)
     nw.add_argument("--out", required=True)
+    rt = sub.add_parser("retree")
+    rt.add_argument("--deploy", required=True)
+    rt.add_argument("--table", required=True)
+    rt.add_argument("--out", required=True)
     d = sub.add_parser("deploy")
     d.add_argument("--table", required=True)
     d.add_argument("--k", type=int, default=8)
@@ -864,6 +903,12 @@ def main(argv=None):
         with open(a.out, "w") as f:
             json.dump(r, f, indent=1)
         print(json.dumps({k: {"config": v["config"], "tflops": v["tflops"]} for k, v in r.items()}, indent=1))
+        return
+    if a.cmd == "retree":
+        r = retree(a.deploy, a.table)
+        with open(a.out, "w") as f:
+            json.dump(r, f, indent=1)
+        print(json.dumps(r["meta"]["scores"], indent=1))
         return
     if a.cmd == "forest":
         r = forest_deploy(a.deploy, a.table, a.trees)

@@ -25,7 +25,7 @@ def test_mlp_beats_tree_on_held_out_shapes(lib):
     assert ids == dep["config_ids"], "training table belongs to another deployment"
     tr, te = wl.train_test_split(len(shapes), 4)
     T, M = tune.mlp_targets(perf)
-    params, hist = tune.mlp_train_params(tune.mlp_features([shapes[i] for i in tr]), T[tr], M[tr], steps=3000)
+    params, hist = tune.mlp_train_params(tune.mlp_features([shapes[i] for i in tr]), T[tr], M[tr], steps=10000)
     assert hist[-1] < 0.05 * hist[0]
     test_shapes = [shapes[i] for i in te]
     col = {c: j for j, c in enumerate(ids)}

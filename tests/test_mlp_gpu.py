@@ -130,3 +130,19 @@ def test_features_kernel(lib, torch):
     lib.mlp_features(dev(torch, shapes, np.int64), X)
     ref = om.features(*[shapes[:, i] for i in range(7)])
     assert np.max(np.abs(X.cpu().numpy() - ref)) <= 1e-6
+
+
+def test_targets_kernel(lib, torch):
+    """log(perf / row max) and the measured mask, against the FP64 oracle: rows
+    with unmeasured (0) kernels, a row with none measured, and a throughput
+    range of nine decades."""
+    rng = np.random.default_rng(11)
+    perf = np.exp(rng.uniform(-3, 18, (513, 8))).astype(np.float32)
+    perf[rng.random((513, 8)) < 0.2] = 0.0
+    perf[7] = 0.0
+    T = torch.empty((513, 8), device="cuda")
+    mask = torch.empty((513, 8), device="cuda")
+    lib.mlp_targets(dev(torch, perf), T, mask)
+    rT, rmask = om.targets(perf.astype(np.float64))
+    assert np.array_equal(mask.cpu().numpy(), rmask)
+    assert np.max(np.abs(T.cpu().numpy() - rT)) <= 1e-5

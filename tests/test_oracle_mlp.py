@@ -79,3 +79,16 @@ def test_bf16_split_error():
     r = x.astype(np.float64) - hi.astype(np.float64) - lo.astype(np.float64)
     assert np.all(np.abs(r) <= 2.0 ** -16 * np.abs(x.astype(np.float64)))
     assert np.array_equal(ob.round_bf16(hi), hi) and np.array_equal(ob.round_bf16(lo), lo)
+
+
+def test_targets_by_hand_and_scale_invariance():
+    """log(perf / row max) on measured entries: the fastest kernel gets 0, one at
+    half its speed log(1/2); unmeasured entries are masked; a size that ran twice
+    as fast everywhere has the same targets (only relative speed is learned)."""
+    perf = np.array([[2.0, 4.0, 0.0, 1.0], [0.0, 0.0, 0.0, 0.0], [3.0, 3.0, 3.0, 3.0]])
+    T, mask = om.targets(perf)
+    assert np.allclose(T[0], [np.log(0.5), 0.0, 0.0, np.log(0.25)], rtol=0, atol=1e-15)
+    assert mask[0].tolist() == [1, 1, 0, 1] and mask[1].tolist() == [0, 0, 0, 0] and T[1].tolist() == [0, 0, 0, 0]
+    assert T[2].tolist() == [0, 0, 0, 0]
+    T2, mask2 = om.targets(perf * 2.0)
+    assert np.allclose(T2, T, rtol=0, atol=1e-15) and np.array_equal(mask2, mask)
