@@ -88,7 +88,7 @@ gemm_status_t kselect_debug_shrink_extents(int64_t a_bytes, int64_t b_bytes, int
  * {64,128,256} and a shared-memory ring of {2,3,4} stages: 9 configs per family
  * (the odd indexes are reserved and name no kernel: GEMM_ERR_NO_KERNEL).
  * gemm_config_id(family, i) = 1000 + 100*(family-1) + 2*i.  Operands are read in place by
- * TMA when K-contiguous (BF16 also when MN-contiguous), 16-byte aligned and
+ * TMA when K- or MN-contiguous (TF32 and BF16), 16-byte aligned and
  * batch-packed; others, and every F32X3 operand (split once into BF16 hi and
  * lo parts), are first rewritten by a pre-pass kernel.
  *
@@ -270,10 +270,10 @@ gemm_status_t gemm_with_config(int32_t config_id, char transA, char transB, int6
  * the global tile index with a fixed stride, mapping it to (problem, tile) by
  * binary search over the problems' first-tile offsets.  Per-problem TMA descriptors live in device
  * memory.  Problems use the row-major conventions above; K >= 1.  Operands
- * the kernel cannot read in place (TF32 ones that are not K-contiguous, i.e.
- * transA 'T' or transB 'N'; any not 16-byte aligned; every F32X3 operand) are
- * first rewritten by one grouped pre-pass launch into plan-owned scratch; BF16
- * operands are read in place in either storage order.
+ * the kernel cannot read in place (any whose rows are not 16-byte aligned, and
+ * every F32X3 operand) are first rewritten by one grouped pre-pass launch into
+ * plan-owned scratch; TF32 and BF16 operands are read in place in either
+ * storage order.
  *
  * A plan validates the problems, encodes their descriptors, uploads them and
  * allocates its scratch once (gemm_grouped_plan_create synchronises

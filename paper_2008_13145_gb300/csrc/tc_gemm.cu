@@ -1,10 +1,11 @@
 // Tensor-core GEMM families on sm_103a: TF32, BF16 and split-BF16 x3, for a
 // single batched GEMM and for an uneven group of GEMMs in one launch.
 //
-// The kernel (tc_kernel.cuh) consumes two K-contiguous operands.  op(A) = A
-// with A stored M x K is used in place, op(B) = B^T with B stored N x K too;
-// other layouts, and operands whose rows are not 16-byte aligned, are first
-// rewritten K-contiguous by a tiled transpose pre-pass into scratch.  The x3
+// The kernel (tc_kernel.cuh) reads each operand in place when its rows are
+// 16-byte aligned and batch-packed: K-contiguous (A stored M x K, B stored
+// N x K) as K-major tiles, MN-contiguous (A stored K x M, B stored K x N) as
+// MN-major tiles.  Other operands, and every x3 operand, are first rewritten
+// K-contiguous by a tiled transpose pre-pass into scratch.  The x3
 // family splits each FP32 value x into hi = bf16(x) and lo = bf16(x - hi) in
 // the same pre-pass and stores [hi | lo] per row; the kernel's K' = 3 K loop
 // reads the segment pairs (hi, hi), (hi, lo), (lo, hi), so one BF16 GEMM
@@ -96,9 +97,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 3-D map over a (batch, rows, inner) operand whose `inner` dimension is
 // contiguous; box = (128-byte inner slice) x box_rows.  K-major operands pass
-// (inner, rows) = (K, R); MN-major ones (R, K).
+// (inner, rows) = (K, R); MN-major ones (R, K), and an MN-major FP32 operand
+// (read as TF32) is swizzled in 32-byte pieces (atom32), the layout the MMA
+// reads 32-bit MN-major operands in.
 bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t K, int64_t rows, int64_t ld, int64_t batch,
-              int box_rows) {
+              int box_rows, bool atom32 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int64_t elem = bf16 ? 2 : 4;
@@ -108,7 +111,8 @@ bool make_map(CUtensorMap* m, const void* base, bool bf16, int64_t K, int64_t ro
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  atom32 ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -379,10 +383,10 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   // tensor map's third dimension steps R x ld); otherwise the pre-pass packs it.
   o.direct = !x3 && kcontig && ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0) &&
              (batch == 1 || stride == (int64_t)R * ld);
-  // A BF16 operand stored K x R (R contiguous) is read in place as MN-major
-  // tiles of whole 64-wide boxes when it is 16-byte aligned and batch-packed
-  // (K x ld per entry).
-  o.mn = !o.direct && c.family == GEMM_PREC_BF16 && !kcontig && mn_ext % tc::kMnBox == 0 &&
+  // A BF16 or TF32 operand stored K x R (R contiguous) is read in place as
+  // MN-major tiles of whole 128-byte boxes (64 BF16 or 32 FP32 elements) when
+  // it is 16-byte aligned and batch-packed (K x ld per entry).
+  o.mn = !o.direct && !x3 && !kcontig && mn_ext % (128 / op_elem) == 0 &&
          ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0) && (batch == 1 || stride == (int64_t)K * ld);
   if (o.mn) o.direct = true;
   const int nseg = x3 ? split_plan(K).nseg : 1;
@@ -456,9 +460,9 @@ gemm_status_t tc_launch(int id, const GemmArgs& g, cudaStream_t s) {
   CUtensorMap ma, mb;
   const int bk = op_bf16 ? 64 : 32;
   const bool map_ok = st == GEMM_OK &&
-                      (pa.mn ? make_map(&ma, Aop, op_bf16, g.M, Kmap, pa.ld, g.batch, bk)
+                      (pa.mn ? make_map(&ma, Aop, op_bf16, g.M, Kmap, pa.ld, g.batch, bk, !op_bf16)
                              : make_map(&ma, Aop, op_bf16, Kmap, g.M, pa.ld, g.batch, tc::kBM)) &&
-                      (pb.mn ? make_map(&mb, Bop, op_bf16, g.N, Kmap, pb.ld, g.batch, bk)
+                      (pb.mn ? make_map(&mb, Bop, op_bf16, g.N, Kmap, pb.ld, g.batch, bk, !op_bf16)
                              : make_map(&mb, Bop, op_bf16, Kmap, g.N, pb.ld, g.batch, b_ext));
   if (st == GEMM_OK && !map_ok) st = GEMM_ERR_MISALIGNED;
   if (st == GEMM_OK) {
@@ -607,9 +611,9 @@ gemm_status_t group_encode(const GroupBuild& b, const gemm_problem_t* probs, cha
     tc::GroupDesc& d = (*descs)[r];
     std::memset(&d, 0, sizeof(d));
     const int64_t Mr = q.M > 0 ? q.M : 1, Nr = q.N > 0 ? q.N : 1;
-    const bool ok_a = pa.mn ? make_map(&d.tmA, Aop, op_bf16, Mr, Kmap, pa.ld, 1, bk)
+    const bool ok_a = pa.mn ? make_map(&d.tmA, Aop, op_bf16, Mr, Kmap, pa.ld, 1, bk, !op_bf16)
                             : make_map(&d.tmA, Aop, op_bf16, Kmap, Mr, pa.ld, 1, tc::kBM);
-    const bool ok_b = pb.mn ? make_map(&d.tmB, Bop, op_bf16, Nr, Kmap, pb.ld, 1, bk)
+    const bool ok_b = pb.mn ? make_map(&d.tmB, Bop, op_bf16, Nr, Kmap, pb.ld, 1, bk, !op_bf16)
                             : make_map(&d.tmB, Bop, op_bf16, Kmap, Nr, pb.ld, 1, c.bn);
     if (!ok_a || !ok_b) return GEMM_ERR_MISALIGNED;
     d.C = q.C;

@@ -1,9 +1,9 @@
 // Persistent warp-specialised tcgen05 GEMM for sm_103a.
 //
 // C[b] = alpha * A[b] * B[b]^T + beta * C[b] with A (M x K) and B (N x K)
-// K-contiguous in global memory (BF16, or FP32 read as TF32); a BF16 operand
-// may instead be MN-contiguous (A stored K x M, B stored K x N), in which case
-// it is staged as MN-major tiles and the MMA reads it transposed.  Tiles of
+// K-contiguous in global memory (BF16, or FP32 read as TF32); an operand may
+// instead be MN-contiguous (A stored K x M, B stored K x N), in which case it
+// is staged as MN-major tiles and the MMA reads it transposed.  Tiles of
 // 128 x BN outputs are distributed over persistent CTAs; each CTA runs
 //   warp 4      : TMA producer (one elected lane) filling a STAGES-deep ring
 //                 of 128-byte-swizzled A/B slices, 128 bytes of K per slice;
@@ -33,7 +33,7 @@ struct TcArgs {
   float* C;
   int64_t ldc, strideC;
   int vecC;
-  int a_mn, b_mn;  // operand staged MN-major (BF16 only)
+  int a_mn, b_mn;  // operand staged MN-major
   // Split-BF16 products: each operand holds nseg segments of seg_blocks
   // K-slices (its BF16 split parts, largest first) and segment g of the K'
   // loop multiplies A's part seg_map bits [2g, 2g + 2) by B's part seg_map bits
@@ -62,7 +62,6 @@ struct GroupArgs {
 
 constexpr int kThreads = 192;
 constexpr int kBM = 128;
-constexpr int kMnBox = 64;  // MN elements of one MN-major TMA box (a 128-byte BF16 row)
 
 template <int BN, int STAGES, bool TF32>
 struct TcCfg {
@@ -76,13 +75,16 @@ struct TcCfg {
   // Epilogue staging: 32 rows x 16 FP32 columns per epilogue warp.
   static constexpr int EPI_BYTES = 4 * 32 * 16 * 4;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
-  // MN-major staging: one TMA box is 64 MN elements (a 128-byte row) by BK K
-  // rows; the boxes of a slice lie MN-block after MN-block.  The 128-byte
-  // swizzle atom is 8 K rows of one box, so the MMA descriptor steps 8 K rows
-  // by 1 KB (SBO) and one MN block by MN_BOX_BYTES (LBO), and each MMA's K
-  // range starts KMMA rows (KMMA x 128 bytes) further on.
-  static constexpr int MN_BOX = kMnBox;
+  // MN-major staging: one TMA box is MN_BOX MN elements (a 128-byte row) by
+  // BK K rows; the boxes of a slice lie MN-block after MN-block.  The swizzle
+  // atom is 8 K rows of one box for BF16 (128-byte swizzle, SBO 1 KB) and 4 K
+  // rows for TF32 (128-byte swizzle of 32-byte pieces, SBO 512 bytes); the
+  // descriptor steps one MN block by MN_BOX_BYTES (LBO), and each MMA's K range
+  // starts KMMA rows (KMMA x 128 bytes) further on.
+  static constexpr int MN_BOX = 128 / ELEM;
   static constexpr int MN_BOX_BYTES = BK * 128;
+  static constexpr uint32_t MN_SBO = TF32 ? 512 : 1024;
+  static constexpr uint32_t MN_MODE = TF32 ? kSw128Atom32 : kSw128;
 };
 
 __device__ __forceinline__ void tile_coords(const TcArgs& p, int tile, int& b, int& tm, int& tn) {
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             xb = (((L.seg_map >> (16 + 2 * g)) & 3) * L.seg_blocks + kk) * Cfg::BK;
           }
           mbar_arrive_expect_tx(&full_bar[stage], Cfg::STAGE_BYTES);
-          if (!TF32 && L.a_mn) {
+          if (L.a_mn) {
 #pragma unroll
             for (int j = 0; j < kBM / Cfg::MN_BOX; ++j)
               tma_load_3d(sa + j * Cfg::MN_BOX_BYTES, L.ma, &full_bar[stage], L.tm * kBM + j * Cfg::MN_BOX, xa,
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else {
             tma_load_3d(sa, L.ma, &full_bar[stage], xa, L.tm * kBM, L.b);
           }
-          if (!TF32 && L.b_mn) {
+          if (L.b_mn) {
 #pragma unroll
             for (int j = 0; j < BN / Cfg::MN_BOX; ++j)
               tma_load_3d(sa + Cfg::A_BYTES + j * Cfg::MN_BOX_BYTES, L.mb, &full_bar[stage],
@@ -303,7 +305,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           a_mn = L.a_mn;
           b_mn = L.b_mn;
         }
-        if constexpr (TF32) a_mn = b_mn = 0;
         const uint32_t idesc = instr_desc<TF32>(kBM, BN, a_mn != 0, b_mn != 0);
         // K-major: the next MMA's K range starts KMMA elements along the swizzled
         // 128-byte row; MN-major: KMMA K rows further on, MN blocks MN_BOX_BYTES apart.
@@ -321,8 +322,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t b_addr = a_addr + Cfg::A_BYTES;
 #pragma unroll
           for (int k = 0; k < Cfg::BK / Cfg::KMMA; ++k) {
-            const uint64_t ad = smem_desc_sw128(a_addr + (uint32_t)k * a_step, a_lbo, 1024);
-            const uint64_t bd = smem_desc_sw128(b_addr + (uint32_t)k * b_step, b_lbo, 1024);
+            const uint64_t ad = a_mn ? smem_desc_sw128(a_addr + (uint32_t)k * a_step, a_lbo, Cfg::MN_SBO, Cfg::MN_MODE)
+                                     : smem_desc_sw128(a_addr + (uint32_t)k * a_step, a_lbo, 1024);
+            const uint64_t bd = b_mn ? smem_desc_sw128(b_addr + (uint32_t)k * b_step, b_lbo, Cfg::MN_SBO, Cfg::MN_MODE)
+                                     : smem_desc_sw128(b_addr + (uint32_t)k * b_step, b_lbo, 1024);
             mma<TF32>(d_tmem, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
           }
           mma_commit(&empty_bar[stage]);  // frees the slot once these MMAs have read it

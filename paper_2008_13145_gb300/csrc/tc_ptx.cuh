@@ -159,18 +159,27 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits
 // [0,14), leading byte offset >> 4 in [16,30), stride byte offset >> 4 in
 // [32,46), descriptor version 1 in [46,48), base offset 0, swizzle mode in
-// [61,64) (2 = 128-byte swizzle).  Tiles start on 1024-byte boundaries.
+// [61,64): kSw128 = 128-byte swizzle of 16-byte pieces (the TMA's
+// CU_TENSOR_MAP_SWIZZLE_128B), kSw128Atom32 = 128-byte swizzle of 32-byte
+// pieces (CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B).  Tiles start on 1024-byte
+// boundaries.
 //   K-major, 128B swizzle: rows of 128 bytes along K, 8-row groups 1024 bytes
 //     apart (SBO); LBO unused.
-//   MN-major, 128B swizzle: rows of 128 bytes along M/N, one row per k; LBO =
-//     bytes between 128-byte-wide M/N chunks, SBO = bytes between 8-row k groups.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+//   MN-major, 16-bit elements, 128B swizzle: rows of 128 bytes along M/N, one
+//     row per k; LBO = bytes between 128-byte-wide M/N chunks, SBO = bytes
+//     between 8-row k groups (1024).
+//   MN-major, 32-bit elements (TF32), 128B swizzle of 32-byte pieces: the same
+//     rows, but the swizzle pattern repeats every 4 rows, so k groups are 4
+//     rows (SBO = 512).
+constexpr uint32_t kSw128 = 2, kSw128Atom32 = 1;
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes,
+                                                    uint32_t mode = kSw128) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
   d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFF) << 16;
   d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(mode & 7) << 61;
   return d;
 }
 

@@ -79,33 +79,35 @@ def test_every_config_ragged(lib, torch, fam):
     assert ks.device_status() == 0
 
 
+@pytest.mark.parametrize("fam", ["tf32", "bf16"])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("T", "T")])
-def test_bf16_mn_major_every_config(lib, torch, ta, tb):
-    """BF16 operands stored MN-contiguous (A as K x M, B as K x N) with 16-byte
-    aligned rows are read in place as MN-major tiles: all 9 configs, two tiles
-    plus a ragged tail in M and N, K not a multiple of the slice, two batch
-    entries, alpha and beta."""
+def test_mn_major_every_config(lib, torch, fam, ta, tb):
+    """TF32 and BF16 operands stored MN-contiguous (A as K x M, B as K x N)
+    with 16-byte aligned rows are read in place as MN-major tiles (TF32: boxes
+    of 32 elements, 128-byte swizzle of 32-byte pieces): all 9 configs, two
+    tiles plus a ragged tail in M and N, K not a multiple of the slice, two
+    batch entries, alpha and beta."""
     ks = lib
     bad = []
-    for cid in tc_ids(ks, "bf16"):
-        C, ref, den = run(ks, torch, cid, "bf16", wl.Shape(300, 333, 136, 2, ta, tb), -0.5, 0.25, seed=12)
+    for cid in tc_ids(ks, fam):
+        C, ref, den = run(ks, torch, cid, fam, wl.Shape(300, 333, 136, 2, ta, tb), -0.5, 0.25, seed=12)
         err = og.error_ratio(C, ref, den)
-        if not err <= FAMILIES["bf16"][1]:
+        if not err <= FAMILIES[fam][1]:
             bad.append((cid, ks.config_params(cid), err))
     assert not bad, bad
     assert ks.device_status() == 0
 
 
+@pytest.mark.parametrize("fam,bound", [("tf32", 64), ("bf16", 16)])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("T", "T")])
-def test_bf16_mn_major_integer_exact(lib, torch, ta, tb):
-    """Small integers are exact in BF16 and their sums in FP32, so reading an
-    MN-major operand transposed must give the FP64 product bit for bit, in a
-    BN 64 and a BN 256 config."""
+def test_mn_major_integer_exact(lib, torch, fam, bound, ta, tb):
+    """Small integers are exact in the operand format and their sums in FP32,
+    so reading an MN-major operand transposed must give the FP64 product bit
+    for bit, in every config."""
     ks = lib
-    ids = tc_ids(ks, "bf16")
-    for cid in (ids[2], ids[8]):
-        C, ref, _ = run(ks, torch, cid, "bf16", wl.Shape(200, 260, 320, 2, ta, tb), 1.0, 1.0, seed=13,
-                        kind="integer", bound=16)
+    for cid in tc_ids(ks, fam):
+        C, ref, _ = run(ks, torch, cid, fam, wl.Shape(200, 260, 320, 2, ta, tb), 1.0, 1.0, seed=13,
+                        kind="integer", bound=bound)
         assert np.array_equal(C.astype(np.float64), ref), cid
 
 
