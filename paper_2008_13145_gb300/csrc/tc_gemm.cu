@@ -152,6 +152,7 @@ struct PrepJob {
   int R, K, Kp, nseg;
   int tiles_k, tiles_r, block_start;  // 64 x 64 tiles; first block of this job (grouped form)
   int vec2;  // element pairs along the source's contiguous dimension may be read as one access
+  int vec4;  // FP32 source, K contiguous, every 4-element group 16-byte aligned (direct split path)
 };
 
 template <typename T>
@@ -166,11 +167,56 @@ __device__ __forceinline__ float to_f32(T v) {
 // consecutive K positions of one output row (two per lane).
 constexpr int kPrepWarps = 8;  // warps per pre-pass block; each takes 64 / kPrepWarps tile rows
 
+// Split of one 64 x 64 tile whose source is FP32 with K contiguous and 16-byte
+// aligned: it needs no transpose, so each thread reads 4 consecutive k of one
+// row as one 16-byte access and writes 4 BF16 of every part as one 8-byte
+// store, without staging through shared memory (a warp covers two rows).
+__device__ __forceinline__ void split_tile_direct(const PrepJob& j, int b, int tr, int tk) {
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const float* src = static_cast<const float*>(j.in) + (int64_t)b * j.in_stride;
+  __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(j.out) + (int64_t)b * j.R * j.ld_out;
+#pragma unroll
+  for (int q = 0; q < 64 * 16 / (32 * kPrepWarps); ++q) {
+    const int idx = q * 32 * kPrepWarps + tid;
+    const int r = tr * 64 + idx / 16, k = tk * 64 + (idx % 16) * 4;
+    if (r >= j.R || k >= j.Kp) continue;
+    const float* p = src + (int64_t)r * j.rs + k;
+    float v[4];
+    if (k + 3 < j.K) {
+      const float4 w = *reinterpret_cast<const float4*>(p);
+      v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (k + e < j.K) ? p[e] : 0.f;
+    }
+    __nv_bfloat16* o = dst + (int64_t)r * j.ld_out + k;  // Kp and ld_out are multiples of 64: 8-byte aligned
+    for (int sg = 0; sg < j.nseg; ++sg) {
+      __nv_bfloat16 part[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        part[e] = __float2bfloat16_rn(v[e]);
+        v[e] -= __bfloat162float(part[e]);
+      }
+      const __nv_bfloat162 p01 = __halves2bfloat162(part[0], part[1]), p23 = __halves2bfloat162(part[2], part[3]);
+      uint2 w;
+      std::memcpy(&w.x, &p01, 4);
+      std::memcpy(&w.y, &p23, 4);
+      *reinterpret_cast<uint2*>(o + (int64_t)sg * j.Kp) = w;
+    }
+  }
+}
+
 template <typename TIn, typename TOut, bool SPLIT>
 __device__ __forceinline__ void prep_tile(const PrepJob& j, int b, int tr, int tk) {
   __shared__ float tile[64][65];
   pdl_wait();
   pdl_launch_dependents();
+  if constexpr (SPLIT && sizeof(TIn) == 4) {
+    if (j.vec4) {  // the same for every thread of the block
+      split_tile_direct(j, b, tr, tk);
+      return;
+    }
+  }
   const int r0 = tr * 64, k0 = tk * 64, lane = threadIdx.x;
   const TIn* src = static_cast<const TIn*>(j.in) + (int64_t)b * j.in_stride;
   const bool k_fast = (j.ks == 1);
@@ -398,8 +444,9 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   // strides all even multiples of the element size.
   const int64_t pair_bytes = 2 * in_elem;
   const int vec2 = ((uintptr_t)ptr % pair_bytes == 0) && (ld % 2 == 0) && (stride % 2 == 0);
+  const int vec4 = x3 && kcontig && ((uintptr_t)ptr % 16 == 0) && (ld % 4 == 0) && (stride % 4 == 0);
   o.job = PrepJob{ptr, stride, kcontig ? ld : 1, kcontig ? 1 : ld, nullptr, o.ld, R, K, (int)Kp, nseg,
-                  (int)((Kp + 63) / 64), (R + 63) / 64, 0, vec2};
+                  (int)((Kp + 63) / 64), (R + 63) / 64, 0, vec2, vec4};
   return o;
 }
 
