@@ -140,7 +140,9 @@ int* status_word_if_ready() { return status_word_of(false); }
 // ---------------------------------------------------------------- K-contiguous pre-pass
 // One rewrite job: out[b][r][seg * Kp + k] for r < R, k < Kp (zero for k >= K)
 // from the logical R x K operand whose element (r, k) of batch entry b sits at
-// in[b * in_stride + r * rs + k * ks].  Copy (nseg 1, same type) or BF16
+// in[b * in_stride + r * rs + k * ks]; with mn_out (a split of an FP32 operand
+// stored MN-contiguous) the parts are written MN-major instead,
+// out[b][seg * Kp + k][r], without a transpose.  Copy (nseg 1, same type) or BF16
 // split (FP32 in, BF16 out, nseg 2 or 3): segment 0 holds p0 = bf16(x) and
 // segment s the rounded remainder p_s = bf16(x - p0 - ... - p_{s-1}); every
 // remainder is exact in FP32.
@@ -152,7 +154,8 @@ struct PrepJob {
   int R, K, Kp, nseg;
   int tiles_k, tiles_r, block_start;  // 64 x 64 tiles; first block of this job (grouped form)
   int vec2;  // element pairs along the source's contiguous dimension may be read as one access
-  int vec4;  // FP32 source, K contiguous, every 4-element group 16-byte aligned (direct split path)
+  int vec4;  // FP32 source, every 4-element group along its contiguous dimension 16-byte aligned (direct split)
+  int mn_out;  // write the parts MN-major (vec4 jobs of an MN-contiguous source only)
 };
 
 template <typename T>
@@ -167,29 +170,39 @@ __device__ __forceinline__ float to_f32(T v) {
 // consecutive K positions of one output row (two per lane).
 constexpr int kPrepWarps = 8;  // warps per pre-pass block; each takes 64 / kPrepWarps tile rows
 
-// Split of one 64 x 64 tile whose source is FP32 with K contiguous and 16-byte
-// aligned: it needs no transpose, so each thread reads 4 consecutive k of one
-// row as one 16-byte access and writes 4 BF16 of every part as one 8-byte
-// store, without staging through shared memory (a warp covers two rows).
+// Split of one 64 x 64 tile of an FP32 source whose contiguous dimension is
+// 16-byte aligned, in the source's own orientation: each thread reads 4
+// consecutive elements along the contiguous dimension as one 16-byte access
+// and writes 4 BF16 of every part as one 8-byte store, without staging through
+// shared memory (a warp covers two lines of the tile).  K-contiguous source:
+// out row r holds the parts side by side along K.  MN-contiguous source
+// (mn_out): out row (seg * Kp + k) holds part seg of column k, so the parts are
+// stacked along K and the GEMM reads them MN-major.
 __device__ __forceinline__ void split_tile_direct(const PrepJob& j, int b, int tr, int tk) {
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const float* src = static_cast<const float*>(j.in) + (int64_t)b * j.in_stride;
-  __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(j.out) + (int64_t)b * j.R * j.ld_out;
+  const int64_t out_stride = j.mn_out ? (int64_t)j.nseg * j.Kp * j.ld_out : (int64_t)j.R * j.ld_out;
+  __nv_bfloat16* dst = static_cast<__nv_bfloat16*>(j.out) + (int64_t)b * out_stride;
 #pragma unroll
   for (int q = 0; q < 64 * 16 / (32 * kPrepWarps); ++q) {
     const int idx = q * 32 * kPrepWarps + tid;
-    const int r = tr * 64 + idx / 16, k = tk * 64 + (idx % 16) * 4;
+    // (r, k) of the first of this thread's 4 elements; the 4 run along the contiguous dimension
+    const int r = j.mn_out ? tr * 64 + (idx % 16) * 4 : tr * 64 + idx / 16;
+    const int k = j.mn_out ? tk * 64 + idx / 16 : tk * 64 + (idx % 16) * 4;
     if (r >= j.R || k >= j.Kp) continue;
-    const float* p = src + (int64_t)r * j.rs + k;
+    const float* p = src + (int64_t)r * j.rs + (int64_t)k * j.ks;  // the step along the 4 is 1
+    const int lim = j.mn_out ? (k < j.K ? j.R - r : 0) : j.K - k;   // how many of the 4 exist in the source
     float v[4];
-    if (k + 3 < j.K) {
+    if (lim >= 4) {
       const float4 w = *reinterpret_cast<const float4*>(p);
       v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
     } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = (k + e < j.K) ? p[e] : 0.f;
+      for (int e = 0; e < 4; ++e) v[e] = (e < lim) ? p[e] : 0.f;
     }
-    __nv_bfloat16* o = dst + (int64_t)r * j.ld_out + k;  // Kp and ld_out are multiples of 64: 8-byte aligned
+    // ld_out is a multiple of 8 (MN-major) or of 64 (K-major), and Kp of 64: the stores are 8-byte aligned
+    __nv_bfloat16* o = j.mn_out ? dst + (int64_t)k * j.ld_out + r : dst + (int64_t)r * j.ld_out + k;
+    const int64_t seg_step = j.mn_out ? (int64_t)j.Kp * j.ld_out : (int64_t)j.Kp;
     for (int sg = 0; sg < j.nseg; ++sg) {
       __nv_bfloat16 part[4];
 #pragma unroll
@@ -201,7 +214,7 @@ __device__ __forceinline__ void split_tile_direct(const PrepJob& j, int b, int t
       uint2 w;
       std::memcpy(&w.x, &p01, 4);
       std::memcpy(&w.y, &p23, 4);
-      *reinterpret_cast<uint2*>(o + (int64_t)sg * j.Kp) = w;
+      *reinterpret_cast<uint2*>(o + (int64_t)sg * seg_step) = w;
     }
   }
 }
@@ -435,18 +448,24 @@ OperandPlan plan_operand(const TcConfig& c, const void* ptr, int64_t ld, int64_t
   o.mn = !o.direct && !x3 && !kcontig && mn_ext % (128 / op_elem) == 0 &&
          ((uintptr_t)ptr % 16 == 0) && ((ld * in_elem) % 16 == 0) && (batch == 1 || stride == (int64_t)K * ld);
   if (o.mn) o.direct = true;
+  // Every x3 operand is split by the pre-pass; an aligned one is split in its
+  // own orientation (vec4), and one stored K x R is then read MN-major.
+  const int vec4 = x3 && ((uintptr_t)ptr % 16 == 0) && (ld % 4 == 0) && (stride % 4 == 0);
+  const bool x3_mn = x3 && !kcontig && vec4 && mn_ext % (128 / op_elem) == 0;
+  if (x3_mn) o.mn = true;
   const int nseg = x3 ? split_plan(K).nseg : 1;
   const int64_t Kp = x3 ? round_up(K, kSplitSeg) : round_up(K, 16 / op_elem);
-  o.ld = o.direct ? ld : nseg * Kp;
-  o.bytes = o.direct ? 0 : (int64_t)batch * R * o.ld * op_elem;
+  // Scratch rows: K-major parts side by side (nseg * Kp per row), or MN-major
+  // rows of R elements padded to 16 bytes (nseg * Kp rows per batch entry).
+  o.ld = o.direct ? ld : x3_mn ? round_up(R, 8) : nseg * Kp;
+  o.bytes = o.direct ? 0 : x3_mn ? (int64_t)batch * nseg * Kp * o.ld * op_elem : (int64_t)batch * R * o.ld * op_elem;
   // Element pairs along the contiguous dimension are read as one access when
   // every pair starts on a multiple of two elements: base, row and batch
   // strides all even multiples of the element size.
   const int64_t pair_bytes = 2 * in_elem;
   const int vec2 = ((uintptr_t)ptr % pair_bytes == 0) && (ld % 2 == 0) && (stride % 2 == 0);
-  const int vec4 = x3 && kcontig && ((uintptr_t)ptr % 16 == 0) && (ld % 4 == 0) && (stride % 4 == 0);
   o.job = PrepJob{ptr, stride, kcontig ? ld : 1, kcontig ? 1 : ld, nullptr, o.ld, R, K, (int)Kp, nseg,
-                  (int)((Kp + 63) / 64), (R + 63) / 64, 0, vec2, vec4};
+                  (int)((Kp + 63) / 64), (R + 63) / 64, 0, vec2, vec4, x3_mn ? 1 : 0};
   return o;
 }
 

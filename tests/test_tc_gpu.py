@@ -98,12 +98,13 @@ def test_mn_major_every_config(lib, torch, fam, ta, tb):
     assert ks.device_status() == 0
 
 
-@pytest.mark.parametrize("fam,bound", [("tf32", 64), ("bf16", 16)])
+@pytest.mark.parametrize("fam,bound", [("tf32", 64), ("bf16", 16), ("f32x3", 128)])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("T", "T")])
 def test_mn_major_integer_exact(lib, torch, fam, bound, ta, tb):
     """Small integers are exact in the operand format and their sums in FP32,
     so reading an MN-major operand transposed must give the FP64 product bit
-    for bit, in every config."""
+    for bit, in every config (x3: its pre-pass splits an aligned MN-contiguous
+    operand without transposing it, and the kernel reads the parts MN-major)."""
     ks = lib
     for cid in tc_ids(ks, fam):
         C, ref, _ = run(ks, torch, cid, fam, wl.Shape(200, 260, 320, 2, ta, tb), 1.0, 1.0, seed=13,
