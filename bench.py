@@ -581,8 +581,41 @@ def grouped_launch(ks, tune):
         if r.get("selector_scores"):
             out[name]["selector_held_out_geomean"] = r["selector_scores"]["tree"]["geomean"]
         plan.close()
+        if r.get("selector"):
+            # The library call of the boundary, gemm_grouped(handle, problems,
+            # precision, stream): selection inside the call, descriptors written
+            # into the handle's workspace by the captured upload kernels on every
+            # replay; captured once after a call that sizes the workspace.
+            h = ks.Handle(r["selector"])
+            ms_h = time_handle_call_graph(ks, h, probs, fam)
+            out[name]["handle_call"] = {"value": flops / (ms_h * 1e9), "ms_per_launch": ms_h,
+                                        "config": ks.grouped_select(h, probs),
+                                        "note": "gemm_grouped(handle, ...) captured in a CUDA graph and replayed"}
         del keep
     return out
+
+
+def time_handle_call_graph(ks, h, probs, precision, reps: int = 20, warmup: int = 3) -> float:
+    """Mean ms of one replay of a CUDA graph holding one gemm_grouped(handle, ...) call."""
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ks.gemm_grouped(h, probs, precision, s)  # sizes the handle's workspace (outside the capture)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ks.gemm_grouped(h, probs, precision, s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(reps):
+            g.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def mlp_serving(ks, tune, dep, n: int = 4096, reps: int = 100):
