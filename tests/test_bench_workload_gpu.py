@@ -18,7 +18,8 @@ from paper_2008_13145_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 DEPLOY = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2008_13145_gb300", "deploy")
-CASES = [("f32.json", 1e-5, False), ("f32mix.json", 1e-5, False), ("tf32.json", 5e-3, False), ("bf16.json", 2e-2, True)]
+CASES = [("f32.json", 1e-5, False), ("f32mix.json", 1e-5, False), ("f32x3.json", 1e-5, False), ("tf32.json", 5e-3, False),
+         ("bf16.json", 2e-2, True)]
 # (deployment, tolerance of its precision class, BF16 inputs)
 
 

@@ -286,3 +286,52 @@ def test_bounded_wait_gives_up_and_context_survives(lib, torch):
     C, ref, den = run(ks, torch, tc_ids(ks, "bf16")[4], "bf16", wl.Shape(128, 128, 128, 1, "N", "T"), 1.0, 0.0, seed=1)
     assert og.error_ratio(C, ref, den) <= FAMILIES["bf16"][1]
     assert ks.device_status() == 0
+
+
+@pytest.mark.parametrize("cid", [7, 2533, 1000, 1116, 1216])
+def test_empty_sizes_and_k_zero_every_family(lib, torch, cid):
+    """The degenerate cases of C = alpha op(A) op(B) + beta C, in every family
+    (SIMT, split-K, TF32, BF16, x3): K = 0 leaves C = beta C (beta = 0 writes
+    exact zeros over a NaN-filled C); M, N or batch = 0 touches nothing.  Guard
+    bands around C and its ldc padding must survive."""
+    ks = lib
+    bf16 = ks.family_of(cid) == ks.PREC_BF16
+    dummy = torch.zeros(64, device="cuda", dtype=torch.bfloat16 if bf16 else torch.float32)
+    for beta in (0.5, 0.0):
+        C0 = wl.uniform_matrix(9, 10, 12, 2, 3, 3)
+        out = Out(torch, C0, beta, 10)
+        ks.gemm_with_config(cid, "N", "T", 9, 10, 0, 1.0, dummy, 1, dummy, 1, beta, out.ptr, 12, 2)
+        torch.cuda.synchronize()
+        want = np.float32(beta) * C0[:, :, :10] if beta != 0 else np.zeros((2, 9, 10), np.float32)
+        assert np.array_equal(out.result(10), want), (cid, beta)
+    for M, N, batch in ((0, 10, 2), (9, 0, 2), (9, 10, 0)):
+        C0 = wl.uniform_matrix(9, 10, 12, 2, 4, 3)
+        out = Out(torch, C0, 0.5, 10)
+        ks.gemm_with_config(cid, "N", "T", M, N, 16, 1.0, dummy, 16, dummy, 16, 0.5, out.ptr, 12, batch)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.result(10), C0[:, :, :10]), (cid, M, N, batch)
+    assert ks.device_status() == 0
+
+
+@pytest.mark.parametrize("cid", [7, 533, 2533, 1000, 1116, 1216])
+def test_maximum_batch_every_family(lib, torch, cid):
+    """batch = 65535, the largest the library accepts (the SIMT grid's z
+    dimension; the tensor-core kernels walk 65535 tiles persistently): 4 x 5 x 6
+    products against the oracle, and 65536 is refused before any launch."""
+    ks = lib
+    fam = ks.family_of(cid)
+    bf16 = fam == ks.PREC_BF16
+    shape = wl.Shape(4, 5, 6, 65535, "N", "T")
+    A, B, C0 = wl.gemm_inputs(shape, seed=77, ld_multiple=8, beta_nonzero=True)
+    tA, tB = to_dev(torch, A, bf16), to_dev(torch, B, bf16)
+    C = torch.from_numpy(C0).cuda()
+    ks.gemm_with_config(cid, "N", "T", 4, 5, 6, 1.0, tA, A.shape[2], tB, B.shape[2], -0.5, C, C0.shape[2], 65535)
+    torch.cuda.synchronize()
+    ref, den = og.gemm("N", "T", 4, 5, 6, 1.0, host_values(tA).reshape(A.shape), host_values(tB).reshape(B.shape),
+                       -0.5, C0)
+    tol = {ks.PREC_F32: 1e-5, ks.PREC_TF32: 5e-3, ks.PREC_BF16: 2e-2, ks.PREC_F32X3: 1e-5}[fam]
+    assert og.error_ratio(C.cpu().numpy()[:, :, :5], ref, den) <= tol
+    with pytest.raises(ks.KSelectError) as e:
+        ks.gemm_with_config(cid, "N", "T", 4, 5, 6, 1.0, tA, A.shape[2], tB, B.shape[2], 0.0, C, C0.shape[2], 65536)
+    assert e.value.status == -2
+    assert ks.device_status() == 0
