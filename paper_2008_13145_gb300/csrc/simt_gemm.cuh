@@ -46,7 +46,34 @@ struct SimtCfg {
   // contiguous for the vector reads.
   __device__ static constexpr int swz_a(int m, int k) { return (((m >> 2) ^ ((k >> 2) & (BM / 4 - 1))) << 2) | (m & 3); }
   __device__ static constexpr int swz_b(int n, int k) { return (((n >> 2) ^ ((k >> 2) & (BN / 4 - 1))) << 2) | (n & 3); }
+  // Lane that holds thread column tx ^ 1 of the same thread row (see thread_coords).
+  static constexpr int TX_LANE_STRIDE = STAGED ? 2 : 1;
 };
+
+// Thread (tx, ty) of the WX x WY block that thread `tid` plays.  Unstaged configs
+// read global memory directly and keep tx = tid % WX, so consecutive lanes read
+// consecutive columns.  Staged configs read their fragments from shared memory,
+// where the cost of a warp's load depends on which lanes share an address: a
+// 16-byte load takes two wavefronts (one per half-warp) only when, in each half,
+// its two quarter-warps touch disjoint banks or lanes sharing a chunk are
+// neighbours (l, l ^ 1); otherwise four.  Each warp therefore covers 4 thread rows
+// x 8 thread columns with the row in lane bit 0 (and bit 4) and the column in lane
+// bits 1-3: the A fragment (per row) and the B fragment (per column) loads both
+// meet the two-wavefront case (measured on GB300 with a per-pattern probe), where
+// tx = tid % WX made every 16-byte B load take four.  Which thread owns which
+// part of C is unchanged, so results are bit-identical.
+template <class Cfg>
+__device__ __forceinline__ void thread_coords(int tid, int& tx, int& ty) {
+  if constexpr (Cfg::STAGED) {
+    static_assert(Cfg::WX % 8 == 0 && Cfg::WY % 4 == 0, "lane map needs 8-column, 4-row warp blocks");
+    const int w = tid >> 5, l = tid & 31;
+    tx = (w % (Cfg::WX / 8)) * 8 + ((l >> 1) & 7);
+    ty = (w / (Cfg::WX / 8)) * 4 + (((l >> 3) & 2) | (l & 1));
+  } else {
+    tx = tid % Cfg::WX;
+    ty = tid / Cfg::WX;
+  }
+}
 
 template <int W>
 struct VecT;
@@ -170,8 +197,7 @@ __device__ __forceinline__ void store_out4(const GemmArgs& p, float* Cb, int gm,
 template <class Cfg>
 __device__ __forceinline__ void epilogue(const GemmArgs& p, float* Cb, int m0, int n0, int tx, int ty,
                                          const float (&acc)[Cfg::TM][Cfg::TN]) {
-  constexpr int TM = Cfg::TM, TN = Cfg::TN, CN = Cfg::CN;
-  const int lane = threadIdx.x & 31;
+  constexpr int TM = Cfg::TM, TN = Cfg::TN, CN = Cfg::CN, XS = Cfg::TX_LANE_STRIDE;
   if constexpr (CN == 4) {
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -181,15 +207,16 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, float* Cb, int m0, i
         store_out4<Cfg>(p, Cb, m0 + Cfg::row(i, ty), n0 + Cfg::col(jc * 4, tx), v);
       }
   } else if constexpr (CN == 2 && TM >= 2) {
-    // Lane pairs (tx even/odd) hold columns 4g..4g+1 / 4g+2..4g+3 of the same
-    // rows; swap half of each 2x4 block so each lane owns one full row.
-    const int q = lane & 1;
+    // Thread pairs (tx even/odd, XS lanes apart) hold columns 4g..4g+1 /
+    // 4g+2..4g+3 of the same rows; swap half of each 2x4 block so each thread
+    // owns one full row.
+    const int q = tx & 1;
 #pragma unroll
     for (int i0 = 0; i0 < TM; i0 += 2) {
       float s0 = q ? acc[i0][0] : acc[i0 + 1][0];
       float s1 = q ? acc[i0][1] : acc[i0 + 1][1];
-      float r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
-      float r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+      float r0 = __shfl_xor_sync(0xffffffffu, s0, XS);
+      float r1 = __shfl_xor_sync(0xffffffffu, s1, XS);
       float v[4];
       if (q == 0) {
         v[0] = acc[i0][0]; v[1] = acc[i0][1]; v[2] = r0; v[3] = r1;
@@ -199,17 +226,18 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, float* Cb, int m0, i
       store_out4<Cfg>(p, Cb, m0 + Cfg::row(i0 + q, ty), n0 + (tx & ~1) * 2, v);
     }
   } else if constexpr (CN == 1 && TM >= 4) {
-    // Lane quads hold one column each of the same 4 rows: 4x4 transpose by
-    // butterfly shuffles so each lane owns one row of 4 columns.
-    const int q = lane & 3;
+    // Thread quads (tx & 3, lanes XS apart) hold one column each of the same 4
+    // rows: 4x4 transpose by butterfly shuffles so each thread owns one row of 4
+    // columns.
+    const int q = tx & 3;
 #pragma unroll
     for (int i0 = 0; i0 < TM; i0 += 4) {
       float v[4] = {acc[i0][0], acc[i0 + 1][0], acc[i0 + 2][0], acc[i0 + 3][0]};
-      // w[c] = element (row q, column c) of the 4x4 block; lane c holds column c.
+      // w[c] = element (row q, column c) of the 4x4 block; thread c of the quad holds column c.
       float w[4] = {q == 0 ? v[0] : 0.f, q == 1 ? v[1] : 0.f, q == 2 ? v[2] : 0.f, q == 3 ? v[3] : 0.f};
 #pragma unroll
       for (int s = 1; s < 4; ++s) {
-        float r = __shfl_xor_sync(0xffffffffu, sel4(v, q ^ s), s);
+        float r = __shfl_xor_sync(0xffffffffu, sel4(v, q ^ s), s * XS);
         const int dst = q ^ s;
         w[0] = (dst == 0) ? r : w[0];
         w[1] = (dst == 1) ? r : w[1];
@@ -227,8 +255,15 @@ __device__ __forceinline__ void epilogue(const GemmArgs& p, float* Cb, int m0, i
 }
 
 // ---------------------------------------------------------------- staged slice copy
-// FAST: the whole slice is inside op(A) and 16-byte loads are legal (interior tile).
-template <class Cfg, bool FAST>
+// How a slice is read from global memory:
+//   kLoadFast  : the whole slice lies inside op(A) / op(B) and 16-byte loads are
+//                legal (interior tile, full K slice);
+//   kLoadKTail : interior tile (rows and columns in range, 16-byte loads legal),
+//                but the slice may run past K: only k is checked;
+//   kLoadGeneral: every bound is checked (edge tiles, unaligned operands).
+constexpr int kLoadGeneral = 0, kLoadKTail = 1, kLoadFast = 2;
+
+template <class Cfg, int MODE>
 __device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArgs& p, const float* Ab,
                                              int m0, int k0, int K, int tid) {
   constexpr int BK = Cfg::BK, BM = Cfg::BM;
@@ -240,21 +275,25 @@ __device__ __forceinline__ void load_slice_a(float4 (&r)[Cfg::RA], const GemmArg
       if (!p.transA) {  // stored M x K: chunk of 4 along k
         const int m = c / (BK / 4), kq = (c % (BK / 4)) * 4;
         const int gm = m0 + m, gk = k0 + kq;
-        if (FAST) {
-          r[u] = ks_in_bounds(p, 0, Ab + (int64_t)gm * p.lda + gk, 16)
-                     ? __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gm * p.lda + gk)) : float4{};
+        const float* src = Ab + (int64_t)gm * p.lda + gk;
+        if (MODE == kLoadFast) {
+          r[u] = ks_in_bounds(p, 0, src, 16) ? __ldg(reinterpret_cast<const float4*>(src)) : float4{};
           continue;
         }
-        if (gm < p.M) load_vec_global<4>(v, Ab + (int64_t)gm * p.lda + gk, K - gk, p.vecA, p, 0);
+        if (MODE == kLoadKTail || gm < p.M) load_vec_global<4>(v, src, K - gk, MODE == kLoadKTail || p.vecA, p, 0);
       } else {  // stored K x M: chunk of 4 along m
         const int k = c / (BM / 4), mq = (c % (BM / 4)) * 4;
         const int gk = k0 + k, gm = m0 + mq;
-        if (FAST) {
-          r[u] = ks_in_bounds(p, 0, Ab + (int64_t)gk * p.lda + gm, 16)
-                     ? __ldg(reinterpret_cast<const float4*>(Ab + (int64_t)gk * p.lda + gm)) : float4{};
+        const float* src = Ab + (int64_t)gk * p.lda + gm;
+        if (MODE == kLoadFast) {
+          r[u] = ks_in_bounds(p, 0, src, 16) ? __ldg(reinterpret_cast<const float4*>(src)) : float4{};
           continue;
         }
-        if (gk < K) load_vec_global<4>(v, Ab + (int64_t)gk * p.lda + gm, p.M - gm, p.vecA, p, 0);
+        if (MODE == kLoadKTail) {
+          r[u] = (gk < K && ks_in_bounds(p, 0, src, 16)) ? __ldg(reinterpret_cast<const float4*>(src)) : float4{};
+          continue;
+        }
+        if (gk < K) load_vec_global<4>(v, src, p.M - gm, p.vecA, p, 0);
       }
     }
     r[u] = make_float4(v[0], v[1], v[2], v[3]);
@@ -283,7 +322,7 @@ __device__ __forceinline__ void store_slice_a(const float4 (&r)[Cfg::RA], const 
   }
 }
 
-template <class Cfg, bool FAST>
+template <class Cfg, int MODE>
 __device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArgs& p, const float* Bb,
                                              int n0, int k0, int K, int tid) {
   constexpr int BK = Cfg::BK, BN = Cfg::BN;
@@ -295,21 +334,25 @@ __device__ __forceinline__ void load_slice_b(float4 (&r)[Cfg::RB], const GemmArg
       if (!p.transB) {  // stored K x N: chunk along n
         const int k = c / (BN / 4), nq = (c % (BN / 4)) * 4;
         const int gk = k0 + k, gn = n0 + nq;
-        if (FAST) {
-          r[u] = ks_in_bounds(p, 1, Bb + (int64_t)gk * p.ldb + gn, 16)
-                     ? __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gk * p.ldb + gn)) : float4{};
+        const float* src = Bb + (int64_t)gk * p.ldb + gn;
+        if (MODE == kLoadFast) {
+          r[u] = ks_in_bounds(p, 1, src, 16) ? __ldg(reinterpret_cast<const float4*>(src)) : float4{};
           continue;
         }
-        if (gk < K) load_vec_global<4>(v, Bb + (int64_t)gk * p.ldb + gn, p.N - gn, p.vecB, p, 1);
+        if (MODE == kLoadKTail) {
+          r[u] = (gk < K && ks_in_bounds(p, 1, src, 16)) ? __ldg(reinterpret_cast<const float4*>(src)) : float4{};
+          continue;
+        }
+        if (gk < K) load_vec_global<4>(v, src, p.N - gn, p.vecB, p, 1);
       } else {  // stored N x K: chunk along k
         const int n = c / (BK / 4), kq = (c % (BK / 4)) * 4;
         const int gn = n0 + n, gk = k0 + kq;
-        if (FAST) {
-          r[u] = ks_in_bounds(p, 1, Bb + (int64_t)gn * p.ldb + gk, 16)
-                     ? __ldg(reinterpret_cast<const float4*>(Bb + (int64_t)gn * p.ldb + gk)) : float4{};
+        const float* src = Bb + (int64_t)gn * p.ldb + gk;
+        if (MODE == kLoadFast) {
+          r[u] = ks_in_bounds(p, 1, src, 16) ? __ldg(reinterpret_cast<const float4*>(src)) : float4{};
           continue;
         }
-        if (gn < p.N) load_vec_global<4>(v, Bb + (int64_t)gn * p.ldb + gk, K - gk, p.vecB, p, 1);
+        if (MODE == kLoadKTail || gn < p.N) load_vec_global<4>(v, src, K - gk, MODE == kLoadKTail || p.vecB, p, 1);
       }
     }
     r[u] = make_float4(v[0], v[1], v[2], v[3]);
@@ -338,6 +381,64 @@ __device__ __forceinline__ void store_slice_b(const float4 (&r)[Cfg::RB], const 
   }
 }
 
+// The staged K loop: each BK slice of op(A) and op(B) is loaded into registers
+// while the previous one (in the other half of the shared-memory ring) is
+// consumed, then stored transposed to [k][m] / [k][n].  INTERIOR: every row and
+// column of the tile is in range and 16-byte loads are legal, so full slices are
+// read without checks and only a slice past K checks k.  Otherwise every load
+// checks every bound.
+template <class Cfg, bool INTERIOR>
+__device__ __forceinline__ void staged_loop(const GemmArgs& p, const float* Ab, const float* Bb, int m0, int n0,
+                                            int K, int tid, int tx, int ty, AccTile<Cfg::TM, Cfg::TN>& acc) {
+  constexpr int TM = Cfg::TM, TN = Cfg::TN, BK = Cfg::BK, CM = Cfg::CM, CN = Cfg::CN;
+  constexpr int PART = INTERIOR ? kLoadKTail : kLoadGeneral;
+  extern __shared__ __align__(16) float smem[];
+  float4 ra[Cfg::RA], rb[Cfg::RB];
+  const int nk = (K + BK - 1) / BK;
+  if (INTERIOR && BK <= K) {
+    load_slice_a<Cfg, kLoadFast>(ra, p, Ab, m0, 0, K, tid);
+    load_slice_b<Cfg, kLoadFast>(rb, p, Bb, n0, 0, K, tid);
+  } else {
+    load_slice_a<Cfg, PART>(ra, p, Ab, m0, 0, K, tid);
+    load_slice_b<Cfg, PART>(rb, p, Bb, n0, 0, K, tid);
+  }
+  store_slice_a<Cfg>(ra, p, smem, tid);
+  store_slice_b<Cfg>(rb, p, smem + BK * Cfg::LDS_A, tid);
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const float* As = smem + (kt & 1) * Cfg::STAGE_FLOATS;
+    const float* Bs = As + BK * Cfg::LDS_A;
+    const bool more = kt + 1 < nk;
+    if (more) {
+      const int kn = (kt + 1) * BK;
+      if (INTERIOR && kn + BK <= K) {
+        load_slice_a<Cfg, kLoadFast>(ra, p, Ab, m0, kn, K, tid);
+        load_slice_b<Cfg, kLoadFast>(rb, p, Bb, n0, kn, K, tid);
+      } else {
+        load_slice_a<Cfg, PART>(ra, p, Ab, m0, kn, K, tid);
+        load_slice_b<Cfg, PART>(rb, p, Bb, n0, kn, K, tid);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      float a[TM], bv[TN];
+#pragma unroll
+      for (int ic = 0; ic < TM / CM; ++ic)
+        load_vec_smem<CM>(a + ic * CM, As + k * Cfg::LDS_A + Cfg::swz_a(ic * (Cfg::WY * CM) + ty * CM, k));
+#pragma unroll
+      for (int jc = 0; jc < TN / CN; ++jc)
+        load_vec_smem<CN>(bv + jc * CN, Bs + k * Cfg::LDS_B + Cfg::swz_b(jc * (Cfg::WX * CN) + tx * CN, k));
+      acc.fma(a, bv);
+    }
+    if (more) {
+      float* An = smem + ((kt + 1) & 1) * Cfg::STAGE_FLOATS;
+      store_slice_a<Cfg>(ra, p, An, tid);
+      store_slice_b<Cfg>(rb, p, An + BK * Cfg::LDS_A, tid);
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- kernel
 template <class Cfg, bool SPLIT>
 __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
@@ -345,7 +446,8 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
   pdl_wait();
   pdl_launch_dependents();
   const int tid = threadIdx.x;
-  const int tx = tid % Cfg::WX, ty = tid / Cfg::WX;
+  int tx, ty;
+  thread_coords<Cfg>(tid, tx, ty);
   const int m0 = blockIdx.x * Cfg::BM, n0 = blockIdx.y * Cfg::BN;
   // SPLIT instances: blockIdx.z enumerates (batch entry, K split) pairs, split
   // s covers k in [s * kchunk, min(K, (s + 1) * kchunk)) and writes its own
@@ -370,52 +472,11 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
 
   const int nk = (K + BK - 1) / BK;
   if constexpr (Cfg::STAGED) {
-    extern __shared__ __align__(16) float smem[];
-    float4 ra[Cfg::RA], rb[Cfg::RB];
-    // Interior tiles with 16-byte-loadable operands skip every bounds check.
-    const bool fast_mn = (m0 + Cfg::BM <= p.M) && (n0 + Cfg::BN <= p.N) && p.vecA && p.vecB;
-    if (fast_mn && BK <= K) {
-      load_slice_a<Cfg, true>(ra, p, Ab, m0, 0, K, tid);
-      load_slice_b<Cfg, true>(rb, p, Bb, n0, 0, K, tid);
-    } else {
-      load_slice_a<Cfg, false>(ra, p, Ab, m0, 0, K, tid);
-      load_slice_b<Cfg, false>(rb, p, Bb, n0, 0, K, tid);
-    }
-    store_slice_a<Cfg>(ra, p, smem, tid);
-    store_slice_b<Cfg>(rb, p, smem + BK * Cfg::LDS_A, tid);
-    __syncthreads();
-    for (int kt = 0; kt < nk; ++kt) {
-      const float* As = smem + (kt & 1) * Cfg::STAGE_FLOATS;
-      const float* Bs = As + BK * Cfg::LDS_A;
-      const bool more = kt + 1 < nk;
-      if (more) {
-        const int kn = (kt + 1) * BK;
-        if (fast_mn && kn + BK <= K) {
-          load_slice_a<Cfg, true>(ra, p, Ab, m0, kn, K, tid);
-          load_slice_b<Cfg, true>(rb, p, Bb, n0, kn, K, tid);
-        } else {
-          load_slice_a<Cfg, false>(ra, p, Ab, m0, kn, K, tid);
-          load_slice_b<Cfg, false>(rb, p, Bb, n0, kn, K, tid);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < BK; ++k) {
-        float a[TM], bv[TN];
-#pragma unroll
-        for (int ic = 0; ic < TM / CM; ++ic)
-          load_vec_smem<CM>(a + ic * CM, As + k * Cfg::LDS_A + Cfg::swz_a(ic * (Cfg::WY * CM) + ty * CM, k));
-#pragma unroll
-        for (int jc = 0; jc < TN / CN; ++jc)
-          load_vec_smem<CN>(bv + jc * CN, Bs + k * Cfg::LDS_B + Cfg::swz_b(jc * (Cfg::WX * CN) + tx * CN, k));
-        acc.fma(a, bv);
-      }
-      if (more) {
-        float* An = smem + ((kt + 1) & 1) * Cfg::STAGE_FLOATS;
-        store_slice_a<Cfg>(ra, p, An, tid);
-        store_slice_b<Cfg>(rb, p, An + BK * Cfg::LDS_A, tid);
-      }
-      __syncthreads();
-    }
+    // Interior tiles with 16-byte-loadable operands run a loop whose loads check
+    // nothing but the K tail; edge tiles and unaligned operands run the general one.
+    const bool interior = (m0 + Cfg::BM <= p.M) && (n0 + Cfg::BN <= p.N) && p.vecA && p.vecB;
+    if (interior) staged_loop<Cfg, true>(p, Ab, Bb, m0, n0, K, tid, tx, ty, acc);
+    else staged_loop<Cfg, false>(p, Ab, Bb, m0, n0, K, tid, tx, ty, acc);
   } else {
     // Direct: every thread reads its own rows of op(A) and columns of op(B).
     for (int kt = 0; kt < nk; ++kt) {
@@ -493,7 +554,9 @@ __global__ void __launch_bounds__(Cfg::T) simt_gemm_kernel(const GemmArgs p) {
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) out[i][j] = acc.get(i, j);
-  epilogue<Cfg>(p, Cb, m0, n0, tx, ty, out);
+  int etx, ety;  // recomputed rather than kept live through the K loop
+  thread_coords<Cfg>(threadIdx.x, etx, ety);
+  epilogue<Cfg>(p, Cb, m0, n0, etx, ety, out);
 }
 
 template <int ID, bool SPLIT = false>

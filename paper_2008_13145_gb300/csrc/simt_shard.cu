@@ -1,7 +1,8 @@
 // One shard of the FP32 SIMT instantiations.  This file is compiled
 // kSimtShards times with -DKS_SHARD=<i>; shard i instantiates the config ids
-// with id % kSimtShards == i, so the 576 kernels (and the 192 split-K
-// instances) build in parallel.
+// with (id / 2) % kSimtShards == i (each unstaged / staged pair together, so every
+// shard holds the same mix of the costlier staged kernels), so the 576 kernels
+// (and the 192 split-K instances) build in parallel.
 #include <utility>
 
 #include "simt_gemm.cuh"
@@ -18,7 +19,7 @@ namespace {
 
 template <int ID>
 void reg_one(LaunchFn* table, LaunchFn* split, OccFn* occ) {
-  if constexpr (ID % kSimtShards == KS_SHARD && ID % KS_SUBSET == 0) {
+  if constexpr ((ID / 2) % kSimtShards == KS_SHARD && ID % KS_SUBSET == 0) {
     table[ID] = &launch_simt<ID, false>;
     if constexpr (split_eligible(ID)) {
       split[ID] = &launch_simt<ID, true>;
