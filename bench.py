@@ -15,8 +15,9 @@ the GEMMs); the share of
 the per-shape exhaustive optimum (each held-out size re-run with the best of
 all configs in the GB300 sweep table -- the 576 base configs and the split-K
 kind -- untimed pass); the dominant
-kernel's roofline; the FP64 CPU oracle timed on a bounded sample on the host
-cores (``cpu_baseline``).
+kernel's roofline; the FP32 kernels on one large product beside the vendor
+library's FP32 GEMM (``fp32_large``, context); the FP64 CPU oracle timed on a
+bounded sample on the host cores (``cpu_baseline``).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -366,6 +367,7 @@ def run_ours(args, ws, rank, local):
 
     tc = tc_families(args, ks, tune, shapes, te, bufs, stream, dev) if not args.no_tc else None
     tc_large = tc_large_shapes(ks) if not args.no_tc else None
+    fp32_large = fp32_large_shape(ks) if not args.no_tc else None
     grouped = grouped_launch(ks, tune) if not args.no_tc else None
     vgg16 = vgg16_inference(ks) if not args.no_tc else None
     c0 = single_gemm_256(ks, tune)
@@ -401,6 +403,7 @@ def run_ours(args, ws, rank, local):
         "selectors": selectors,
         "tc": tc,
         "tc_large": tc_large,
+        "fp32_large": fp32_large,
         "grouped": grouped,
         "vgg16": vgg16,
         "single_gemm_256": c0,
@@ -557,6 +560,63 @@ def tc_large_shapes(ks, n: int = 8192, reps: int = 10, warmup: int = 3):
                                     "best_config": best_id, "best_value": flops / (best_ms * 1e9)}
         del A, B
     return out
+
+
+def fp32_large_shape(ks, n: int = 4096, reps: int = 10, warmup: int = 3):
+    """The FP32 SIMT family on one large product: n^3 NN through gemm() with the
+    FP32 deployment (its decision tree picks the kernel) and with each deployed
+    kernel directly, CUDA-event timed like tc_large_shapes (A, B and C together
+    exceed L2), against the FP32 FMA peak.  Beside it, as context only, the
+    vendor library's FP32 GEMM on the same operands (torch.mm with TF32 off, i.e.
+    cuBLAS computing in FP32 with FMA instructions), with the largest difference
+    between its product and ours."""
+    import torch
+    dpath = os.path.join(DEPLOY, "f32.json")
+    if not os.path.exists(dpath):
+        return None
+    dep = json.load(open(dpath))
+    h = ks.Handle(dep)
+    flops = 2.0 * n ** 3
+    A = torch.empty(n * n, device="cuda")
+    B = torch.empty(n * n, device="cuda")
+    ks.fill_uniform(A, n, n, n, 1, 81)
+    ks.fill_uniform(B, n, n, n, 1, 82)
+    C = torch.empty(n * n, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(run):
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed(lambda: ks.gemm(h, "N", "N", n, n, n, 1.0, A, n, B, n, 0.0, C, n, 1))
+    tf = flops / (ms * 1e9)
+    per_cfg = {c: flops / (timed(lambda c=c: ks.gemm_with_config(c, "N", "N", n, n, n, 1.0, A, n, B, n, 0.0, C, n, 1))
+                           * 1e9) for c in dep["config_ids"]}
+    ks.gemm(h, "N", "N", n, n, n, 1.0, A, n, B, n, 0.0, C, n, 1)
+    A2, B2 = A.view(n, n), B.view(n, n)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        lib_ms = timed(lambda: torch.mm(A2, B2))
+        diff = (torch.mm(A2, B2) - C.view(n, n)).abs().max().item()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    best = max(per_cfg, key=per_cfg.get)
+    return {"shape": f"{n}^3 NN", "timing": f"{warmup} warm-up + {reps} timed back-to-back launches",
+            "value": tf, "unit": "TFLOP/s", "ms": ms, "config": ks.select_kernel(h, n, n, n, 1),
+            "roofline": {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tf / FP32_PEAK_TFLOPS},
+            "deployed_configs": {str(c): v for c, v in per_cfg.items()}, "best_config": best,
+            "best_value": per_cfg[best],
+            "vendor_fp32_gemm_context": {"what": "torch.mm, TF32 off (cuBLAS FP32 GEMM)", "value": flops / (lib_ms * 1e9),
+                                         "unit": "TFLOP/s", "max_abs_diff_vs_ours": diff}}
 
 
 def grouped_launch(ks, tune):

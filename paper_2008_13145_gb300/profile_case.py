@@ -2,6 +2,11 @@
 
     python -m paper_2008_13145_gb300.profile_case --config 531 --shape 4096 4096 4096 1 N N --reps 3
     python -m paper_2008_13145_gb300.profile_case --grouped 1216 --reps 2
+    python -m paper_2008_13145_gb300.profile_case --vendor-fp32 --shape 4096 4096 4096 1 N N --reps 2
+
+--vendor-fp32 runs the vendor library's FP32 GEMM instead (torch.mm with TF32
+off, a batch-1 NN product only): a reference point for profiling, not part of
+the library.
 
 Inputs are filled on the device by the library; nothing is checked here
 (parity lives in tests/).  Prints the CUDA-event time of the last launch.
@@ -21,6 +26,7 @@ def main(argv=None):
     ap.add_argument("--config", type=int)
     ap.add_argument("--shape", nargs=6, metavar=("M", "N", "K", "BATCH", "TA", "TB"))
     ap.add_argument("--grouped", type=int, help="config id: run the 256-problem grouped workload")
+    ap.add_argument("--vendor-fp32", action="store_true", help="time torch.mm (cuBLAS FP32, TF32 off) instead")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -37,6 +43,21 @@ def main(argv=None):
         for _ in range(a.reps):
             e0.record()
             plan.run()
+            e1.record()
+    elif a.vendor_fp32:
+        M, N, K, b = (int(x) for x in a.shape[:4])
+        if b != 1 or a.shape[4] != "N" or a.shape[5] != "N":
+            raise SystemExit("--vendor-fp32 takes batch-1 NN shapes only")
+        A = torch.empty(M * K, device="cuda")
+        B = torch.empty(K * N, device="cuda")
+        ks.fill_uniform(A, M, K, K, 1, 1)
+        ks.fill_uniform(B, K, N, N, 1, 2)
+        A2, B2 = A.view(M, K), B.view(K, N)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        flops = 2.0 * M * N * K
+        for _ in range(a.reps):
+            e0.record()
+            torch.mm(A2, B2)
             e1.record()
     else:
         M, N, K, b = (int(x) for x in a.shape[:4])
