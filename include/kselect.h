@@ -561,21 +561,19 @@ gemm_status_t mlp_forward(int32_t n, const float* params_dev, const float* X_dev
 gemm_status_t mlp_loss_grad(int32_t n, const float* params_dev, const float* X_dev, const float* T_dev,
                             const float* mask_dev, float* grad_dev, float* loss_dev, void* stream);
 
-/* mlp_loss_grad for callers that cannot allocate device memory: code that runs
- * while a CUDA stream is being captured into a graph, where an allocation
- * would break the capture; processes whose device memory is owned by an
- * external pool that reserved it all up front; and latency-bound serving or
- * training loops where a cudaMalloc/cudaFree (which may synchronise the
- * device) is not acceptable.  The paper has no counterpart: this is an
- * interface choice of the library.
+/* mlp_loss_grad for callers that cannot allocate device memory: processes
+ * whose device memory is owned by an external pool that reserved it all up
+ * front, and latency-bound serving or training loops where a
+ * cudaMalloc/cudaFree (which may synchronise the device) is not acceptable.
+ * The paper has no counterpart: this is an interface choice of the library.
  * Same inputs, outputs and results as mlp_loss_grad, but its scratch is a
  * fixed array inside the library (about 5.3 MB per device, held until the
  * process exits); n is limited to 8192 samples, larger n returns
  * GEMM_ERR_UNSUPPORTED.  It calls no cudaMalloc or cudaFree.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
- * calls on a device share the array: calls that overlap on the GPU (different
- * streams, or different host threads) race and give wrong results. */
+ * that device current.  All calls on a device share the array: calls that
+ * overlap on the GPU (different streams, or different host threads) race and
+ * give wrong results. */
 gemm_status_t mlp_loss_grad_noalloc(int32_t n, const float* params_dev, const float* X_dev, const float* T_dev,
                                     const float* mask_dev, float* grad_dev, float* loss_dev, void* stream);
 

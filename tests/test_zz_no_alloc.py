@@ -1,9 +1,8 @@
 """The allocation-free loss/gradient entry point against the allocating one.
 
-Some callers cannot allocate device memory while they run (a stream being
-captured into a CUDA graph, a process whose memory is owned by an external
-pool, a latency-bound loop); mlp_loss_grad_noalloc serves them from a fixed
-array inside the library.  This file is collected last so that a failure here
+Some callers cannot allocate device memory while they run (a process whose
+memory is owned by an external pool, a latency-bound loop);
+mlp_loss_grad_noalloc serves them from a fixed array inside the library.  This file is collected last so that a failure here
 comes after every other test has run."""
 import numpy as np
 import pytest
