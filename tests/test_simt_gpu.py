@@ -338,3 +338,30 @@ def test_host_pipeline(lib, torch):
             continue
         ref, den = og.gemm(sh.transA, sh.transB, sh.M, sh.N, sh.K, 1.25, A, B, beta, C0 if beta != 0 else None)
         assert og.error_ratio(got, ref, den) <= TOL_F32, sh
+
+
+def test_staged_configs_equal_their_direct_twins_bit_for_bit(lib, torch):
+    """A staged config (shared-memory slices, warp lane map, interior-tile loop)
+    and its unstaged twin (same TM, TN, work group and K-step, operands read
+    straight from global memory) accumulate every element's K terms in the same
+    order with the same packed FMAs, so on real-valued data their products must
+    agree to the bit: whatever the staged path does to feed its FMAs, it may
+    not change a result.  Interior and edge tiles (ragged M, N, K), every
+    transpose pair, alpha and beta both non-trivial."""
+    ks = lib
+    for n_case, (M, N, K, b) in enumerate([(131, 97, 75, 2), (192, 256, 160, 1)]):
+        for tA, tB in TRANS:
+            shape = wl.Shape(M, N, K, b, tA, tB)
+            A, B, C0 = wl.gemm_inputs(shape, seed=40 + n_case, beta_nonzero=True)
+            gA, gB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+            gC0 = torch.from_numpy(np.ascontiguousarray(C0)).cuda()
+            ldc = C0.shape[2]
+            for direct in range(0, 576, 2):
+                outs = []
+                for cid in (direct, direct + 1):
+                    C = gC0.clone()
+                    ks.gemm_with_config(cid, tA, tB, M, N, K, 0.75, gA, A.shape[2], gB, B.shape[2], -0.5, C, ldc, b)
+                    outs.append(C)
+                torch.cuda.synchronize()
+                # bit patterns: the results, signed zeros, and the untouched NaN padding of C
+                assert torch.equal(outs[0].view(torch.int32), outs[1].view(torch.int32)), (direct, shape)
