@@ -362,18 +362,17 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc
   auto kern = tc::tc_gemm_kernel<BN, STAGES, TF32, GROUPED>;
   static unsigned long long done_mask = 0;
   static int slots_cache[64] = {0};
+  static int dyn_cache[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & bit)) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
     // Resident CTAs per SM from the kernel's own resources: shared memory
     // (plus what the system reserves per CTA), registers and TMEM columns.
     // The runtime's occupancy query reports one CTA per SM for these kernels
     // whatever their size, while the SM runs as many as these resources allow.
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, kern);
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
     int smem_sm = 0, sms = 0, reserved = 0, regs_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -381,14 +380,27 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const tc
     cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     const int regs = (fa.numRegs + 7) / 8 * 8;
-    int occ = std::min(smem_sm / (Cfg::SMEM_BYTES + (int)fa.sharedSizeBytes + reserved), regs_sm / (regs * tc::kThreads));
+    const int per_cta = (int)fa.sharedSizeBytes + reserved;
+    const int occ_smem = smem_sm / (Cfg::SMEM_BYTES + per_cta);
+    int occ = std::min(occ_smem, regs_sm / (regs * tc::kThreads));
     occ = std::max(1, std::min(occ, 512 / Cfg::TMEM_COLS));  // every resident CTA must fit in TMEM
+    // Where shared memory alone would let more CTAs onto an SM than TMEM or the
+    // registers hold (BN 128 and BN 256 with two stages), ask for enough of it that
+    // it cannot.  Otherwise the block scheduler may place an extra CTA on an SM
+    // whose TMEM is taken: it waits in tcgen05.alloc until a persistent CTA there
+    // has finished all its tiles, while the grid, sized for `occ` CTAs per SM,
+    // leaves other SMs idle.  The padding is never touched.
+    int dyn = Cfg::SMEM_BYTES;
+    if (occ_smem > occ) dyn = std::max(dyn, (smem_sm / (occ + 1) - per_cta + 16 + 15) / 16 * 16);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    dyn_cache[dev & 63] = dyn;
     slots_cache[dev & 63] = occ * sms;
     __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);
   }
   const int ctas = std::min(a.num_tiles, slots_cache[dev & 63]);
-  return launch_pdl(kern, dim3((unsigned)ctas, 1, 1), dim3(tc::kThreads, 1, 1), Cfg::SMEM_BYTES, s, nullptr, 0, ma,
-                    mb, a, g);
+  return launch_pdl(kern, dim3((unsigned)ctas, 1, 1), dim3(tc::kThreads, 1, 1), (size_t)dyn_cache[dev & 63], s,
+                    nullptr, 0, ma, mb, a, g);
 }
 
 using TcLaunch = cudaError_t (*)(const CUtensorMap&, const CUtensorMap&, const tc::TcArgs&, const tc::GroupArgs&,
