@@ -14,7 +14,7 @@ timed region, uploads and downloads on the library's copy streams overlapping
 the GEMMs); the share of
 the per-shape exhaustive optimum (each held-out size re-run with the best of
 all configs in the GB300 sweep table -- the 576 base configs and the split-K
-kind -- untimed pass); the dominant
+kind -- untimed passes, per-shape medians of 3 on both sides); the dominant
 kernel's roofline; the FP32 kernels on one large product beside the vendor
 library's FP32 GEMM (``fp32_large``, context); the FP64 CPU oracle timed on a
 bounded sample on the host cores (``cpu_baseline``).
@@ -258,18 +258,22 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize(dev)
         return np.array([a.elapsed_time(b) for a, b in ev])
 
-    # Warm-up steps (selected kernels); the last one also times every launch, after
+    def per_launch_median(cfgs=None, passes=3):
+        return np.median([per_launch_ms(cfgs) for _ in range(passes)], axis=0)
+
+    # Warm-up steps (selected kernels); the last ones also time every launch, after
     # the first has loaded every module.
     for _ in range(args.warmup - 1):
         step()
-    sel_ms = per_launch_ms()
+    sel_ms = per_launch_median()
     # Untimed reference passes: every shape with its exhaustive-best config (the
-    # first loads the kernels the deployment does not use, the second is timed).
+    # first loads the kernels the deployment does not use, the next ones are timed).
     per_launch_ms(best_cfg)
-    exh_ms = per_launch_ms(best_cfg)
+    exh_ms = per_launch_median(best_cfg)
     ratio = np.minimum(exh_ms / sel_ms, 1.0)
     live = {"geomean": float(np.exp(np.mean(np.log(ratio)))), "mean": float(np.mean(ratio)),
-            "source": "per-shape launch times this run: exhaustive-best config vs selected config"}
+            "source": "per-shape launch times this run, median of 3 passes each: exhaustive-best config vs "
+                      "selected config"}
     # Dominant kernel: the deployed config with the largest share of step time.
     by_cfg = {}
     for c, t, sh in zip(chosen, sel_ms, shapes):
@@ -327,7 +331,7 @@ def run_ours(args, ws, rank, local):
                                                       dep["config_ids"])]
     for name, cfgs in alt.items():
         per_launch_ms(cfgs)
-        r = np.minimum(exh_ms / per_launch_ms(cfgs), 1.0)
+        r = np.minimum(exh_ms / per_launch_median(cfgs), 1.0)
         torch.cuda.synchronize(dev)
         e0.record(stream)
         for _ in range(10):
@@ -454,8 +458,9 @@ def tc_families(args, ks, tune, shapes, te, bufs, stream, dev):
 
         for _ in range(args.warmup):
             run()
-        sel = per_launch()
-        exh = per_launch(best)
+        sel = np.median([per_launch() for _ in range(3)], axis=0)
+        run(best)  # loads the kernels the deployment does not use
+        exh = np.median([per_launch(best) for _ in range(3)], axis=0)
         ratio = np.minimum(exh / sel, 1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
